@@ -316,6 +316,9 @@ def oem_path(G, c, d, pen: Penalty, lambdas: Sequence[float], tol: float = 1e-7,
     G = np.asarray(G, dtype=np.float64)
     c = np.asarray(c, dtype=np.float64)
     p = c.size
+    # A = d I - G must use the same d as the threshold (effective_d raises it
+    # for MCP / SCAD when needed; any d >= lambda_1 is valid)
+    d = effective_d(d, pen)
     lambdas = np.asarray(lambdas, dtype=np.float64)
     L = lambdas.size
     beta = np.zeros(p) if beta0 is None else np.array(beta0, dtype=np.float64)

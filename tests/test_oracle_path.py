@@ -228,6 +228,22 @@ def test_paths_satisfy_kkt(kind):
         assert kkt_violation(G, c, r.beta[l], lam, pen) <= 1e-9
 
 
+@pytest.mark.parametrize("kind,gam", [("mcp", 3.0), ("scad", 3.7)])
+def test_small_d_raised_consistently(kind, gam):
+    """With lambda_1(G) below 1/gamma (MCP) or 1/(gamma-1) (SCAD), d is raised
+    to d_eff; the fixed point must still satisfy the KKT conditions."""
+    X, y, G, c, N = _small(n=2000, p=6, rho=0.2)
+    s = 0.25 / float(np.linalg.eigvalsh(G)[-1])
+    G2, c2 = G * s, c * s   # lambda_1(G2) = 0.25 < 1/(gamma-1)
+    pen = Penalty(kind, gamma=gam)
+    d = lanczos_d(G2)[0]
+    assert d < 1.0 / (gam - 1.0)
+    lam = 0.1 * lambda_max(c2, pen)
+    r = oem_path(G2, c2, d, pen, [lam], tol=1e-13, max_iter=500000)
+    assert r.converged.all()
+    assert kkt_violation(G2, c2, r.beta[0], lam, pen) <= 1e-9
+
+
 def test_kkt_detects_a_wrong_solution():
     X, y, G, c, N = _small(p=8)
     pen = Penalty("lasso")
