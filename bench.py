@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark of the OEM hot path on GB300.
+
+Default workload (one "step" = the whole path over one synthetic problem):
+n = 1,000,000 rows, p = 500, float32 X with AR(0.5) rows, 25 nonzero true
+coefficients (|beta_j| ~ U[0.5, 2], random signs), noise sd 1; the X^T X /
+X^T y pass (split-bfloat16 products on the tcgen05 tensor cores), d by
+Lanczos, the lambda grids, and warm-started paths of 100 lambdas for four
+penalties at once (lasso, elastic net alpha = 0.5, MCP gamma = 3, SCAD
+gamma = 3.7), tol 1e-7. Metric: fitted paths per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 oracle (the plain CPU restatement of the
+method) on the host cores on a bounded sample of the same workload.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthgen  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+WORKLOAD = "four_penalties_f32_n1e6_p500"
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+def penalties_of(w):
+    ex = w.extra
+    out = []
+    for k in w.penalties:
+        if k == "enet":
+            out.append(("enet", {"alpha": ex.get("alpha", 0.5)}))
+        elif k == "mcp":
+            out.append(("mcp", {"gamma": ex.get("gamma_mcp", 3.0)}))
+        elif k == "scad":
+            out.append(("scad", {"gamma": ex.get("gamma_scad", 3.7)}))
+        elif k == "grp.lasso":
+            out.append(("grp.lasso", {"groups": np.arange(w.p) // w.group_size}))
+        else:
+            out.append((k, {}))
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# FP64 oracle on the host (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_step(w, n_sample: int, seed_shift: int = 0):
+    """One bounded oracle step: the Gram of the first n_sample rows (its time
+    scaled to the full n, the Gram being linear in n), d, lambda grids and
+    the warm-started paths of every penalty on that Gram. Returns
+    (scaled seconds, raw seconds)."""
+    import oracle
+    ww = synthgen.Workload(**{**w.__dict__, "seed": w.seed + seed_shift})
+    X, y, _, _ = synthgen.make_data(ww, n=n_sample)
+    t0 = time.perf_counter()
+    G, c, N, n = oracle.gram_sums(synthgen.as_f64(X), y)
+    t_gram = time.perf_counter() - t0
+    G, c = G / n, c / n
+    t1 = time.perf_counter()
+    d = oracle.lanczos_d(G)[0]
+    for kind, kw in penalties_of(w):
+        pen = oracle.Penalty(kind, **kw)
+        lams = oracle.lambda_grid(oracle.lambda_max(c, pen), w.nlambda, w.lambda_min_ratio)
+        oracle.oem_path(G, c, d, pen, lams, tol=w.tol, max_iter=10000)
+    t_rest = time.perf_counter() - t1
+    return t_gram * (w.n / n_sample) + t_rest, t_gram + t_rest
+
+
+def cpu_cores():
+    return os.cpu_count() or 1
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return 0
+    n_sample = min(w.n, args.cpu_sample_rows)
+    npaths = len(w.penalties)
+    for _ in range(args.warmup):
+        oracle_step(w, n_sample)
+    times = []
+    for k in range(args.steps):
+        s, _ = oracle_step(w, n_sample, seed_shift=0)
+        times.append(s)
+    total = sum(times)
+    value = npaths * args.steps / total
+    sample = (f"Gram of the first {n_sample} of {w.n} rows (time scaled by n/{n_sample}), then d "
+              f"and {npaths} x {w.nlambda}-lambda paths on that Gram, per step")
+    line = {
+        "impl": "reference", "metric": "fitted paths/s", "value": value, "unit": "paths/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "p": w.p, "penalties": list(w.penalties),
+                   "nlambda": w.nlambda, "tol": w.tol},
+        "cpu_baseline": {"value": value, "unit": "paths/s", "cores": cpu_cores(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, w, rank, world, local_rank):
+    import torch
+    import paper_1801_09661_gb300 as oem
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    ww = synthgen.Workload(**{**w.__dict__, "seed": w.seed + 1000 * rank})
+    t0 = time.time()
+    X, y, _, _ = synthgen.make_data(ww)
+    t_gen = time.time() - t0
+    Xd = oem.padded(X, device=dev)
+    yd = torch.from_numpy(y).to(dev)
+    pens = [oem.Penalty(k, **kw) for k, kw in penalties_of(w)]
+    npen = len(pens)
+    ctx = oem.Context(local_rank, budget_bytes=64 << 30)
+    stream = torch.cuda.current_stream(dev)
+    opts = dict(nlambda=w.nlambda, lambda_min_ratio=w.lambda_min_ratio, tol=w.tol,
+                gram_mode=args.gram_mode)
+    beta, lam, its, conv = (torch.empty((npen, w.nlambda, w.p), dtype=torch.float64, device=dev),
+                            torch.empty((npen, w.nlambda), dtype=torch.float64, device=dev),
+                            torch.empty((npen, w.nlambda), dtype=torch.int32, device=dev),
+                            torch.empty((npen, w.nlambda), dtype=torch.uint8, device=dev))
+    dout = torch.empty(1, dtype=torch.float64, device=dev)
+    out = (beta, lam, its, conv, dout)
+
+    def step():
+        oem.oem_fit(ctx, Xd, yd, pens, out=out, **opts)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    # ---------------- timed region: device-resident inputs
+    clocks = ClockSampler(local_rank)
+    ctx.profile(True)
+    l0 = ctx.launches()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = ctx.launches() - l0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    status = ctx.sync()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    its_h = its.cpu().numpy().astype(np.int64)
+    conv_h = conv.cpu().numpy()
+    loops = int(its_h.sum(axis=1).max())
+    # ---------------- e2e: pinned host buffers, copies inside the timed region
+    Xh = torch.from_numpy(np.ascontiguousarray(X)).pin_memory()
+    yh = torch.from_numpy(y).pin_memory()
+    bh = torch.empty(beta.shape, dtype=beta.dtype).pin_memory()
+    lh = torch.empty(lam.shape, dtype=lam.dtype).pin_memory()
+    ih = torch.empty(its.shape, dtype=its.dtype).pin_memory()
+    ch = torch.empty(conv.shape, dtype=conv.dtype).pin_memory()
+    Xe = torch.empty_like(Xd)
+    ye = torch.empty_like(yd)
+
+    def e2e_step():
+        Xe.copy_(Xh, non_blocking=True)
+        ye.copy_(yh, non_blocking=True)
+        oem.oem_fit(ctx, Xe, ye, pens, out=out, **opts)
+        bh.copy_(beta, non_blocking=True)
+        lh.copy_(lam, non_blocking=True)
+        ih.copy_(its, non_blocking=True)
+        ch.copy_(conv, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = f0.elapsed_time(f1)
+    if world > 1:
+        t = torch.tensor([ms_e2e], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    h2d = Xh.numel() * Xh.element_size() + yh.numel() * yh.element_size()
+    d2h = sum(t.numel() * t.element_size() for t in (bh, lh, ih, ch))
+
+    if rank != 0:
+        ctx.close()
+        return 0
+    peaks, peak_src = load_peaks()
+    total_paths = npen * args.steps * world
+    value = total_paths / (ms / 1000.0)
+    # roofline: the OEM iteration kernel (dominant) against HBM
+    p = w.p
+    it_ms, it_n = prof.get("oem_iter_kernel", (float("nan"), 0))
+    bytes_per_loop = p * (p + 1) / 2 * 4 + npen * 3 * p * 4
+    it_bytes = loops * bytes_per_loop  # per launch (one launch per step)
+    it_ms_launch = it_ms / max(1, it_n)
+    it_gbs = it_bytes / (it_ms_launch / 1000.0) / 1e9
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
+    # the Gram pass (tensor cores): useful flops n (p+1)(p+2)
+    gk = "gram_tc_kernel" if "gram_tc_kernel" in prof else "gram_simt_kernel"
+    g_ms, g_n = prof.get(gk, (float("nan"), 0))
+    g_ms_launch = g_ms / max(1, g_n)
+    g_flops = w.n * (p + 1) * (p + 2)
+    g_tf = g_flops / (g_ms_launch / 1000.0) / 1e12
+    nprod = 4 if args.gram_mode in ("auto", "split_bf16") else 1
+    nt = math.ceil((p + 1) / 128)
+    mma_flops = 2.0 * (nt * (nt + 1) / 2) * 128 * 128 * w.n * nprod
+    bf16 = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
+    step_ms = ms / args.steps
+    kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
+                   "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
+               for k, v in prof.items()}
+    line = {
+        "metric": "fitted paths/s", "value": value, "unit": "paths/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "p": p, "penalties": list(w.penalties),
+                   "nlambda": w.nlambda, "lambda_min_ratio": w.lambda_min_ratio, "tol": w.tol,
+                   "gram_mode": args.gram_mode, "x_dtype": w.dtype,
+                   "l2": "inputs larger than L2 (X is %.2f GB)" % (X.nbytes / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": npen * args.steps * world / (ms_e2e / 1000.0), "unit": "paths/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "oem_iter_kernel", "bound": "hbm", "achieved": it_gbs, "peak": hbm,
+                     "unit": "GB/s", "frac": it_gbs / hbm, "traffic": None,
+                     "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": it_bytes, "loop_iterations": loops,
+                     "ms_per_launch": it_ms_launch},
+        "roofline_gram": {"kernel": gk, "bound": "tensor", "achieved": g_tf, "peak": bf16,
+                          "unit": "TFLOP/s", "frac": g_tf / bf16, "traffic": None,
+                          "peak_source": peak_src, "useful_flops": g_flops,
+                          "mma_flops": mma_flops,
+                          "mma_tflops": mma_flops / (g_ms_launch / 1000.0) / 1e12,
+                          "ms_per_launch": g_ms_launch,
+                          "hbm_gbs": X.nbytes / (g_ms_launch / 1000.0) / 1e9},
+        "x_tx_tflops": g_tf,
+        "kernels": kernels,
+        "clocks": clk,
+        "status": status,
+        "converged_frac": float(conv_h.mean()),
+        "datagen_s": t_gen,
+    }
+    if not args.no_cpu_baseline:
+        n_sample = min(w.n, args.cpu_sample_rows)
+        scaled, raw = oracle_step(w, n_sample)
+        line["cpu_baseline"] = {
+            "value": npen / scaled, "unit": "paths/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": (f"Gram of the first {n_sample} of {w.n} rows (time scaled by n/{n_sample}),"
+                       f" then d and {npen} x {w.nlambda}-lambda paths; {raw:.1f} s of CPU work")}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synthgen.WORKLOADS))
+    ap.add_argument("--gram-mode", default="auto",
+                    choices=["auto", "split_bf16", "tf32", "fp32", "fp64", "bf16"])
+    ap.add_argument("--cpu-sample-rows", type=int, default=100_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    w = synthgen.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    rc = run_ours(args, w, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,218 @@
+/*
+ * oem.h -- C ABI of the GB300 (sm_103a) OEM penalized least-squares library.
+ *
+ * The library computes the data-parallel hot path of the orthogonalizing EM
+ * (OEM) method for penalized linear regression on tall data (Huling & Qian,
+ * "Fast penalized regression and cross validation for tall data with the oem
+ * package", arXiv 1801.09661):
+ *   - the sufficient statistics X^T X, X^T y, y^T y in one pass over X, split
+ *     into per-fold partial sums for cross validation (Section 3);
+ *   - the OEM constant d >= lambda_1(X^T X / n) (Section 2.1, by Lanczos);
+ *   - warm-started OEM paths beta <- threshold(X^T y/n + d beta - (X^T X/n) beta)
+ *     for the lasso, elastic net, MCP, SCAD and group lasso (Section 2.2);
+ *   - K-fold cross validation from the fold statistics (Sections 3, 5.5).
+ *
+ * Conventions (all entry points):
+ *   - Array arguments are DEVICE pointers owned by the caller, unless a
+ *     parameter says "host". The library never frees caller memory.
+ *   - Matrices are row-major (C order). X is n x p with leading dimension
+ *     ldx >= p (elements); ldx * sizeof(element) must be a multiple of 16 and
+ *     X, y must be 16-byte aligned, else OEM_EINVAL.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL = the
+ *     legacy default stream) and the call returns without waiting, except
+ *     where a parameter is a host output. Argument errors are returned before
+ *     anything is launched. Conditions found on the device (non-finite input,
+ *     a bounded device wait that expired) are recorded in the context and
+ *     returned by oem_sync().
+ *   - Workspace comes from a per-context arena that never exceeds the byte
+ *     budget given to oem_create (OEM_EBUDGET otherwise). A context is used by
+ *     one host thread and one stream at a time.
+ *   - Objective (reading of the paper's scaling, Section 2.1 and the oem.xtx
+ *     example of Section 5.6): minimise (1/2n)||y - X beta||^2 + P_lambda(beta),
+ *     i.e. beta^T G beta / 2 - c^T beta + P_lambda(beta) with G = X^T X / n,
+ *     c = X^T y / n.
+ */
+#ifndef OEM_GB300_H
+#define OEM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct oem_ctx oem_ctx;
+
+/* Status codes. Negative = error, 0 = ok, positive = warning. */
+enum {
+  OEM_OK = 0,
+  OEM_WARN_NOTCONV = 1,   /* some (lambda, penalty) hit max_iter */
+  OEM_EINVAL = -1,        /* bad argument (size, pointer, alignment, option) */
+  OEM_ENOMEM = -2,        /* device allocation failed */
+  OEM_EBUDGET = -3,       /* workspace would exceed the context's byte budget */
+  OEM_ECUDA = -4,         /* a CUDA runtime call failed */
+  OEM_ENONFINITE = -5,    /* NaN/Inf in X or y */
+  OEM_ETIMEOUT = -6,      /* a bounded device wait expired; results invalid */
+  OEM_EUNSUPPORTED = -7   /* valid request this build does not serve */
+};
+
+/* Element type of X (and y). y is float64 when X is float64, else float32. */
+enum { OEM_F64 = 0, OEM_F32 = 1, OEM_BF16 = 2 };
+
+/* How the Gram pass forms products and sums (Section 3, O(np^2) step):
+ *   FP64       : float64 products and sums on CUDA cores (X float64 or float32).
+ *   FP32       : float32 products, float32 sums over short row blocks, float64
+ *                across blocks, on CUDA cores (the plain form).
+ *   TF32       : tcgen05 tensor cores, kind::tf32 (X float32), float32
+ *                accumulation in tensor memory, compensated across blocks.
+ *   BF16       : tcgen05 kind::f16 with bfloat16 operands (X bfloat16: exact
+ *                products; the float32 y is carried exactly as three bfloat16
+ *                columns hi + mid + lo).
+ *   SPLIT_BF16 : tcgen05 kind::f16, X float32 split as hi + lo bfloat16,
+ *                products hi*hi + hi*lo + lo*hi + lo*lo (X float32).
+ *   AUTO       : SPLIT_BF16 for float32, BF16 for bfloat16, FP64 for float64. */
+enum {
+  OEM_GRAM_FP64 = 0,
+  OEM_GRAM_FP32 = 1,
+  OEM_GRAM_TF32 = 2,
+  OEM_GRAM_BF16 = 3,
+  OEM_GRAM_SPLIT_BF16 = 4,
+  OEM_GRAM_AUTO = 5
+};
+
+/* Penalties of Table 1 (Section 2.2 updates). */
+enum { OEM_LASSO = 0, OEM_ENET = 1, OEM_MCP = 2, OEM_SCAD = 3, OEM_GROUP_LASSO = 4 };
+
+/* Precision of the OEM iteration: float32 mat-vec with a compensated
+ * (float32 hi + lo) running u, or float64 throughout. */
+enum { OEM_ITER_F32 = 0, OEM_ITER_F64 = 1 };
+
+typedef struct oem_penalty {
+  int32_t kind;          /* OEM_LASSO .. OEM_GROUP_LASSO */
+  double alpha;          /* elastic net mixing alpha in [0,1] (Eq. net) */
+  double gamma;          /* MCP gamma > 1 (Eq. mcp), SCAD gamma > 2 (Eq. scad) */
+  const double* w;       /* host, p variable weights w_j >= 0, or NULL (all 1) */
+  const int32_t* group;  /* host, p group ids in [0, ngroups), group lasso only;
+                            each group's variables must be contiguous */
+  const double* cg;      /* host, ngroups group weights c_k >= 0, or NULL (sqrt|g_k|) */
+  int32_t ngroups;
+} oem_penalty;
+
+typedef struct oem_options {
+  int32_t nlambda;          /* lambdas per path (default 100) */
+  double lambda_min_ratio;  /* smallest / largest lambda (default 1e-3) */
+  const double* lambdas;    /* host, npen x nlambda user grid, or NULL (computed) */
+  double tol;               /* stop when max|dbeta| <= tol*max(1,max|beta|) (1e-7) */
+  int64_t max_iter;         /* iteration cap per lambda (default 10000) */
+  int32_t lanczos_steps;    /* Lanczos steps for d (default 64) */
+  int32_t gram_mode;        /* OEM_GRAM_* (default OEM_GRAM_AUTO) */
+  int32_t iter_precision;   /* OEM_ITER_F32 (default) or OEM_ITER_F64 */
+  int32_t cluster_ctas;     /* CTAs cooperating on one Gram in the iteration
+                               (0 = chosen by the library; else 1,2,4,8,16) */
+} oem_options;
+
+/* Fill *opt with the defaults listed above. */
+void oem_options_default(oem_options* opt);
+
+/* Create a context on CUDA device `device` whose workspace arena may grow to
+ * mem_budget_bytes (0 = 8 GiB). Returns OEM_OK and sets *ctx, or an error. */
+int oem_create(oem_ctx** ctx, int device, size_t mem_budget_bytes);
+
+/* Free the context and its workspace (synchronises the device first). */
+int oem_destroy(oem_ctx* ctx);
+
+/* Text of the last error recorded in ctx (static storage inside ctx). */
+const char* oem_last_error(const oem_ctx* ctx);
+
+/* Wait for all work enqueued on `stream`, then return (and clear) the worst
+ * device-side status recorded since the last oem_sync: OEM_OK,
+ * OEM_WARN_NOTCONV, OEM_ENONFINITE or OEM_ETIMEOUT. */
+int oem_sync(oem_ctx* ctx, void* stream);
+
+/* Number of kernels this context has launched so far (for accounting). */
+int64_t oem_kernel_launches(const oem_ctx* ctx);
+
+/* Per-kernel device timing. While enabled, every launch of this context is
+ * bracketed by CUDA events on its stream; oem_profile_get() waits for the
+ * pending events and returns the accumulated device milliseconds and launch
+ * count of one kernel class (0 <= kernel < OEM_PROF_NKERNELS, names from
+ * oem_profile_name). Enabling (again) clears the totals. */
+enum {
+  OEM_PROF_FOLD_SORT = 0, OEM_PROF_CHUNKS = 1, OEM_PROF_GRAM_SIMT = 2, OEM_PROF_GRAM_TC = 3,
+  OEM_PROF_GRAM_REDUCE = 4, OEM_PROF_ASSEMBLE = 5, OEM_PROF_LANCZOS = 6, OEM_PROF_LAMBDA = 7,
+  OEM_PROF_ITER = 8, OEM_PROF_CV = 9, OEM_PROF_COPY = 10, OEM_PROF_NKERNELS = 11
+};
+int oem_profile_enable(oem_ctx* ctx, int enable);
+int oem_profile_get(oem_ctx* ctx, int kernel, double* ms, int64_t* launches);
+const char* oem_profile_name(int kernel);
+
+/* Full-data sufficient statistics (Section 3: X^T X and X^T y).
+ * X: n x p (ldx), element type xtype; y: n (float64 if xtype == OEM_F64, else
+ * float32). Outputs RAW sums (not divided by n), float64, device:
+ * G: p x p row-major, full symmetric; c: p; yty: 1. mode: OEM_GRAM_*.
+ * n >= 1, p >= 1. */
+int oem_gram(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p,
+             int64_t ldx, const void* y, int32_t mode,
+             double* G, double* c, double* yty, void* stream);
+
+/* Per-fold raw sums in one pass (Section 3: X_k^T X_k, X_k^T y_k for every k).
+ * fold: n uint8 labels in [0, K). Outputs: Gk K x p x p, ck K x p, ytyk K,
+ * nk K (int64) -- all device. A fold with no rows gets zeros. 1 <= K <= 64. */
+int oem_fold_grams(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p,
+                   int64_t ldx, const void* y, const uint8_t* fold, int32_t K,
+                   int32_t mode, double* Gk, double* ck, double* ytyk, int64_t* nk,
+                   void* stream);
+
+/* d_b >= lambda_1(G_b) for b < batch (Section 2.1, computed by Lanczos).
+ * G_b = G + b*strideG, p x p float64 symmetric with leading dimension ldg.
+ * steps: Lanczos steps (<= 0: 64; capped at p). d: batch float64, device.
+ * d_b = theta + r, theta the largest Ritz value and r its residual norm;
+ * an all-zero G_b gives d_b = 1. */
+int oem_spectral_d(oem_ctx* ctx, const double* G, int64_t p, int64_t ldg,
+                   int32_t batch, int64_t strideG, int32_t steps, double* d,
+                   void* stream);
+
+/* Warm-started OEM paths from SCALED statistics (Section 5.6, oem.xtx):
+ * G = X^T X / n (p x p float64, device), c = X^T y / n (p float64, device).
+ * d > 0: use it; d <= 0: computed by Lanczos (opt->lanczos_steps).
+ * pens, npen (1..8), opt: host. Outputs (device): beta npen x nlambda x p
+ * float64; lambdas_out npen x nlambda float64; iters npen x nlambda int32;
+ * converged npen x nlambda uint8. Lambda grid per penalty (when
+ * opt->lambdas is NULL): lambda_max (the smallest lambda with beta = 0)
+ * down to lambda_min_ratio * lambda_max, log-spaced. */
+int oem_fit_path(oem_ctx* ctx, const double* G, const double* c, int64_t p, double d,
+                 const oem_penalty* pens, int32_t npen, const oem_options* opt,
+                 double* beta, double* lambdas_out, int32_t* iters,
+                 uint8_t* converged, void* stream);
+
+/* oem(): Gram pass over X (opt->gram_mode), d, lambda grid and paths, in one
+ * call (Section 5.1-5.2: several penalties from one Gram). Outputs as for
+ * oem_fit_path, plus d_out (1 float64, device, may be NULL). */
+int oem_fit(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p,
+            int64_t ldx, const void* y, const oem_penalty* pens, int32_t npen,
+            const oem_options* opt, double* beta, double* lambdas_out,
+            int32_t* iters, uint8_t* converged, double* d_out, void* stream);
+
+/* xval.oem(): K-fold cross validation by per-fold statistics (Section 3).
+ * One pass forms every fold's sums; leave-fold-out statistics by
+ * subtraction; d per Gram; the full-data lambda grid per penalty; paths for
+ * the full data and each of the K leave-fold-out fits (all in one batched
+ * launch); held-out MSE_k(lambda) = ||y_k - X_k beta_{-k}(lambda)||^2 / n_k.
+ * Outputs (device): beta_full npen x nlambda x p float64 (full-data paths);
+ * lambdas_out npen x nlambda; cvm, cvsd npen x nlambda (mean over folds and
+ * sample sd / sqrt(K)); idx_min, idx_1se npen int32 (lambda.min: argmin cvm,
+ * ties to the larger lambda; lambda.1se: largest lambda with
+ * cvm <= cvm_min + cvsd_min); best_penalty 1 int32 (lowest cvm at its
+ * lambda.min). 2 <= K <= 64; every fold must have >= 1 row (OEM_EINVAL after
+ * the fold count pass otherwise, reported by oem_sync). */
+int oem_cv(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p,
+           int64_t ldx, const void* y, const uint8_t* fold, int32_t K,
+           const oem_penalty* pens, int32_t npen, const oem_options* opt,
+           double* beta_full, double* lambdas_out, double* cvm, double* cvsd,
+           int32_t* idx_min, int32_t* idx_1se, int32_t* best_penalty, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OEM_GB300_H */

@@ -1,0 +1,169 @@
+// Internal declarations shared by the CUDA translation units of liboem.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/oem.h"
+
+namespace oem {
+
+constexpr int kNumSMsHint = 152;
+
+// Device-side status word bits (ctx->dstatus[0]); oem_sync() maps them to codes.
+enum : unsigned {
+  kStatNotConv = 1u,
+  kStatNonFinite = 2u,
+  kStatTimeout = 4u,
+  kStatEmptyFold = 8u,
+};
+
+// ----------------------------------------------------------------------------
+// Gram pass work decomposition. The augmented matrix Z = [X | y-columns] has q
+// columns; its upper triangle is cut into T x T tiles (ti <= tj). Rows are
+// processed in fold order (perm) as "chunks", each inside one fold. One work
+// item = (tile, chunk); it writes a T x T float64 partial sum. The reduction
+// adds the partials of each fold's chunks in a fixed order (deterministic).
+// ----------------------------------------------------------------------------
+struct ChunkTable {
+  int64_t* row0;     // [max_chunks] first sorted row of the chunk
+  int64_t* row1;     // [max_chunks] one past the last sorted row
+  int32_t* fold;     // [max_chunks] fold of the chunk
+  int32_t* count;    // [1] number of valid chunks
+  int32_t* fold_c0;  // [K+1] first chunk of each fold (prefix)
+  int64_t* fold_off; // [K+1] row offsets of each fold in sorted order
+};
+
+struct GramArgs {
+  const void* X;
+  int32_t xtype;
+  int64_t n, p, ldx;
+  const void* y;
+  const int32_t* perm;  // sorted row -> original row (NULL = identity)
+  int32_t mode;         // OEM_GRAM_*
+  int32_t q;            // augmented columns
+  int32_t ycols;        // y columns appended (1 or 2)
+  int32_t T;            // tile size
+  int32_t ntile1;       // tiles per side
+  int32_t ntiles;       // upper-triangular tile count
+  ChunkTable ct;
+  int32_t max_chunks;
+  double* partial;      // [max_chunks][ntiles][T][T]
+  unsigned* dstatus;
+};
+
+// tile index -> (ti, tj), ti <= tj, row-major over the upper triangle
+__host__ __device__ inline void tile_coords(int t, int nt, int* ti, int* tj) {
+  int i = 0, rem = t;
+  while (rem >= nt - i) { rem -= nt - i; ++i; }
+  *ti = i;
+  *tj = i + rem;
+}
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_fold_count(const uint8_t* fold, int64_t n, int K, int32_t* blk_counts,
+                              int64_t nblk, cudaStream_t s);
+cudaError_t launch_fold_scan(const int32_t* blk_counts, int64_t nblk, int K, int64_t chunk_rows,
+                             int32_t* blk_offsets, ChunkTable ct, int max_chunks,
+                             unsigned* dstatus, int require_nonempty, cudaStream_t s);
+cudaError_t launch_fold_scatter(const uint8_t* fold, int64_t n, int K, const int32_t* blk_offsets,
+                                int32_t* perm, cudaStream_t s);
+cudaError_t launch_identity_chunks(int64_t n, int64_t chunk_rows, ChunkTable ct, int max_chunks,
+                                   cudaStream_t s);
+
+cudaError_t launch_gram_simt(const GramArgs& a, cudaStream_t s);
+cudaError_t launch_gram_tc(const GramArgs& a, int flush_rows, cudaStream_t s);
+cudaError_t launch_check_finite(const void* X, int32_t xtype, int64_t n, int64_t p, int64_t ldx,
+                                const void* y, unsigned* dstatus, cudaStream_t s);
+
+// Reduce partials into per-fold raw Grams of Z (float64, full symmetric,
+// [K][q][q]).
+cudaError_t launch_gram_reduce(const GramArgs& a, int K, double* Zg, cudaStream_t s);
+
+// Extract per-fold X^T X, X^T y, y^T y from Z Grams (raw) in the public layout.
+cudaError_t launch_extract_folds(const double* Zg, int K, int q, int p, int ycols, double* Gk,
+                                 double* ck, double* ytyk, int64_t* nk, const int64_t* fold_off,
+                                 cudaStream_t s);
+
+// Assemble scaled statistics: b = 0 full data, b = k+1 leave fold k out.
+// G64 [B][p][p], G32 [B][p][ldg32] (may be NULL), c [B][p], N [B], cnt [B].
+cudaError_t launch_assemble(const double* Zg, int K, int q, int p, int ycols,
+                            const int64_t* fold_off, int with_leave_out, double* G64, float* G32,
+                            int ldg32, double* c, double* N, double* cnt, cudaStream_t s);
+
+// Lanczos d for a batch of float64 Grams.
+struct LanczosWork {
+  double* V;       // [batch][3][p] rolling vectors
+  double* alpha;   // [batch][steps]
+  double* beta;    // [batch][steps]
+  double* fro;     // [batch]
+  int32_t* mlen;   // [batch] steps taken
+};
+cudaError_t launch_lanczos(const double* G, int64_t p, int64_t ldg, int batch, int64_t strideG,
+                           int steps, LanczosWork w, double* d, cudaStream_t s, int64_t* launches);
+
+// Penalty descriptor on the device.
+struct DevPenalty {
+  int32_t kind;
+  float alpha, gamma;
+  double alpha64, gamma64;
+  const float* w32;     // [p] or NULL
+  const double* w64;    // [p] or NULL
+  const int32_t* grp;   // [p] group ids (group lasso) or NULL
+  const double* cg;     // [ngroups]
+  int32_t ngroups;
+};
+
+// Lambda grid: lam[pen][l] from c (full data).
+cudaError_t launch_lambda_grid(const double* c, int p, const DevPenalty* pens, int npen,
+                               int nlambda, double ratio, double* lam, cudaStream_t s);
+
+// OEM iteration over all (Gram b, penalty i) instances.
+struct IterArgs {
+  int32_t p;
+  int32_t B;             // Grams
+  int32_t npen;          // instances per Gram
+  int32_t nlambda;
+  const float* G32;      // [B][p][ldg]
+  const double* G64;     // [B][p][p]  (float64 iteration)
+  int32_t ldg;
+  const double* c;       // [B][p]
+  const double* d;       // [B]
+  const double* lam;     // [npen][nlambda]
+  const DevPenalty* pens;// [npen]
+  double tol;
+  int64_t max_iter;
+  double* beta;          // [B][npen][nlambda][p]
+  int32_t* iters;        // [B][npen][nlambda]
+  uint8_t* conv;         // [B][npen][nlambda]
+  unsigned* dstatus;
+  // row slices: CTA r of a cluster owns rows [slice[r], slice[r+1])
+  const int32_t* slice;  // [C+1]
+  int32_t C;
+  int32_t max_rows;      // max slice length
+  int32_t smem_rows;     // leading rows of each slice kept in shared memory
+  int32_t precision;     // OEM_ITER_F32 / OEM_ITER_F64
+};
+// Instances per Gram are padded to M in {1, 2, 4, 8}.
+int oem_iter_mpad(int npen);
+// Shared memory needed besides the resident Gram rows, and per resident row.
+size_t oem_iter_smem_fixed(int p, int npen, int max_rows, int C, int precision);
+size_t oem_iter_smem_per_row(int p, int precision);
+// Largest cluster size the device can co-schedule for this configuration (0 if none).
+int oem_iter_max_cluster(const IterArgs& a, size_t smem, int C);
+cudaError_t launch_oem_iter(const IterArgs& a, size_t smem, cudaStream_t s);
+
+// CV scoring from raw fold Grams of Z and the fold paths.
+cudaError_t launch_cv_score(const double* Zg, int K, int q, int p, int ycols,
+                            const int64_t* fold_off, const double* beta_all, int npen,
+                            int nlambda, double* mse, double* cvm, double* cvsd,
+                            int32_t* idx_min, int32_t* idx_1se, int32_t* best, cudaStream_t s);
+
+// Copy the full-data (b = 0) paths out of the batched buffers.
+cudaError_t launch_copy_paths(const double* beta_all, const int32_t* it_all, const uint8_t* cv_all,
+                              int npen, int nlambda, int p, double* beta, int32_t* iters,
+                              uint8_t* conv, unsigned* dstatus, cudaStream_t s);
+
+}  // namespace oem

@@ -1,0 +1,98 @@
+"""GPU parity of the tcgen05 Gram pass against the FP64 oracle.
+
+Tolerances (relative Frobenius error of X^T X, and relative error of X^T y
+and y^T y):
+  * SPLIT_BF16 (float32 X, hi/lo bfloat16 products, float32 accumulation in
+    tensor memory, compensated across 256-row windows): 1e-6;
+  * BF16 (bfloat16 X: exact products; float32 y split into two columns): 1e-6;
+  * TF32 (float32 X rounded to tf32): 5e-4 (reported mode; its operand
+    rounding alone is 2^-11 per element).
+Sizes span one to three 128-column tiles with ragged tails and rows that are
+not a multiple of the 32-row stage.
+"""
+import numpy as np
+import pytest
+
+import synthgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"split_bf16": 1e-6, "bf16": 1e-6, "tf32": 5e-4}
+
+
+@pytest.fixture(scope="module")
+def oem():
+    import paper_1801_09661_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(oem):
+    c = oem.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _xdev(X):
+    from paper_1801_09661_gb300 import padded
+    if X.dtype == np.uint16:
+        return padded(torch.from_numpy(X.view(np.int16)).view(torch.bfloat16))
+    return padded(X)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _data(n, p, seed, mode):
+    dt = "bf16" if mode == "bf16" else np.float32
+    X = synthgen.ar1_design(n, p, 0.5, seed, dt)
+    y = synthgen.response(X, synthgen.leading_beta(p, [1.0, -0.5, 0.25]), 1.0, seed, np.float32)
+    return X, y
+
+
+@pytest.mark.parametrize("mode", ["split_bf16", "bf16", "tf32"])
+@pytest.mark.parametrize("n,p", [(5003, 70), (777, 130), (20011, 300), (1, 3), (4096, 127)])
+def test_tc_gram_matches_oracle(oem, ctx, mode, n, p):
+    X, y = _data(n, p, 31 + p, mode)
+    G, c, yty = oem.oem_gram(ctx, _xdev(X), _dev(y), mode=mode)
+    assert ctx.sync() == 0
+    Gr, cr, Nr, _ = oracle.gram_sums(synthgen.as_f64(X), y)
+    eg = _rel(G.cpu().numpy(), Gr)
+    ec = _rel(c.cpu().numpy(), cr)
+    en = abs(float(yty.cpu()[0]) - Nr) / Nr
+    print(f"{mode} n={n} p={p}: G {eg:.2e} c {ec:.2e} yty {en:.2e}")
+    assert eg <= TOL[mode] and ec <= TOL[mode] and en <= TOL[mode]
+
+
+@pytest.mark.parametrize("mode", ["split_bf16", "bf16"])
+def test_tc_fold_grams_gathered_rows(oem, ctx, mode):
+    n, p, K = 30011, 150, 7
+    X, y = _data(n, p, 5, mode)
+    fold = synthgen.fold_ids(n, K, 5)
+    Gk, ck, ytyk, nk = oem.oem_fold_grams(ctx, _xdev(X), _dev(y), _dev(fold), K, mode=mode)
+    assert ctx.sync() == 0
+    Gr, cr, Nr, nr = oracle.fold_gram_sums(synthgen.as_f64(X), y, fold, K)
+    assert np.array_equal(nk.cpu().numpy(), nr)
+    for k in range(K):
+        assert _rel(Gk[k].cpu().numpy(), Gr[k]) <= TOL[mode]
+        assert _rel(ck[k].cpu().numpy(), cr[k]) <= TOL[mode]
+
+
+def test_split_gram_precision_at_large_n(oem, ctx):
+    """Error growth over many flush windows: n = 2,000,000 rows, p = 100."""
+    n, p = 2_000_000, 100
+    X, y = _data(n, p, 9, "split_bf16")
+    G, c, yty = oem.oem_gram(ctx, _xdev(X), _dev(y), mode="split_bf16")
+    assert ctx.sync() == 0
+    Gr, cr, Nr, _ = oracle.gram_sums(X, y)
+    eg = _rel(G.cpu().numpy(), Gr)
+    print(f"split_bf16 n={n} p={p}: G rel Frobenius {eg:.3e}")
+    assert eg <= 1e-6
