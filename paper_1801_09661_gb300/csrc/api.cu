@@ -265,9 +265,11 @@ int run_gram(oem_ctx* ctx, const GramPlan& g, GramBufs& b, const void* X, int32_
   if (tc_mode(g.mode)) {
     // Rows summed in float32 tensor memory before the compensated flush. The
     // tensor cores' float32 accumulation rounds toward zero, so the error
-    // grows with the number of MMAs per window: split mode (4 products) uses
-    // 64-row windows, bfloat16 / tf32 256 / 128. OEM_GRAM_FLUSH_ROWS overrides.
-    int flush = g.mode == OEM_GRAM_SPLIT_BF16 ? 64 : g.mode == OEM_GRAM_TF32 ? 128 : 256;
+    // grows with the number of MMAs per window (measured at n = 2e6, p = 100,
+    // split mode: 32 rows 3.2e-7, 64 rows 5.2e-7, 256 rows 1.6e-6 relative
+    // Frobenius): split mode (4 products) uses 32-row windows, bfloat16 / tf32
+    // 256 / 128. OEM_GRAM_FLUSH_ROWS overrides.
+    int flush = g.mode == OEM_GRAM_SPLIT_BF16 ? 32 : g.mode == OEM_GRAM_TF32 ? 128 : 256;
     if (const char* ev = getenv("OEM_GRAM_FLUSH_ROWS")) {
       const int v = atoi(ev);
       if (v >= 32 && v <= 65536) flush = v;
