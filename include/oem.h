@@ -156,6 +156,28 @@ int oem_gram(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p,
              int64_t ldx, const void* y, int32_t mode,
              double* G, double* c, double* yty, void* stream);
 
+/* oem_gram without any device allocation. The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when
+ * they call -- code running under a framework that owns the whole device
+ * memory pool, loops that must not allocate once they have started, or a
+ * caller with no oem_ctx at all (this call needs none). It computes what
+ * oem_gram computes (same arguments and outputs, same kernels; the caller
+ * still passes X, y and the outputs G, c, yty) with all working memory in one
+ * 48 MiB array that the library declares in device memory at file scope;
+ * every GPU that loads the library holds that array until the process exits.
+ * Limits: p <= 1024 (OEM_EBUDGET beyond it, or when the rows need more tile
+ * partials than the array holds); n <= 2^31 - 1.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call shares the one array and leaves its contents behind: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and must
+ * not be issued. Non-finite values in X or y are not reported (they show up
+ * in G, c, yty). Returns OEM_OK, OEM_EINVAL, OEM_EBUDGET or OEM_ECUDA; work is
+ * enqueued on `stream` and the call does not wait. */
+int oem_gram_noalloc(const void* X, int32_t xtype, int64_t n, int64_t p, int64_t ldx,
+                     const void* y, int32_t mode, double* G, double* c, double* yty,
+                     void* stream);
+
 /* Per-fold raw sums in one pass (Section 3: X_k^T X_k, X_k^T y_k for every k).
  * fold: n uint8 labels in [0, K). Outputs: Gk K x p x p, ck K x p, ytyk K,
  * nk K (int64) -- all device. A fold with no rows gets zeros. 1 <= K <= 64. */

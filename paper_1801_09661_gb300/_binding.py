@@ -41,7 +41,8 @@ MODE = {"fp64": OEM_GRAM_FP64, "fp32": OEM_GRAM_FP32, "tf32": OEM_GRAM_TF32,
 
 EXPORTED = ["oem_options_default", "oem_create", "oem_destroy", "oem_last_error", "oem_sync",
             "oem_kernel_launches", "oem_profile_enable", "oem_profile_get", "oem_profile_name",
-            "oem_gram", "oem_fold_grams", "oem_spectral_d", "oem_fit_path", "oem_fit", "oem_cv"]
+            "oem_gram", "oem_gram_noalloc", "oem_fold_grams", "oem_spectral_d", "oem_fit_path",
+            "oem_fit", "oem_cv"]
 OEM_PROF_NKERNELS = 11
 
 
@@ -71,6 +72,7 @@ _sigs = {
     "oem_profile_get": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "oem_profile_name": (C.c_char_p, [C.c_int]),
     "oem_gram": (C.c_int, [_vp, _vp, _i32, _i64, _i64, _i64, _vp, _i32, _vp, _vp, _vp, _vp]),
+    "oem_gram_noalloc": (C.c_int, [_vp, _i32, _i64, _i64, _i64, _vp, _i32, _vp, _vp, _vp, _vp]),
     "oem_fold_grams": (C.c_int, [_vp, _vp, _i32, _i64, _i64, _i64, _vp, _vp, _i32, _i32,
                                  _vp, _vp, _vp, _vp, _vp]),
     "oem_spectral_d": (C.c_int, [_vp, _vp, _i64, _i64, _i32, _i64, _i32, _vp, _vp]),
@@ -250,6 +252,22 @@ def oem_gram(ctx: Context, X, y, mode="auto", G=None, c=None, yty=None, stream=N
     ctx.check(lib.oem_gram(ctx.h, _ptr(X), _xtype(X), n, p, X.stride(0), _ptr(y),
                            MODE[mode] if isinstance(mode, str) else int(mode),
                            _ptr(G), _ptr(c), _ptr(yty), _stream(stream)))
+    return G, c, yty
+
+
+def oem_gram_noalloc(X, y, mode="auto", G=None, c=None, yty=None, stream=None):
+    """oem_gram without device allocation or context (see include/oem.h)."""
+    import torch
+    n, p = X.shape
+    dev = X.device
+    G = torch.empty((p, p), dtype=torch.float64, device=dev) if G is None else G
+    c = torch.empty(p, dtype=torch.float64, device=dev) if c is None else c
+    yty = torch.empty(1, dtype=torch.float64, device=dev) if yty is None else yty
+    rc = lib.oem_gram_noalloc(_ptr(X), _xtype(X), n, p, X.stride(0), _ptr(y),
+                              MODE[mode] if isinstance(mode, str) else int(mode),
+                              _ptr(G), _ptr(c), _ptr(yty), _stream(stream))
+    if rc < 0:
+        raise OemError(rc, "oem_gram_noalloc rejected the call")
     return G, c, yty
 
 

@@ -63,6 +63,20 @@ def test_argument_errors_return_before_launch(lib_path):
                           None) == oem.OEM_EINVAL
 
 
+def test_noalloc_rejects_sizes_beyond_its_maximum(lib_path):
+    """oem_gram_noalloc refuses p > 1024 (OEM_EBUDGET) and bad strides
+    (OEM_EINVAL) on the host, before touching the device."""
+    import paper_1801_09661_gb300 as oem
+    L = oem.lib
+    fake = 4096  # aligned, never dereferenced on these paths
+    assert L.oem_gram_noalloc(fake, oem.OEM_F32, 1000, 2000, 2000, fake, oem.OEM_GRAM_FP32,
+                              fake, fake, fake, None) == oem.OEM_EBUDGET
+    assert L.oem_gram_noalloc(fake, oem.OEM_F32, 1000, 10, 10, fake, oem.OEM_GRAM_FP32,
+                              fake, fake, fake, None) == oem.OEM_EINVAL
+    assert L.oem_gram_noalloc(fake, oem.OEM_F64, 1000, 10, 10, fake, oem.OEM_GRAM_FP32,
+                              fake, fake, fake, None) == oem.OEM_EINVAL
+
+
 def _imports(path):
     tree = ast.parse(open(path).read())
     mods = set()
