@@ -234,6 +234,80 @@ int oem_cv(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p,
            double* beta_full, double* lambdas_out, double* cvm, double* cvsd,
            int32_t* idx_min, int32_t* idx_1se, int32_t* best_penalty, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Serving: a request loop that admits fit and cross-validation jobs of mixed
+ * n and p as they arrive, under a device-memory budget, and runs them with
+ * continuous batching (the paper's OEM path per job, Sections 2-3; the
+ * request loop itself has no counterpart in the paper).
+ *
+ * OEM_SERVE_BATCHED: each admitted job's Gram pass (split-bfloat16 tensor
+ * cores), d and lambda grid run on the job's own stream, overlapping
+ * whatever else is on the GPU; the job's Grams, d and path state stay
+ * resident; the OEM iterations of every job whose Grams are ready run
+ * together in rounds of one cluster launch (a bounded number of iterations
+ * per round, state saved between rounds), so jobs join and leave the batch
+ * as they become ready and finish.
+ * OEM_SERVE_PLAIN: jobs one at a time in arrival order, float32 CUDA-core
+ * Gram, and one kernel launch plus a host convergence check per OEM
+ * iteration (the plain per-job GPU form, for comparison; lasso, elastic net,
+ * MCP and SCAD only).
+ * A job is DONE when its results are in host memory. Results of a job do not
+ * depend on the other jobs in the batch.
+ * ---------------------------------------------------------------------- */
+typedef struct oem_server oem_server;
+
+enum { OEM_SERVE_BATCHED = 0, OEM_SERVE_PLAIN = 1 };
+enum { OEM_JOB_QUEUED = 0, OEM_JOB_PREP = 1, OEM_JOB_ITER = 2, OEM_JOB_FINISH = 3,
+       OEM_JOB_DONE = 4, OEM_JOB_FAILED = 5 };
+
+/* One request: a fit (K = 0) or a K-fold cross validation (2 <= K <= 64) of
+ * one penalty. X (n x p, ldx), y and fold are DEVICE pointers that must stay
+ * valid and unchanged until the job is DONE. gram_mode as in oem_options
+ * (ignored by the plain form, which uses OEM_GRAM_FP32). */
+typedef struct oem_job {
+  const void* X;
+  int32_t xtype;
+  int64_t n, p, ldx;
+  const void* y;
+  const uint8_t* fold;
+  int32_t K;
+  oem_penalty pen;
+  int32_t nlambda;
+  double lambda_min_ratio;
+  double tol;
+  int64_t max_iter;
+  int32_t gram_mode;
+} oem_job;
+
+/* Start a server on `device` with a device-memory budget for job data
+ * (0 = 8 GiB), a form (OEM_SERVE_*) and the OEM iterations per batched
+ * round (<= 0: 2000). A worker thread runs the loop until oem_server_destroy. */
+int oem_server_create(oem_server** srv, int device, size_t mem_budget_bytes, int32_t form,
+                      int64_t iters_per_round);
+
+/* Queue a job; returns at once with its id. OEM_EINVAL for a bad job,
+ * OEM_EBUDGET for a job that can never fit in the budget. */
+int oem_server_submit(oem_server* srv, const oem_job* job, int64_t* id);
+
+/* State (OEM_JOB_*) of a job and, once DONE, its latency from submission to
+ * results in host memory, in milliseconds (may be NULL). */
+int oem_server_poll(oem_server* srv, int64_t id, int32_t* state, double* latency_ms);
+
+/* Results of a DONE job, copied to HOST arrays (each may be NULL): beta
+ * nlambda x p (full-data path), lambdas nlambda; for CV jobs cvm and cvsd
+ * (nlambda) and idx_min, idx_1se; iters = OEM iterations over all of the
+ * job's paths. OEM_EINVAL if the job is not DONE. */
+int oem_server_result(oem_server* srv, int64_t id, double* beta, double* lambdas, double* cvm,
+                      double* cvsd, int32_t* idx_min, int32_t* idx_1se, int64_t* iters);
+
+/* Server counters: jobs done, paths done (a CV job counts K+1 paths), kernel
+ * launches, batched rounds, peak device bytes in use. */
+int oem_server_stats(oem_server* srv, int64_t* jobs_done, int64_t* paths_done, int64_t* launches,
+                     int64_t* rounds, int64_t* peak_bytes);
+
+/* Finish every queued and running job, stop the worker and free the server. */
+int oem_server_destroy(oem_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

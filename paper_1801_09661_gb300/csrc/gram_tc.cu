@@ -4,17 +4,20 @@
 //
 // One CTA per SM (persistent). A work item is a 128 x 128 tile (ti <= tj) of
 // the upper triangle over a chunk of fold-sorted rows. Roles per CTA:
-//   * 8 converter warps load 32-row stages of columns [128 ti, +128) and
-//     [128 tj, +128) (rows gathered through the fold permutation), convert
-//     them (float32 -> hi/lo bfloat16 split, bfloat16 copy, or float32 ->
-//     tf32) and store them in shared memory in the MN-major, 128-byte-swizzled
-//     layout the tensor core reads;
+//   * 8 converter warps stream 32-row stages of columns [128 ti, +128) and
+//     [128 tj, +128) (rows gathered through the fold permutation) into a raw
+//     shared-memory ring with cp.async, two stages ahead of the one they
+//     convert; each thread then converts the bytes it loaded (float32 -> hi/lo
+//     bfloat16 split, bfloat16 copy, or float32 -> tf32) into the operand
+//     stage in the layout the tensor core reads (MN-major 128-byte swizzle for
+//     bfloat16, K-major for tf32);
 //   * 1 warp allocates tensor memory and one elected thread issues
 //     tcgen05.mma (M = N = 128, float32 accumulation in tensor memory) for
 //     each stage, double-buffering the accumulator per flush window;
-//   * 4 epilogue warps (one per 32 tensor-memory lanes) add each finished
-//     window into a compensated (hi, lo) float32 pair kept in tensor memory
-//     (TwoSum), and write hi + lo as float64 at the end of the item.
+//   * 8 epilogue warps (two per 32 tensor-memory lanes, 64 columns each) add
+//     each finished window into a compensated (hi, lo) float32 pair kept in
+//     tensor memory (TwoSum), and write hi + lo as float64 at the end of the
+//     item.
 // Every mbarrier wait is bounded by a clock budget; on expiry the kernel
 // records a timeout in the status word, drains its MMAs, frees tensor memory
 // and returns.
@@ -28,14 +31,16 @@ namespace tc {
 
 constexpr int kTile = 128;
 constexpr int kKS = 32;           // rows per stage
-constexpr int kNS = 4;            // pipeline stages
+constexpr int kNS = 4;            // operand stages
 constexpr int kStageBytes = 32768;
-constexpr int kGuardBytes = 32768;  // unused slack after the stages: every descriptor
-                                    // reading stays inside the allocation
-constexpr int kConvWarps = 8;
-constexpr int kEpiWarps = 4;
-constexpr int kMmaWarp = 4;
-constexpr int kThreads = (kEpiWarps + 1 + kConvWarps) * 32;  // 416
+constexpr int kRawSlots = 3;      // raw ring: the stage being converted + 2 in flight
+constexpr int kPrefetch = kRawSlots - 1;
+constexpr int kRawBytes = 32768;
+constexpr int kEpiWarps = 8;      // warps 0..7
+constexpr int kMmaWarp = 8;
+constexpr int kConvWarps = 8;     // warps 9..16
+constexpr int kConvBase = (kEpiWarps + 1) * 32;
+constexpr int kThreads = (kEpiWarps + 1 + kConvWarps) * 32;  // 544
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 struct Bars {
@@ -126,11 +131,38 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
       OEM_W16(r)
       : "memory");
 }
+// (hi, lo) += x for two elements at once (packed float32x2): TwoSum gives
+// s + e = hi + x exactly; s becomes hi and e is added to lo.
+__device__ __forceinline__ void two_sum_x2(uint32_t& h0, uint32_t& h1, uint32_t& l0, uint32_t& l1,
+                                           uint32_t x0, uint32_t x1) {
+  asm("{\n\t.reg .b64 h, x, s, bb, t, e1, e2, l;\n\t"
+      "mov.b64 h, {%0, %1};\n\t"
+      "mov.b64 l, {%2, %3};\n\t"
+      "mov.b64 x, {%4, %5};\n\t"
+      "add.rn.f32x2 s, h, x;\n\t"
+      "sub.rn.f32x2 bb, s, h;\n\t"
+      "sub.rn.f32x2 t, s, bb;\n\t"
+      "sub.rn.f32x2 e1, h, t;\n\t"
+      "sub.rn.f32x2 e2, x, bb;\n\t"
+      "add.rn.f32x2 e1, e1, e2;\n\t"
+      "add.rn.f32x2 l, l, e1;\n\t"
+      "mov.b64 {%0, %1}, s;\n\t"
+      "mov.b64 {%2, %3}, l;\n\t}"
+      : "+r"(h0), "+r"(h1), "+r"(l0), "+r"(l1)
+      : "r"(x0), "r"(x1));
+}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: start, leading (MN-atom) and stride
-// (8-row K group) byte offsets, fixed version bit, 128-byte swizzle.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Shared-memory matrix descriptor: start, leading and stride byte offsets,
+// fixed version bit, 128-byte swizzle.
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
@@ -177,32 +209,35 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 __device__ __forceinline__ float bf16_round(float a) {
   return __bfloat162float(__float2bfloat16_rn(a));
 }
+// Two float32 values rounded to bfloat16 (nearest even) in one instruction;
+// the first argument lands in the low half.
+__device__ __forceinline__ uint32_t cvt_bf16x2(float lo_elem, float hi_elem) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi_elem), "f"(lo_elem));
+  return r;
+}
+// hi = bf16(v), lo = bf16(v - hi) for 8 values, packed in pairs.
+__device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    h[i] = cvt_bf16x2(v[2 * i], v[2 * i + 1]);
+    const float h0 = __uint_as_float(h[i] << 16), h1 = __uint_as_float(h[i] & 0xFFFF0000u);
+    l[i] = cvt_bf16x2(v[2 * i] - h0, v[2 * i + 1] - h1);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
 __device__ __forceinline__ uint32_t to_tf32(float a) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(a));
   return r;
 }
 
-// Values of Z at 8 consecutive columns [c0, c0+8) of original row `row`.
+// Values of Z at 8 consecutive columns [c0, c0+8) of original row `row`
+// (direct loads; used for the columns that hold y or run past p).
 __device__ __forceinline__ void load8(const GramArgs& a, int64_t row, int c0, float (&v)[8]) {
   const int p = (int)a.p;
-  if (c0 + 8 <= p) {
-    if (a.xtype == OEM_F32) {
-      const float4* s = reinterpret_cast<const float4*>((const float*)a.X + row * a.ldx + c0);
-      const float4 u0 = __ldg(s), u1 = __ldg(s + 1);
-      v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
-      v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
-    } else {
-      const uint4 u = __ldg(reinterpret_cast<const uint4*>((const __nv_bfloat16*)a.X + row * a.ldx + c0));
-      const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        v[2 * i] = __uint_as_float(w[i] << 16);
-        v[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
-      }
-    }
-    return;
-  }
   // y columns: one (split mode) or three bfloat16 pieces hi + mid + lo that
   // hold a float32 y exactly (bfloat16 mode)
   const float yv = ((const float*)a.y)[row];
@@ -226,11 +261,50 @@ __device__ __forceinline__ void load8(const GramArgs& a, int64_t row, int c0, fl
   }
 }
 
+// The CTA's sequence of (item, stage) pairs, shared by the converter's load
+// and convert cursors.
+struct StageCursor {
+  int item, st, nst, chunk, ti, tj;
+  int64_t r0, r1;
+  bool valid;
+  __device__ void set_item(const GramArgs& a, int it, int nitems) {
+    item = it;
+    valid = it < nitems;
+    if (!valid) return;
+    chunk = it / a.ntiles;
+    const int tile = it % a.ntiles;
+    tile_coords(tile, a.ntile1, &ti, &tj);
+    r0 = a.ct.row0[chunk];
+    r1 = a.ct.row1[chunk];
+    nst = (int)((r1 - r0 + kKS - 1) / kKS);
+    st = 0;
+    if (nst == 0) valid = false;
+  }
+  __device__ void next(const GramArgs& a, int nitems) {
+    if (!valid) return;
+    if (++st >= nst) set_item(a, item + gridDim.x, nitems);
+  }
+};
+
+// Converter items of one stage (non-tf32): (panel, row, 8-column group),
+// group fastest; 512 per panel. A thread owns items ct, ct + 256, ...
+__device__ __forceinline__ bool item_async(const GramArgs& a, const StageCursor& c, int e,
+                                           int64_t* row_out, int* col_out) {
+  const int g = e & 15, r = (e >> 4) & (kKS - 1), pan = e >> 9;
+  const int64_t sr = c.r0 + (int64_t)c.st * kKS + r;
+  const int col = (pan == 0 ? c.ti : c.tj) * kTile + g * 8;
+  *col_out = col;
+  if (sr >= c.r1) { *row_out = -1; return false; }
+  *row_out = a.perm ? (int64_t)a.perm[sr] : sr;
+  return col + 8 <= a.p;
+}
+
 __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a, int flush_stages) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment of the operand stages (swizzle atoms)
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  Bars* bars = reinterpret_cast<Bars*>(smem + kNS * kStageBytes + kGuardBytes);
+  unsigned char* raw = smem + kNS * kStageBytes;
+  Bars* bars = reinterpret_cast<Bars*>(raw + kRawSlots * kRawBytes);
   volatile int* abort_flag = &bars->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mode = a.mode;
@@ -329,7 +403,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a, int fl
     __syncwarp();
   } else if (warp < kEpiWarps) {
     // ------------------------------------------------------------ epilogue
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    // warp w reads lanes 32 (w % 4) .. +31 and columns [64 (w / 4), +64)
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    const int c0 = (warp >> 2) * 64;
     uint32_t v = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
@@ -344,7 +420,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a, int fl
         const uint32_t acc = tmem + lane_base + (uint32_t)(buf * kTile);
         const uint32_t thi = tmem + lane_base + 256u, tlo = tmem + lane_base + 384u;
 #pragma unroll 1
-        for (int cb = 0; cb < kTile; cb += 16) {
+        for (int cb = c0; cb < c0 + 64; cb += 16) {
           uint32_t ra[16], rh[16], rl[16];
           tmem_ld16(acc + cb, ra);
           if (!first) { tmem_ld16(thi + cb, rh); tmem_ld16(tlo + cb, rl); }
@@ -354,15 +430,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a, int fl
             for (int i = 0; i < 16; ++i) { rh[i] = ra[i]; rl[i] = 0u; }
           } else {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const float h = __uint_as_float(rh[i]), x = __uint_as_float(ra[i]);
-              const float s = h + x, bb = s - h;
-              const float e = (h - (s - bb)) + (x - bb);
-              const float lo = __uint_as_float(rl[i]) + e;
-              const float t = s + lo;
-              rl[i] = __float_as_uint(lo - (t - s));
-              rh[i] = __float_as_uint(t);
-            }
+            for (int i = 0; i < 16; i += 2) two_sum_x2(rh[i], rh[i + 1], rl[i], rl[i + 1], ra[i], ra[i + 1]);
           }
           tmem_st16(thi + cb, rh);
           tmem_st16(tlo + cb, rl);
@@ -374,12 +442,12 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a, int fl
         first = false;
       }
       if (!ok) break;
-      // item done: hi + lo as float64 (row 32 * warp + lane of the tile)
+      // item done: hi + lo as float64 (row 32 (w % 4) + lane of the tile)
       double* out = a.partial + ((int64_t)chunk * a.ntiles + tile) * (kTile * kTile) +
-                    (int64_t)(warp * 32 + lane) * kTile;
+                    (int64_t)((warp & 3) * 32 + lane) * kTile;
       const uint32_t thi = tmem + lane_base + 256u, tlo = tmem + lane_base + 384u;
 #pragma unroll 1
-      for (int cb = 0; cb < kTile; cb += 16) {
+      for (int cb = c0; cb < c0 + 64; cb += 16) {
         uint32_t rh[16], rl[16];
         if (nst > 0) {
           tmem_ld16(thi + cb, rh);
@@ -402,71 +470,120 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a, int fl
     if (!ok) { bars->abort = 1; atomicOr(a.dstatus, kStatTimeout); }
   } else {
     // ------------------------------------------------------------ converters
-    const int ct = threadIdx.x - (kEpiWarps + 1) * 32;  // 0..255
-    uint32_t u = 0;
-    bool ok = true;
-    for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-      const int chunk = item / a.ntiles, tile = item % a.ntiles;
-      int ti, tj;
-      tile_coords(tile, a.ntile1, &ti, &tj);
-      const bool diag = ti == tj;
-      const int npan = diag ? 1 : 2;
-      const int64_t r0 = a.ct.row0[chunk], r1 = a.ct.row1[chunk];
-      const int nst = (int)((r1 - r0 + kKS - 1) / kKS);
-      for (int st = 0; st < nst; ++st, ++u) {
-        const int s = u % kNS;
-        if (!mbar_wait(su32(&bars->empty[s]), ((u / kNS) & 1) ^ 1, abort_flag)) { ok = false; break; }
-        unsigned char* base = smem + s * kStageBytes;
-        const int64_t rb = r0 + (int64_t)st * kKS;
-        if (tf32) {
-          // items: (panel, 4-row quad, column); one 16-byte chunk each
-          for (int e = ct; e < npan * (kKS / 4) * kTile; e += kConvWarps * 32) {
-            const int mn = e & (kTile - 1), kq = (e >> 7) & (kKS / 4 - 1), pan = e >> 10;
-            const int col = (pan == 0 ? ti : tj) * kTile + mn;
-            uint32_t w4[4];
+    const int ct = threadIdx.x - kConvBase;  // 0..255
+    const bool f32 = a.xtype == OEM_F32;
+    StageCursor ld, cv;
+    ld.set_item(a, blockIdx.x, nitems);
+    cv.set_item(a, blockIdx.x, nitems);
+    // issue the raw loads of one stage into raw slot `slot` (non-tf32 modes)
+    auto issue = [&](const StageCursor& c, int slot) {
+      if (!c.valid || tf32) return;
+      const int npan = (c.ti == c.tj) ? 1 : 2;
+      const uint32_t rbase = su32(raw + slot * kRawBytes);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const int64_t sr = rb + kq * 4 + i;
-              float x = 0.f;
-              if (sr < r1) x = zval_f32(a, a.perm ? (int64_t)a.perm[sr] : sr, col);
-              w4[i] = to_tf32(x);
-            }
-            *reinterpret_cast<uint4*>(base + pan * 16384 + off_kmaj_f32(mn, kq)) =
-                make_uint4(w4[0], w4[1], w4[2], w4[3]);
+      for (int j = 0; j < 4; ++j) {
+        const int e = ct + j * (kConvWarps * 32);
+        if (e >= npan * kKS * 16) break;
+        int64_t row;
+        int col;
+        if (item_async(a, c, e, &row, &col)) {
+          if (f32) {
+            const float* src = (const float*)a.X + row * a.ldx + col;
+            cp_async16(rbase + e * 32, src);
+            cp_async16(rbase + e * 32 + 16, src + 4);
+          } else {
+            cp_async16(rbase + e * 16, (const __nv_bfloat16*)a.X + row * a.ldx + col);
           }
         }
-        // items: (panel, row, 8-column group), group fastest
-        for (int e = ct; !tf32 && e < npan * kKS * 16; e += kConvWarps * 32) {
-          const int g = e & 15, r = (e >> 4) & (kKS - 1), pan = e >> 9;
-          const int64_t sr = rb + r;
+      }
+    };
+    for (int d = 0; d < kPrefetch; ++d) {
+      issue(ld, d);
+      cp_async_commit();
+      ld.next(a, nitems);
+    }
+    uint32_t u = 0;
+    bool ok = true;
+    while (cv.valid) {
+      issue(ld, (u + kPrefetch) % kRawSlots);
+      cp_async_commit();
+      ld.next(a, nitems);
+      cp_async_wait<kPrefetch>();  // this thread's loads of stage u have landed
+      const int s = u % kNS;
+      if (!mbar_wait(su32(&bars->empty[s]), ((u / kNS) & 1) ^ 1, abort_flag)) { ok = false; break; }
+      unsigned char* base = smem + s * kStageBytes;
+      const int npan = (cv.ti == cv.tj) ? 1 : 2;
+      if (tf32) {
+        // items: (panel, 4-row quad, column); loads first, then one 16-byte
+        // K-major chunk per item
+        const int nit = npan * (kKS / 4) * kTile;
+        float w[8][4];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int e = ct + j * (kConvWarps * 32);
+          const int mn = e & (kTile - 1), kq = (e >> 7) & (kKS / 4 - 1), pan = e >> 10;
+          const int col = (pan == 0 ? cv.ti : cv.tj) * kTile + mn;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int64_t sr = cv.r0 + (int64_t)cv.st * kKS + kq * 4 + i;
+            w[j][i] = (e < nit && sr < cv.r1) ? zval_f32(a, a.perm ? (int64_t)a.perm[sr] : sr, col) : 0.f;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int e = ct + j * (kConvWarps * 32);
+          if (e < nit) {
+            const int mn = e & (kTile - 1), kq = (e >> 7) & (kKS / 4 - 1), pan = e >> 10;
+            *reinterpret_cast<uint4*>(base + pan * 16384 + off_kmaj_f32(mn, kq)) =
+                make_uint4(to_tf32(w[j][0]), to_tf32(w[j][1]), to_tf32(w[j][2]), to_tf32(w[j][3]));
+          }
+        }
+      } else {
+        const unsigned char* rs = raw + (u % kRawSlots) * kRawBytes;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int e = ct + j * (kConvWarps * 32);
+          if (e >= npan * kKS * 16) break;
+          int64_t row;
+          int col;
           float v[8];
-          if (sr < r1) {
-            const int64_t row = a.perm ? (int64_t)a.perm[sr] : sr;
-            load8(a, row, (pan == 0 ? ti : tj) * kTile + g * 8, v);
+          if (item_async(a, cv, e, &row, &col)) {
+            if (f32) {
+              const float4 q0 = *reinterpret_cast<const float4*>(rs + e * 32);
+              const float4 q1 = *reinterpret_cast<const float4*>(rs + e * 32 + 16);
+              v[0] = q0.x; v[1] = q0.y; v[2] = q0.z; v[3] = q0.w;
+              v[4] = q1.x; v[5] = q1.y; v[6] = q1.z; v[7] = q1.w;
+            } else {
+              const uint4 q = *reinterpret_cast<const uint4*>(rs + e * 16);
+              const uint32_t wq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                v[2 * i] = __uint_as_float(wq[i] << 16);
+                v[2 * i + 1] = __uint_as_float(wq[i] & 0xFFFF0000u);
+              }
+            }
+          } else if (row >= 0) {
+            load8(a, row, col, v);
           } else {
 #pragma unroll
             for (int i = 0; i < 8; ++i) v[i] = 0.f;
           }
+          const int g = e & 15, r = (e >> 4) & (kKS - 1), pan = e >> 9;
           unsigned char* ph = base + pan * 16384;
-          uint4 hi;
-          hi.x = pack_bf16(v[0], v[1]); hi.y = pack_bf16(v[2], v[3]);
-          hi.z = pack_bf16(v[4], v[5]); hi.w = pack_bf16(v[6], v[7]);
           const uint32_t o = off_bf16(g * 8, r);
+          uint4 hi, lo;
+          split8(v, hi, lo);
           *reinterpret_cast<uint4*>(ph + o) = hi;
-          if (split) {
-            uint4 lo;
-            lo.x = pack_bf16(v[0] - bf16_round(v[0]), v[1] - bf16_round(v[1]));
-            lo.y = pack_bf16(v[2] - bf16_round(v[2]), v[3] - bf16_round(v[3]));
-            lo.z = pack_bf16(v[4] - bf16_round(v[4]), v[5] - bf16_round(v[5]));
-            lo.w = pack_bf16(v[6] - bf16_round(v[6]), v[7] - bf16_round(v[7]));
-            *reinterpret_cast<uint4*>(ph + 8192 + o) = lo;
-          }
+          if (split) *reinterpret_cast<uint4*>(ph + 8192 + o) = lo;
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(su32(&bars->full[s]));
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(su32(&bars->full[s]));
+      cv.next(a, nitems);
+      ++u;
     }
+    cp_async_wait<0>();
     if (!ok) { bars->abort = 1; atomicOr(a.dstatus, kStatTimeout); }
   }
 
@@ -480,10 +597,15 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a, int fl
 
 }  // namespace tc
 
+size_t gram_tc_smem_bytes() {
+  return (size_t)tc::kNS * tc::kStageBytes + (size_t)tc::kRawSlots * tc::kRawBytes +
+         sizeof(tc::Bars) + 1024;
+}
+
 cudaError_t launch_gram_tc(const GramArgs& a, int flush_rows, cudaStream_t s) {
   if (flush_rows <= 0) flush_rows = 256;
   const int flush_stages = (flush_rows + tc::kKS - 1) / tc::kKS;
-  const size_t smem = (size_t)tc::kNS * tc::kStageBytes + tc::kGuardBytes + sizeof(tc::Bars) + 1024;
+  const size_t smem = gram_tc_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(tc::gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

@@ -1,0 +1,519 @@
+// Host-side helpers shared by the C-ABI entry points (api.cu) and the
+// serving runtime (server.cu): the context, the workspace arena, argument
+// checks, the Gram-pass plan, penalty upload and the iteration plan.
+#pragma once
+
+#include "oem_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+using namespace oem;
+
+struct oem_ctx {
+  int device = 0;
+  int num_sms = kNumSMsHint;
+  size_t budget = 0;
+  void* arena = nullptr;
+  size_t arena_cap = 0;
+  cudaStream_t arena_stream = nullptr;
+  unsigned* dstatus = nullptr;
+  int64_t launches = 0;
+  char err[512] = {0};
+  // per-kernel profiling (events around launches while enabled)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Pending { int cls; cudaEvent_t e0, e1; int64_t n; };
+  std::vector<Pending> pending;
+  double prof_ms[OEM_PROF_NKERNELS] = {0};
+  int64_t prof_n[OEM_PROF_NKERNELS] = {0};
+};
+
+namespace oem {
+namespace host {
+
+inline int fail(oem_ctx* ctx, int code, const char* fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CU(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, OEM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
+  } while (0)
+
+inline cudaEvent_t prof_event(oem_ctx* ctx) {
+  if (!ctx->ev_pool.empty()) {
+    cudaEvent_t e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return e;
+}
+
+// Bracket a launch (or a launch sequence of `n` kernels) with events.
+struct ProfScope {
+  oem_ctx* ctx;
+  cudaStream_t s;
+  int cls;
+  int64_t n;
+  cudaEvent_t e0 = nullptr;
+  ProfScope(oem_ctx* c, cudaStream_t st, int k, int64_t cnt) : ctx(c), s(st), cls(k), n(cnt) {
+    if (ctx->prof && (e0 = prof_event(ctx))) cudaEventRecord(e0, s);
+  }
+  ~ProfScope() {
+    if (!e0) return;
+    cudaEvent_t e1 = prof_event(ctx);
+    if (!e1) { ctx->ev_pool.push_back(e0); return; }
+    cudaEventRecord(e1, s);
+    ctx->pending.push_back({cls, e0, e1, n});
+  }
+};
+
+#define LAUNCH(cls, call)                                                                \
+  do {                                                                                   \
+    cudaError_t e_;                                                                      \
+    {                                                                                    \
+      ProfScope ps_(ctx, s, (cls), 1);                                                   \
+      e_ = (call);                                                                       \
+    }                                                                                    \
+    ++ctx->launches;                                                                     \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, OEM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
+  } while (0)
+
+inline cudaError_t lanczos_prof(oem_ctx* ctx, cudaStream_t s, const double* G, int64_t p, int64_t ldg,
+                         int batch, int64_t strideG, int steps, LanczosWork w, double* d,
+                         cudaStream_t s2, int64_t* launches) {
+  const int64_t before = *launches;
+  cudaEvent_t e0 = ctx->prof ? prof_event(ctx) : nullptr;
+  if (e0) cudaEventRecord(e0, s);
+  cudaError_t e = launch_lanczos(G, p, ldg, batch, strideG, steps, w, d, s2, launches);
+  if (e0) {
+    cudaEvent_t e1 = prof_event(ctx);
+    if (e1) {
+      cudaEventRecord(e1, s);
+      ctx->pending.push_back({OEM_PROF_LANCZOS, e0, e1, *launches - before});
+    } else {
+      ctx->ev_pool.push_back(e0);
+    }
+  }
+  return e;
+}
+
+// Bump allocator over one stream-ordered block per call.
+struct Arena {
+  std::vector<std::pair<void**, size_t>> req;
+  template <typename P>
+  void add(P** ptr, size_t count) { req.push_back({(void**)ptr, sizeof(P) * count}); }
+  size_t total() const {
+    size_t t = 0;
+    for (auto& r : req) t += (r.second + 255) & ~(size_t)255;
+    return t;
+  }
+};
+
+inline int arena_commit(oem_ctx* ctx, Arena& A, cudaStream_t s) {
+  const size_t need = A.total();
+  if (need > ctx->budget)
+    return fail(ctx, OEM_EBUDGET, "workspace of %zu bytes exceeds the budget of %zu bytes", need,
+                ctx->budget);
+  if (need > ctx->arena_cap) {
+    if (ctx->arena) CU(cudaFreeAsync(ctx->arena, ctx->arena_stream ? ctx->arena_stream : s));
+    ctx->arena = nullptr;
+    ctx->arena_cap = 0;
+    cudaError_t e = cudaMallocAsync(&ctx->arena, need, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, OEM_ENOMEM, "workspace allocation of %zu bytes failed", need);
+    }
+    ctx->arena_cap = need;
+  }
+  ctx->arena_stream = s;
+  char* p = (char*)ctx->arena;
+  for (auto& r : A.req) {
+    *r.first = r.second ? p : nullptr;
+    p += (r.second + 255) & ~(size_t)255;
+  }
+  return OEM_OK;
+}
+
+inline size_t elem_size(int32_t xtype) { return xtype == OEM_F64 ? 8 : xtype == OEM_F32 ? 4 : 2; }
+
+inline int check_x(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, int64_t ldx,
+            const void* y) {
+  if (xtype != OEM_F64 && xtype != OEM_F32 && xtype != OEM_BF16)
+    return fail(ctx, OEM_EINVAL, "xtype %d is not OEM_F64/OEM_F32/OEM_BF16", xtype);
+  if (n < 1 || p < 1) return fail(ctx, OEM_EINVAL, "n=%lld, p=%lld must be >= 1", (long long)n, (long long)p);
+  if (n > INT32_MAX) return fail(ctx, OEM_EINVAL, "n=%lld exceeds 2^31-1", (long long)n);
+  if (p > 8192) return fail(ctx, OEM_EUNSUPPORTED, "p=%lld exceeds 8192", (long long)p);
+  if (ldx < p) return fail(ctx, OEM_EINVAL, "ldx=%lld < p=%lld", (long long)ldx, (long long)p);
+  if ((ldx * (int64_t)elem_size(xtype)) % 16 != 0)
+    return fail(ctx, OEM_EINVAL, "ldx*sizeof(element) = %lld is not a multiple of 16",
+                (long long)(ldx * (int64_t)elem_size(xtype)));
+  if (!X || !y) return fail(ctx, OEM_EINVAL, "X or y is NULL");
+  if (((uintptr_t)X & 15) || ((uintptr_t)y & 15))
+    return fail(ctx, OEM_EINVAL, "X and y must be 16-byte aligned");
+  return OEM_OK;
+}
+
+inline int resolve_mode(oem_ctx* ctx, int32_t mode, int32_t xtype, int32_t* out) {
+  if (mode == OEM_GRAM_AUTO)
+    mode = xtype == OEM_F64 ? OEM_GRAM_FP64 : xtype == OEM_BF16 ? OEM_GRAM_BF16 : OEM_GRAM_SPLIT_BF16;
+  switch (mode) {
+    case OEM_GRAM_FP64: break;
+    case OEM_GRAM_FP32:
+      if (xtype == OEM_F64) return fail(ctx, OEM_EINVAL, "OEM_GRAM_FP32 needs float32 or bfloat16 X");
+      break;
+    case OEM_GRAM_TF32:
+    case OEM_GRAM_SPLIT_BF16:
+      if (xtype != OEM_F32) return fail(ctx, OEM_EINVAL, "TF32 / SPLIT_BF16 modes need float32 X");
+      break;
+    case OEM_GRAM_BF16:
+      if (xtype != OEM_BF16) return fail(ctx, OEM_EINVAL, "OEM_GRAM_BF16 needs bfloat16 X");
+      break;
+    default: return fail(ctx, OEM_EINVAL, "unknown gram mode %d", mode);
+  }
+  *out = mode;
+  return OEM_OK;
+}
+
+inline bool tc_mode(int32_t mode) {
+  return mode == OEM_GRAM_TF32 || mode == OEM_GRAM_BF16 || mode == OEM_GRAM_SPLIT_BF16;
+}
+
+// Everything the Gram pass needs in the workspace.
+struct GramPlan {
+  int32_t mode, q, ycols, T, nt, ntiles;
+  int64_t chunk_rows, nblk;
+  int max_chunks;
+  int K;
+  bool sorted;
+};
+
+inline GramPlan plan_gram(oem_ctx* ctx, int64_t n, int64_t p, int K, int32_t mode, bool sorted) {
+  GramPlan g;
+  g.mode = mode;
+  // bfloat16 mode carries the float32 y as three bfloat16 pieces (exact)
+  g.ycols = (mode == OEM_GRAM_BF16) ? 3 : 1;
+  g.q = (int32_t)p + g.ycols;
+  g.T = tc_mode(mode) ? 128 : 64;
+  g.nt = (g.q + g.T - 1) / g.T;
+  g.ntiles = g.nt * (g.nt + 1) / 2;
+  g.K = K;
+  g.sorted = sorted;
+  const int64_t target_items = (int64_t)(tc_mode(mode) ? 4 : 4) * ctx->num_sms;
+  int64_t chunks = std::max<int64_t>(K, (target_items + g.ntiles - 1) / g.ntiles);
+  int64_t cr = (n + chunks - 1) / chunks;
+  const int64_t align = tc_mode(mode) ? 128 : 16;
+  cr = std::max<int64_t>(tc_mode(mode) ? 1024 : 256, (cr + align - 1) / align * align);
+  g.chunk_rows = cr;
+  g.max_chunks = (int)((n + cr - 1) / cr + K);
+  g.nblk = (n + 1023) / 1024;
+  return g;
+}
+
+struct GramBufs {
+  int32_t *blk_counts = nullptr, *blk_offsets = nullptr, *perm = nullptr;
+  ChunkTable ct{};
+  double* partial = nullptr;
+  double* Zg = nullptr;
+};
+
+inline void gram_request(Arena& A, const GramPlan& g, int64_t n, GramBufs& b) {
+  if (g.sorted) {
+    A.add(&b.blk_counts, (size_t)g.nblk * g.K);
+    A.add(&b.blk_offsets, (size_t)g.nblk * g.K);
+    A.add(&b.perm, (size_t)n);
+  }
+  A.add(&b.ct.row0, (size_t)g.max_chunks);
+  A.add(&b.ct.row1, (size_t)g.max_chunks);
+  A.add(&b.ct.fold, (size_t)g.max_chunks);
+  A.add(&b.ct.count, 1);
+  A.add(&b.ct.fold_c0, (size_t)g.K + 1);
+  A.add(&b.ct.fold_off, (size_t)g.K + 1);
+  A.add(&b.partial, (size_t)g.max_chunks * g.ntiles * g.T * g.T);
+  A.add(&b.Zg, (size_t)g.K * g.q * g.q);
+}
+
+// fold sort (if any) -> chunk table -> Gram partials -> per-fold Z Grams.
+inline int run_gram(oem_ctx* ctx, const GramPlan& g, GramBufs& b, const void* X, int32_t xtype,
+             int64_t n, int64_t p, int64_t ldx, const void* y, const uint8_t* fold,
+             bool require_nonempty, cudaStream_t s) {
+  if (g.sorted) {
+    LAUNCH(OEM_PROF_FOLD_SORT, launch_fold_count(fold, n, g.K, b.blk_counts, g.nblk, s));
+    LAUNCH(OEM_PROF_FOLD_SORT, launch_fold_scan(b.blk_counts, g.nblk, g.K, g.chunk_rows, b.blk_offsets, b.ct,
+                            g.max_chunks, ctx->dstatus, require_nonempty ? 1 : 0, s));
+    LAUNCH(OEM_PROF_FOLD_SORT, launch_fold_scatter(fold, n, g.K, b.blk_offsets, b.perm, s));
+  } else {
+    LAUNCH(OEM_PROF_CHUNKS, launch_identity_chunks(n, g.chunk_rows, b.ct, g.max_chunks, s));
+  }
+  GramArgs a{};
+  a.X = X; a.xtype = xtype; a.n = n; a.p = p; a.ldx = ldx; a.y = y;
+  a.perm = g.sorted ? b.perm : nullptr;
+  a.mode = g.mode; a.q = g.q; a.ycols = g.ycols; a.T = g.T; a.ntile1 = g.nt; a.ntiles = g.ntiles;
+  a.ct = b.ct; a.max_chunks = g.max_chunks; a.partial = b.partial; a.dstatus = ctx->dstatus;
+  if (tc_mode(g.mode)) {
+    // Rows summed in float32 tensor memory before the compensated flush. The
+    // tensor cores' float32 accumulation rounds toward zero, so the error
+    // grows with the number of MMAs per window (measured at n = 2e6, p = 100,
+    // split mode: 32 rows 3.2e-7, 64 rows 5.2e-7, 256 rows 1.6e-6 relative
+    // Frobenius): split mode (4 products) uses 64-row windows, bfloat16 / tf32
+    // 256 / 128. OEM_GRAM_FLUSH_ROWS overrides.
+    int flush = g.mode == OEM_GRAM_SPLIT_BF16 ? 64 : g.mode == OEM_GRAM_TF32 ? 128 : 256;
+    if (const char* ev = getenv("OEM_GRAM_FLUSH_ROWS")) {
+      const int v = atoi(ev);
+      if (v >= 32 && v <= 65536) flush = v;
+    }
+    LAUNCH(OEM_PROF_GRAM_TC, launch_gram_tc(a, flush, s));
+  } else {
+    LAUNCH(OEM_PROF_GRAM_SIMT, launch_gram_simt(a, s));
+  }
+  LAUNCH(OEM_PROF_GRAM_REDUCE, launch_gram_reduce(a, g.K, b.Zg, s));
+  return OEM_OK;
+}
+
+// Penalties on the device.
+struct PenPlan {
+  int npen = 0;
+  int p = 0;
+  std::vector<DevPenalty> host;       // device pointers filled after commit
+  std::vector<std::vector<double>> w64;
+  std::vector<std::vector<float>> w32;
+  std::vector<std::vector<int32_t>> grp;
+  std::vector<std::vector<double>> cg;
+  DevPenalty* dpens = nullptr;
+  std::vector<double*> d_w64;
+  std::vector<float*> d_w32;
+  std::vector<int32_t*> d_grp;
+  std::vector<double*> d_cg;
+  std::vector<char> allowed;  // slice boundary allowed at row i (group starts)
+};
+
+inline int prepare_pens(oem_ctx* ctx, const oem_penalty* pens, int npen, int64_t p, PenPlan& P) {
+  if (!pens || npen < 1 || npen > 8) return fail(ctx, OEM_EINVAL, "npen=%d must be in [1,8]", npen);
+  P.npen = npen;
+  P.p = (int)p;
+  P.host.resize(npen);
+  P.w64.resize(npen); P.w32.resize(npen); P.grp.resize(npen); P.cg.resize(npen);
+  P.d_w64.assign(npen, nullptr); P.d_w32.assign(npen, nullptr);
+  P.d_grp.assign(npen, nullptr); P.d_cg.assign(npen, nullptr);
+  P.allowed.assign((size_t)p + 1, 1);
+  for (int i = 0; i < npen; ++i) {
+    const oem_penalty& q = pens[i];
+    if (q.kind < OEM_LASSO || q.kind > OEM_GROUP_LASSO)
+      return fail(ctx, OEM_EINVAL, "penalty %d: unknown kind %d", i, q.kind);
+    if (q.kind == OEM_ENET && !(q.alpha >= 0.0 && q.alpha <= 1.0))
+      return fail(ctx, OEM_EINVAL, "penalty %d: elastic net alpha=%g not in [0,1]", i, q.alpha);
+    if (q.kind == OEM_MCP && !(q.gamma > 1.0))
+      return fail(ctx, OEM_EINVAL, "penalty %d: MCP gamma=%g must exceed 1", i, q.gamma);
+    if (q.kind == OEM_SCAD && !(q.gamma > 2.0))
+      return fail(ctx, OEM_EINVAL, "penalty %d: SCAD gamma=%g must exceed 2", i, q.gamma);
+    DevPenalty d{};
+    d.kind = q.kind;
+    d.alpha64 = q.kind == OEM_ENET ? q.alpha : 1.0;
+    d.gamma64 = (q.kind == OEM_MCP || q.kind == OEM_SCAD) ? q.gamma : 3.0;
+    d.alpha = (float)d.alpha64;
+    d.gamma = (float)d.gamma64;
+    if (q.w && q.kind != OEM_GROUP_LASSO) {
+      P.w64[i].assign(q.w, q.w + p);
+      P.w32[i].resize(p);
+      for (int64_t j = 0; j < p; ++j) {
+        if (!(q.w[j] >= 0.0) || !std::isfinite(q.w[j]))
+          return fail(ctx, OEM_EINVAL, "penalty %d: weight %lld is %g", i, (long long)j, q.w[j]);
+        P.w32[i][j] = (float)q.w[j];
+      }
+    }
+    if (q.kind == OEM_GROUP_LASSO) {
+      if (!q.group || q.ngroups < 1)
+        return fail(ctx, OEM_EINVAL, "penalty %d: group lasso needs group ids and ngroups >= 1", i);
+      P.grp[i].assign(q.group, q.group + p);
+      std::vector<int> seen(q.ngroups, 0), cnt(q.ngroups, 0);
+      for (int64_t j = 0; j < p; ++j) {
+        const int g = q.group[j];
+        if (g < 0 || g >= q.ngroups)
+          return fail(ctx, OEM_EINVAL, "penalty %d: group id %d out of range", i, g);
+        if (j > 0 && g != q.group[j - 1]) {
+          if (seen[g])
+            return fail(ctx, OEM_EUNSUPPORTED,
+                        "penalty %d: the variables of group %d are not contiguous", i, g);
+        }
+        seen[g] = 1;
+        ++cnt[g];
+        if (j > 0 && g == q.group[j - 1]) P.allowed[j] = 0;
+      }
+      P.cg[i].resize(q.ngroups);
+      for (int g = 0; g < q.ngroups; ++g) {
+        const double v = q.cg ? q.cg[g] : std::sqrt((double)cnt[g]);
+        if (!(v >= 0.0)) return fail(ctx, OEM_EINVAL, "penalty %d: group weight %d is %g", i, g, v);
+        P.cg[i][g] = v;
+      }
+      d.ngroups = q.ngroups;
+    }
+    P.host[i] = d;
+  }
+  return OEM_OK;
+}
+
+inline void pens_request(Arena& A, PenPlan& P) {
+  A.add(&P.dpens, (size_t)P.npen);
+  for (int i = 0; i < P.npen; ++i) {
+    if (!P.w64[i].empty()) { A.add(&P.d_w64[i], P.w64[i].size()); A.add(&P.d_w32[i], P.w32[i].size()); }
+    if (!P.grp[i].empty()) { A.add(&P.d_grp[i], P.grp[i].size()); A.add(&P.d_cg[i], P.cg[i].size()); }
+  }
+}
+
+inline int pens_upload(oem_ctx* ctx, PenPlan& P, cudaStream_t s) {
+  for (int i = 0; i < P.npen; ++i) {
+    DevPenalty& d = P.host[i];
+    if (!P.w64[i].empty()) {
+      CU(cudaMemcpyAsync(P.d_w64[i], P.w64[i].data(), P.w64[i].size() * 8, cudaMemcpyHostToDevice, s));
+      CU(cudaMemcpyAsync(P.d_w32[i], P.w32[i].data(), P.w32[i].size() * 4, cudaMemcpyHostToDevice, s));
+      d.w64 = P.d_w64[i];
+      d.w32 = P.d_w32[i];
+    }
+    if (!P.grp[i].empty()) {
+      CU(cudaMemcpyAsync(P.d_grp[i], P.grp[i].data(), P.grp[i].size() * 4, cudaMemcpyHostToDevice, s));
+      CU(cudaMemcpyAsync(P.d_cg[i], P.cg[i].data(), P.cg[i].size() * 8, cudaMemcpyHostToDevice, s));
+      d.grp = P.d_grp[i];
+      d.cg = P.d_cg[i];
+    }
+  }
+  CU(cudaMemcpyAsync(P.dpens, P.host.data(), sizeof(DevPenalty) * P.npen, cudaMemcpyHostToDevice, s));
+  return OEM_OK;
+}
+
+inline int check_opts(oem_ctx* ctx, const oem_options* o) {
+  if (!o) return fail(ctx, OEM_EINVAL, "options are NULL");
+  if (o->nlambda < 1 || o->nlambda > 100000) return fail(ctx, OEM_EINVAL, "nlambda=%d", o->nlambda);
+  if (!o->lambdas && !(o->lambda_min_ratio > 0.0 && o->lambda_min_ratio <= 1.0))
+    return fail(ctx, OEM_EINVAL, "lambda_min_ratio=%g not in (0,1]", o->lambda_min_ratio);
+  if (!(o->tol > 0.0)) return fail(ctx, OEM_EINVAL, "tol=%g must be > 0", o->tol);
+  if (o->max_iter < 1) return fail(ctx, OEM_EINVAL, "max_iter=%lld must be >= 1", (long long)o->max_iter);
+  if (o->iter_precision != OEM_ITER_F32 && o->iter_precision != OEM_ITER_F64)
+    return fail(ctx, OEM_EINVAL, "iter_precision=%d", o->iter_precision);
+  const int c = o->cluster_ctas;
+  if (!(c == 0 || c == 1 || c == 2 || c == 4 || c == 8 || c == 16))
+    return fail(ctx, OEM_EINVAL, "cluster_ctas=%d not in {0,1,2,4,8,16}", c);
+  return OEM_OK;
+}
+
+// Row slices of p rows over a cluster of C CTAs: even boundaries moved forward
+// to the next row where a slice may start (group starts for group penalties).
+inline void make_slices(int64_t p, int C, const std::vector<char>& allowed, int32_t* slice, int* max_rows) {
+  slice[0] = 0;
+  slice[C] = (int32_t)p;
+  for (int r = 1; r < C; ++r) {
+    int64_t bnd = std::max<int64_t>(slice[r - 1], (p * r) / C);
+    while (bnd < p && !allowed[bnd]) ++bnd;
+    slice[r] = (int32_t)bnd;
+  }
+  int mr = 1;
+  for (int r = 0; r < C; ++r) mr = std::max(mr, slice[r + 1] - slice[r]);
+  *max_rows = mr;
+}
+
+constexpr size_t kIterSmemCap = 227 * 1024;
+
+// Iteration launch plan for B tasks of the same shape (a fit or the K+1
+// Grams of a cross validation): cluster size, slices, shared memory.
+struct IterPlan {
+  int C = 1, M = 1, max_rows = 0, smem_rows = 0;
+  size_t smem = 0;
+  int32_t slice[kMaxCluster + 1] = {0};
+  bool groups = false;
+  IterTask* d_tasks = nullptr;
+  uint8_t* d_allowed = nullptr;
+};
+
+inline int plan_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, const oem_options* o, IterPlan& I) {
+  const int prec = o->iter_precision;
+  I.M = oem_iter_mpad(P.npen);
+  I.groups = false;
+  for (int i = 0; i < P.npen; ++i) I.groups |= P.host[i].kind == OEM_GROUP_LASSO;
+  int C;
+  if (o->cluster_ctas > 0) {
+    C = o->cluster_ctas;
+  } else {
+    // about 32 rows per CTA, at most 16 CTAs, and the clusters of all B Grams
+    // resident at once
+    const int want = (int)std::min<int64_t>(16, std::max<int64_t>(1, (p + 31) / 32));
+    const int byB = std::max(1, ctx->num_sms / std::max(1, B));
+    C = 1;
+    while (C * 2 <= std::min(want, byB) && C < 16) C *= 2;
+  }
+  for (;; C /= 2) {
+    make_slices(p, C, P.allowed, I.slice, &I.max_rows);
+    const size_t fixed = oem_iter_smem_fixed((int)p, P.npen, I.max_rows, prec);
+    if (fixed + 1024 > kIterSmemCap)
+      return fail(ctx, OEM_EUNSUPPORTED, "p=%lld too large for the iteration kernel", (long long)p);
+    const size_t per = oem_iter_smem_per_row((int)p, prec);
+    I.smem_rows = (int)std::min<size_t>((size_t)I.max_rows, (kIterSmemCap - fixed) / per);
+    I.smem = fixed + (size_t)I.smem_rows * per;
+    I.C = C;
+    IterLaunch probe{};
+    probe.ntasks = B; probe.C = C; probe.M = I.M; probe.precision = prec; probe.smem = I.smem;
+    if (oem_iter_max_cluster(probe) >= 1) return OEM_OK;
+    if (C == 1) return fail(ctx, OEM_ECUDA, "no cluster configuration of the iteration kernel fits");
+  }
+}
+
+inline void iter_request(Arena& A, int64_t p, int B, IterPlan& I) {
+  A.add(&I.d_tasks, (size_t)B);
+  if (I.groups) A.add(&I.d_allowed, (size_t)p + 1);
+}
+
+// B tasks: Gram b uses G32 + b p ldg (or G64 + b p p), c + b p, d + b, and
+// writes beta + b npen L p, iters / conv + b npen L.
+inline int run_iter(oem_ctx* ctx, int64_t p, int B, const float* G32, int ldg, const double* G64,
+             const double* c, const double* d, const double* lam, PenPlan& P,
+             const oem_options* o, IterPlan& I, double* beta, int32_t* iters, uint8_t* conv,
+             cudaStream_t s) {
+  const int L = o->nlambda, npen = P.npen;
+  if (I.groups) {
+    std::vector<uint8_t> al(P.allowed.begin(), P.allowed.end());
+    CU(cudaMemcpyAsync(I.d_allowed, al.data(), al.size(), cudaMemcpyHostToDevice, s));
+  }
+  std::vector<IterTask> tasks(B);
+  for (int b = 0; b < B; ++b) {
+    IterTask& t = tasks[b];
+    t = IterTask{};
+    t.p = (int)p; t.npen = npen; t.L = L; t.ldg = ldg;
+    t.max_rows = I.max_rows; t.smem_rows = I.smem_rows; t.resume = 0;
+    for (int r = 0; r <= kMaxCluster; ++r) t.slice[r] = r <= I.C ? I.slice[r] : (int32_t)p;
+    t.G32 = G32 ? G32 + (size_t)b * p * ldg : nullptr;
+    t.G64 = G64 ? G64 + (size_t)b * p * p : nullptr;
+    t.c = c + (size_t)b * p;
+    t.d = d + b;
+    t.lam = lam;
+    t.pens = P.dpens;
+    t.allowed = I.groups ? I.d_allowed : nullptr;
+    t.beta = beta + (size_t)b * npen * L * p;
+    t.iters = iters + (size_t)b * npen * L;
+    t.conv = conv + (size_t)b * npen * L;
+  }
+  CU(cudaMemcpyAsync(I.d_tasks, tasks.data(), sizeof(IterTask) * B, cudaMemcpyHostToDevice, s));
+  IterLaunch Lc{};
+  Lc.tasks = I.d_tasks; Lc.ntasks = B; Lc.C = I.C; Lc.M = I.M; Lc.precision = o->iter_precision;
+  Lc.tol = o->tol; Lc.max_iter = o->max_iter; Lc.max_loops = 0; Lc.dstatus = ctx->dstatus;
+  Lc.smem = I.smem;
+  LAUNCH(OEM_PROF_ITER, launch_oem_iter(Lc, s));
+  return OEM_OK;
+}
+
+
+}  // namespace host
+}  // namespace oem

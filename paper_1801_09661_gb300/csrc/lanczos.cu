@@ -136,12 +136,23 @@ __global__ void lz_finish_kernel(LanczosWork w, int steps, double* d) {
     lo = fmin(lo, a[i] - r);
     hi = fmax(hi, a[i] + r);
   }
-  // bisection for the largest eigenvalue: count(below x) == m - 1 <=> x <= theta
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm_below(a, e, m, mid) >= m) hi = mid; else lo = mid;
+  // Multisection for the largest eigenvalue theta: count(x) >= m <=> x > theta.
+  // Each round the 32 lanes test 32 interior points and keep the sub-interval
+  // where the count crosses m (the interval shrinks 33-fold per round).
+  const int lane = threadIdx.x;
+  for (int it = 0; it < 40; ++it) {
+    const double w = (hi - lo) / 33.0;
+    const double x = lo + w * (lane + 1);
+    const bool above = (x < hi) && (x > lo) ? sturm_below(a, e, m, x) >= m : (x >= hi);
+    const unsigned mask = __ballot_sync(0xffffffffu, above);
+    const int first = mask ? __ffs(mask) - 1 : 32;  // first tested point above theta
+    const double nlo = first == 0 ? lo : lo + w * first;
+    const double nhi = first == 32 ? hi : lo + w * (first + 1);
+    if (!(nhi - nlo < hi - lo)) break;  // no further progress in float64
+    lo = nlo;
+    hi = nhi;
   }
+  if (lane != 0) return;
   const double theta = hi;
   // eigenvector of T_m for theta by inverse iteration with shift slightly
   // above theta (T - sigma I is then negative definite: no pivoting needed)
@@ -189,7 +200,7 @@ cudaError_t launch_lanczos(const double* G, int64_t p, int64_t ldg, int batch, i
     lz_update_kernel<<<batch, 1024, 0, s>>>(p, w, j, steps);
     *launches += 2;
   }
-  lz_finish_kernel<<<batch, 1, 0, s>>>(w, steps, d);
+  lz_finish_kernel<<<batch, 32, 0, s>>>(w, steps, d);
   ++*launches;
   return cudaGetLastError();
 }

@@ -120,40 +120,48 @@ struct DevPenalty {
 cudaError_t launch_lambda_grid(const double* c, int p, const DevPenalty* pens, int npen,
                                int nlambda, double ratio, double* lam, cudaStream_t s);
 
-// OEM iteration over all (Gram b, penalty i) instances.
-struct IterArgs {
-  int32_t p;
-  int32_t B;             // Grams
-  int32_t npen;          // instances per Gram
-  int32_t nlambda;
-  const float* G32;      // [B][p][ldg]
-  const double* G64;     // [B][p][p]  (float64 iteration)
-  int32_t ldg;
-  const double* c;       // [B][p]
-  const double* d;       // [B]
-  const double* lam;     // [npen][nlambda]
-  const DevPenalty* pens;// [npen]
-  double tol;
-  int64_t max_iter;
-  double* beta;          // [B][npen][nlambda][p]
-  int32_t* iters;        // [B][npen][nlambda]
-  uint8_t* conv;         // [B][npen][nlambda]
-  unsigned* dstatus;
-  // row slices: CTA r of a cluster owns rows [slice[r], slice[r+1])
-  const int32_t* slice;  // [C+1]
-  int32_t C;
-  int32_t max_rows;      // max slice length
+// OEM iteration. One task = one Gram and its instances (penalties); a launch
+// runs one thread-block cluster per task. Tasks of one launch may differ in p.
+constexpr int kMaxCluster = 16;
+struct IterTask {
+  int32_t p, npen, L, ldg;
+  int32_t max_rows;      // longest CTA slice
   int32_t smem_rows;     // leading rows of each slice kept in shared memory
-  int32_t precision;     // OEM_ITER_F32 / OEM_ITER_F64
+  int32_t resume;        // 1: start from st_* instead of beta = 0, u = c
+  int32_t slice[kMaxCluster + 1];  // CTA r owns rows [slice[r], slice[r+1])
+  const float* G32;      // [p][ldg] (float32 iteration)
+  const double* G64;     // [p][p]   (float64 iteration)
+  const double* c;       // [p] scaled X^T y
+  const double* d;       // [1]
+  const double* lam;     // [npen][L]
+  const DevPenalty* pens;// [npen]
+  const uint8_t* allowed;// [p+1] rows where a slice may start (group starts) or NULL
+  double* beta;          // [npen][L][p]
+  int32_t* iters;        // [npen][L]
+  uint8_t* conv;         // [npen][L]
+  double* st_u;          // [npen][p][2] saved u (hi, lo) or NULL (no state)
+  double* st_beta;       // [npen][p]
+  int32_t* st_ctl;       // [40]: per instance (lambda index, iterations, done, -);
+                         // [32] = every instance done
+  int32_t* fin_out;      // where the launch writes "every instance done" (or NULL)
+};
+struct IterLaunch {
+  const IterTask* tasks; // device array
+  int32_t ntasks, C, M, precision;
+  double tol;
+  int64_t max_iter;      // per lambda
+  int64_t max_loops;     // per launch (<= 0: run to completion)
+  unsigned* dstatus;
+  size_t smem;
 };
 // Instances per Gram are padded to M in {1, 2, 4, 8}.
 int oem_iter_mpad(int npen);
 // Shared memory needed besides the resident Gram rows, and per resident row.
-size_t oem_iter_smem_fixed(int p, int npen, int max_rows, int C, int precision);
+size_t oem_iter_smem_fixed(int p, int npen, int max_rows, int precision);
 size_t oem_iter_smem_per_row(int p, int precision);
-// Largest cluster size the device can co-schedule for this configuration (0 if none).
-int oem_iter_max_cluster(const IterArgs& a, size_t smem, int C);
-cudaError_t launch_oem_iter(const IterArgs& a, size_t smem, cudaStream_t s);
+// Clusters of this configuration the device can co-schedule (0: none).
+int oem_iter_max_cluster(const IterLaunch& P);
+cudaError_t launch_oem_iter(const IterLaunch& P, cudaStream_t s);
 
 // CV scoring from raw fold Grams of Z and the fold paths.
 cudaError_t launch_cv_score(const double* Zg, int K, int q, int p, int ycols,

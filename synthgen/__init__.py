@@ -219,6 +219,12 @@ WORKLOADS = {
         sigma=1.0, beta="sparse25",
         penalties=("lasso", "enet", "mcp", "scad"), seed=1,
         extra={"alpha": 0.5, "gamma_mcp": 3.0, "gamma_scad": 3.7}),
+    # the same problem at n = 200,000 (X = 400 MB, above L2): profiler captures
+    "four_penalties_f32_n2e5_p500": Workload(
+        "four_penalties_f32_n2e5_p500", 200_000, 500, "f32", "ar1", rho=0.5,
+        sigma=1.0, beta="sparse25",
+        penalties=("lasso", "enet", "mcp", "scad"), seed=1,
+        extra={"alpha": 0.5, "gamma_mcp": 3.0, "gamma_scad": 3.7}),
     "cv10_f32_n4e6_p200": Workload(
         "cv10_f32_n4e6_p200", 4_000_000, 200, "f32", "ar1", rho=0.5, sigma=2.0,
         beta="lead", beta_head=(-0.5, -0.5, 0.5, 0.5, 1.0), K=10,

@@ -3,13 +3,16 @@
 Tolerances (relative Frobenius error of X^T X, and relative error of X^T y
 and y^T y):
   * SPLIT_BF16 (float32 X, hi/lo bfloat16 products, float32 accumulation in
-    tensor memory, compensated across 256-row windows): 1e-6;
-  * BF16 (bfloat16 X: exact products; float32 y split into two columns): 1e-6;
+    tensor memory, compensated across 64-row windows): 1e-6 for tall X (see
+    _tol for short, wide X);
+  * BF16 (bfloat16 X: exact products; float32 y as three bfloat16 columns): 1e-6;
   * TF32 (float32 X rounded to tf32): 5e-4 (reported mode; its operand
     rounding alone is 2^-11 per element).
 Sizes span one to three 128-column tiles with ragged tails and rows that are
 not a multiple of the 32-row stage.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -20,6 +23,16 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {"split_bf16": 1e-6, "bf16": 1e-6, "tf32": 5e-4}
+
+
+def _tol(mode, n, p):
+    """Split-bf16 carries each element as hi + lo with a relative error up to
+    2^-18; over the p^2 entries that noise is about 2^-18 sqrt(p/n) of
+    ||G||_F, which passes 1e-6 only when p/n > ~0.07 (short, wide X, outside
+    the tall regime the method targets). Tall shapes keep the 1e-6 bar."""
+    if mode == "split_bf16":
+        return max(TOL[mode], 2.0 * 2.0 ** -18 * math.sqrt(p / max(n, 1)))
+    return TOL[mode]
 
 
 @pytest.fixture(scope="module")
@@ -69,7 +82,8 @@ def test_tc_gram_matches_oracle(oem, ctx, mode, n, p):
     ec = _rel(c.cpu().numpy(), cr)
     en = abs(float(yty.cpu()[0]) - Nr) / Nr
     print(f"{mode} n={n} p={p}: G {eg:.2e} c {ec:.2e} yty {en:.2e}")
-    assert eg <= TOL[mode] and ec <= TOL[mode] and en <= TOL[mode]
+    tol = _tol(mode, n, p)
+    assert eg <= tol and ec <= tol and en <= tol
 
 
 @pytest.mark.parametrize("mode", ["split_bf16", "bf16"])
@@ -82,8 +96,21 @@ def test_tc_fold_grams_gathered_rows(oem, ctx, mode):
     Gr, cr, Nr, nr = oracle.fold_gram_sums(synthgen.as_f64(X), y, fold, K)
     assert np.array_equal(nk.cpu().numpy(), nr)
     for k in range(K):
-        assert _rel(Gk[k].cpu().numpy(), Gr[k]) <= TOL[mode]
-        assert _rel(ck[k].cpu().numpy(), cr[k]) <= TOL[mode]
+        tol = _tol(mode, int(nr[k]), p)
+        assert _rel(Gk[k].cpu().numpy(), Gr[k]) <= tol
+        assert _rel(ck[k].cpu().numpy(), cr[k]) <= tol
+
+
+def test_split_gram_tall_bench_shape(oem, ctx):
+    """The benchmark's shape at n = 200,000 (p = 500): the strict 1e-6 bar."""
+    n, p = 200_000, 500
+    X, y = _data(n, p, 13, "split_bf16")
+    G, c, yty = oem.oem_gram(ctx, _xdev(X), _dev(y), mode="split_bf16")
+    assert ctx.sync() == 0
+    Gr, cr, Nr, _ = oracle.gram_sums(X, y)
+    eg, ec = _rel(G.cpu().numpy(), Gr), _rel(c.cpu().numpy(), cr)
+    print(f"split_bf16 n={n} p={p}: G {eg:.2e} c {ec:.2e}")
+    assert eg <= 1e-6 and ec <= 1e-6
 
 
 def test_split_gram_precision_at_large_n(oem, ctx):
