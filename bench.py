@@ -343,13 +343,119 @@ def run_ours(args, w, rank, world, local_rank):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Serving: Poisson arrivals of mixed fit / CV jobs, served (batched) vs plain
+# ---------------------------------------------------------------------------
+
+def run_serving(args, rank, world, local_rank):
+    """Requests arrive as a Poisson stream (50/s); each has n log-uniform in
+    [1e4, 2e6], p uniform in [20, 1000], float32 AR(0.5) rows, 30% 5-fold CV,
+    lasso or MCP (gamma 3) with 50 lambdas. The batched server admits them
+    under a 150 GB budget and runs them with continuous batching; latency is
+    submission -> results in host memory. The plain per-job form runs the
+    first --plain-requests of them (submitted at once) for the throughput
+    comparison, against the batched form on the same requests."""
+    import torch
+    import paper_1801_09661_gb300 as oem
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    reqs = synthgen.serving_requests(args.requests, seed=5 + 1000 * rank, rate_per_s=args.rate)
+    n_max = max(r["n"] for r in reqs)
+    bases = [synthgen.device_ar1_base(n_max, 1000, 0.5, 77 + b, device=dev) for b in range(2)]
+    data = [synthgen.device_request_data(bases[r["id"] % 2], r) for r in reqs]
+    torch.cuda.synchronize()
+
+    def submit(srv, r, d):
+        X, y, fold = d
+        pen = oem.Penalty(r["penalty"], gamma=r["gamma"])
+        return srv.submit(X, y, pen, fold=fold, K=r["K"], nlambda=r["nlambda"], tol=1e-7,
+                          gram_mode="auto")
+
+    def paths_of(r):
+        return r["K"] + 1 if r["K"] else 1
+
+    # ---- served, Poisson arrivals
+    srv = oem.Server(local_rank, budget_bytes=int(args.budget_gb * (1 << 30)), form="batched",
+                     iters_per_round=args.iters_per_round)
+    clocks = ClockSampler(local_rank)
+    t0 = time.perf_counter()
+    ids = []
+    for r, d in zip(reqs, data):
+        dt = r["arrival_s"] - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(submit(srv, r, d))
+    lat = []
+    for i in ids:
+        st, l, rc = srv.wait(i, 3600)
+        lat.append(l)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    st_b = srv.stats()
+    srv.close()
+    total_paths = sum(paths_of(r) for r in reqs)
+    lat = np.array(lat)
+    served = {"paths_per_s": total_paths / wall, "wall_s": wall, "requests": len(reqs),
+              "paths": total_paths, "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                                   "p99": float(np.percentile(lat, 99)),
+                                                   "mean": float(lat.mean())},
+              "rounds": st_b["rounds"], "kernel_launches": st_b["launches"],
+              "peak_device_bytes": st_b["peak_bytes"]}
+
+    # ---- throughput on the same requests: batched vs plain, all submitted at once
+    m = min(args.plain_requests, len(reqs))
+    out = {}
+    for form in ("batched", "plain"):
+        s2 = oem.Server(local_rank, budget_bytes=int(args.budget_gb * (1 << 30)), form=form,
+                        iters_per_round=args.iters_per_round)
+        t1 = time.perf_counter()
+        ii = [submit(s2, reqs[k], data[k]) for k in range(m)]
+        ll = [s2.wait(i, 7200)[1] for i in ii]
+        w2 = time.perf_counter() - t1
+        res = [s2.result(i) for i in ii]
+        s2.close()
+        out[form] = {"paths_per_s": sum(paths_of(reqs[k]) for k in range(m)) / w2, "wall_s": w2,
+                     "p50_ms": float(np.percentile(ll, 50)), "p99_ms": float(np.percentile(ll, 99)),
+                     "betas": [r["beta"] for r in res]}
+    # equal accuracy: the two forms' paths agree (max |dbeta| relative to ||beta||_inf)
+    acc = max(float(np.abs(a - b).max() / max(1.0, np.abs(b).max()))
+              for a, b in zip(out["batched"]["betas"], out["plain"]["betas"]))
+    for f in out.values():
+        f.pop("betas")
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "fitted paths/s (served, Poisson arrivals)", "value": served["paths_per_s"],
+        "unit": "paths/s", "n_gpus": world, "steps": len(reqs), "warmup": 0,
+        "ms_per_step": 1000.0 * wall / len(reqs), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving", "requests": len(reqs), "rate_per_s": args.rate,
+                   "n": "log-uniform [1e4, 2e6]", "p": "uniform [20, 1000]", "cv_frac": 0.3,
+                   "K": 5, "nlambda": 50, "penalties": ["lasso", "mcp"],
+                   "budget_gb": args.budget_gb, "iters_per_round": args.iters_per_round},
+        "served": served,
+        "same_requests": {"requests": m, "batched": out["batched"], "plain": out["plain"],
+                          "batched_over_plain": out["batched"]["paths_per_s"] / out["plain"]["paths_per_s"],
+                          "max_rel_beta_diff": acc},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synthgen.WORKLOADS))
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synthgen.WORKLOADS) + ["serving"])
+    ap.add_argument("--requests", type=int, default=300, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=50.0, help="serving: arrivals per second")
+    ap.add_argument("--plain-requests", type=int, default=40,
+                    help="serving: requests in the batched-vs-plain comparison")
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--iters-per-round", type=int, default=1000)
     ap.add_argument("--gram-mode", default="auto",
                     choices=["auto", "split_bf16", "tf32", "fp32", "fp64", "bf16"])
     ap.add_argument("--cpu-sample-rows", type=int, default=100_000)
@@ -360,6 +466,13 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "serving":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "serving is a GPU request loop; the oracle has no serving form "
+                              "(run the default workload for the oracle reference arm)"}))
+            return 0
+        return run_serving(args, rank, world, local_rank)
     w = synthgen.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w, rank, world)

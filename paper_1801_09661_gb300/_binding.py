@@ -42,7 +42,8 @@ MODE = {"fp64": OEM_GRAM_FP64, "fp32": OEM_GRAM_FP32, "tf32": OEM_GRAM_TF32,
 EXPORTED = ["oem_options_default", "oem_create", "oem_destroy", "oem_last_error", "oem_sync",
             "oem_kernel_launches", "oem_profile_enable", "oem_profile_get", "oem_profile_name",
             "oem_gram", "oem_gram_noalloc", "oem_fold_grams", "oem_spectral_d", "oem_fit_path",
-            "oem_fit", "oem_cv"]
+            "oem_fit", "oem_cv", "oem_server_create", "oem_server_submit", "oem_server_poll",
+            "oem_server_result", "oem_server_stats", "oem_server_destroy"]
 OEM_PROF_NKERNELS = 11
 
 
@@ -59,6 +60,16 @@ class oem_options(C.Structure):
                 ("gram_mode", C.c_int32), ("iter_precision", C.c_int32),
                 ("cluster_ctas", C.c_int32)]
 
+
+class oem_job(C.Structure):
+    _fields_ = [("X", C.c_void_p), ("xtype", C.c_int32), ("n", C.c_int64), ("p", C.c_int64),
+                ("ldx", C.c_int64), ("y", C.c_void_p), ("fold", C.c_void_p), ("K", C.c_int32),
+                ("pen", oem_penalty), ("nlambda", C.c_int32), ("lambda_min_ratio", C.c_double),
+                ("tol", C.c_double), ("max_iter", C.c_int64), ("gram_mode", C.c_int32)]
+
+
+OEM_SERVE_BATCHED, OEM_SERVE_PLAIN = 0, 1
+JOB_STATES = {0: "queued", 1: "prep", 2: "iter", 3: "finish", 4: "done", 5: "failed"}
 
 _vp, _i32, _i64, _d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
 _sigs = {
@@ -83,6 +94,12 @@ _sigs = {
     "oem_cv": (C.c_int, [_vp, _vp, _i32, _i64, _i64, _i64, _vp, _vp, _i32,
                          C.POINTER(oem_penalty), _i32, C.POINTER(oem_options), _vp, _vp, _vp,
                          _vp, _vp, _vp, _vp, _vp]),
+    "oem_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_size_t, _i32, _i64]),
+    "oem_server_submit": (C.c_int, [_vp, C.POINTER(oem_job), C.POINTER(C.c_int64)]),
+    "oem_server_poll": (C.c_int, [_vp, _i64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+    "oem_server_result": (C.c_int, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "oem_server_stats": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "oem_server_destroy": (C.c_int, [_vp]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(lib, _name)
@@ -349,3 +366,96 @@ def oem_cv(ctx: Context, X, y, fold, K, pens: Sequence[Penalty], stream=None, **
                          _ptr(imin), _ptr(i1se), _ptr(best), _stream(stream)))
     return {"beta": beta, "lambdas": lam, "cvm": cvm, "cvsd": cvsd, "idx_min": imin,
             "idx_1se": i1se, "best_penalty": best}
+
+
+class Server:
+    """A serving loop (oem_server_*): submit fit / CV jobs on device-resident
+    data as they arrive; the library admits them under the memory budget and
+    batches their OEM iterations (form "batched") or runs them one by one
+    with per-iteration launches (form "plain")."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0, form: str = "batched",
+                 iters_per_round: int = 2000):
+        h = C.c_void_p()
+        f = OEM_SERVE_PLAIN if form == "plain" else OEM_SERVE_BATCHED
+        rc = lib.oem_server_create(C.byref(h), int(device), C.c_size_t(int(budget_bytes)), f,
+                                   int(iters_per_round))
+        if rc != OEM_OK:
+            raise OemError(rc, "oem_server_create failed")
+        self.h = h
+        self._keep = {}
+        self._shape = {}
+
+    def submit(self, X, y, pen: Penalty, fold=None, K: int = 0, nlambda: int = 50,
+               lambda_min_ratio: float = 1e-3, tol: float = 1e-7, max_iter: int = 10000,
+               gram_mode="auto") -> int:
+        n, p = X.shape
+        P = _PenArray([pen])
+        j = oem_job()
+        j.X, j.xtype, j.n, j.p, j.ldx = _ptr(X), _xtype(X), n, p, X.stride(0)
+        j.y = _ptr(y)
+        j.fold = _ptr(fold) if fold is not None else None
+        j.K = int(K)
+        j.pen = P.arr[0]
+        j.nlambda, j.lambda_min_ratio, j.tol, j.max_iter = int(nlambda), float(lambda_min_ratio), \
+            float(tol), int(max_iter)
+        j.gram_mode = MODE[gram_mode] if isinstance(gram_mode, str) else int(gram_mode)
+        jid = C.c_int64()
+        rc = lib.oem_server_submit(self.h, C.byref(j), C.byref(jid))
+        if rc != OEM_OK:
+            raise OemError(rc, "oem_server_submit rejected the job")
+        self._keep[jid.value] = (X, y, fold, P)
+        self._shape[jid.value] = (p, int(nlambda), int(K))
+        return jid.value
+
+    def poll(self, jid: int):
+        st, lat = C.c_int32(), C.c_double()
+        rc = lib.oem_server_poll(self.h, int(jid), C.byref(st), C.byref(lat))
+        return JOB_STATES.get(st.value, "?"), lat.value, rc
+
+    def wait(self, jid: int, timeout_s: float = 600.0):
+        import time
+        t0 = time.time()
+        while True:
+            st, lat, rc = self.poll(jid)
+            if st in ("done", "failed"):
+                return st, lat, rc
+            if time.time() - t0 > timeout_s:
+                raise TimeoutError(f"job {jid} still {st}")
+            time.sleep(0.0005)
+
+    def result(self, jid: int) -> dict:
+        p, L, K = self._shape[jid]
+        beta = np.empty((L, p))
+        lam = np.empty(L)
+        cvm = np.empty(L)
+        cvsd = np.empty(L)
+        imin, i1se, its = C.c_int32(-1), C.c_int32(-1), C.c_int64()
+        rc = lib.oem_server_result(self.h, int(jid), beta.ctypes.data, lam.ctypes.data,
+                                   cvm.ctypes.data, cvsd.ctypes.data, C.addressof(imin),
+                                   C.addressof(i1se), C.addressof(its))
+        if rc != OEM_OK:
+            raise OemError(rc, f"job {jid} has no result")
+        self._keep.pop(jid, None)
+        out = {"beta": beta, "lambdas": lam, "iters": its.value}
+        if K:
+            out.update(cvm=cvm, cvsd=cvsd, idx_min=imin.value, idx_1se=i1se.value)
+        return out
+
+    def stats(self) -> dict:
+        v = [C.c_int64() for _ in range(5)]
+        lib.oem_server_stats(self.h, *[C.addressof(x) for x in v])
+        return dict(zip(("jobs_done", "paths_done", "launches", "rounds", "peak_bytes"),
+                        [x.value for x in v]))
+
+    def close(self):
+        if self.h:
+            lib.oem_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -93,7 +93,12 @@ __global__ void assemble_kernel(const double* __restrict__ Zg, int K, int q, int
     if (b > 0) s -= Zg[(b - 1) * qq + o];
     const double v = s * inv;
     if (G64) G64[b * pp + e] = v;
-    if (G32) G32[(int64_t)b * p * ldg32 + (int64_t)i * ldg32 + j] = (float)v;
+    if (G32) {
+      float* row = G32 + (int64_t)b * p * ldg32 + (int64_t)i * ldg32;
+      row[j] = (float)v;
+      if (j == p - 1)  // zero the padding columns of the float32 copy
+        for (int jj = p; jj < ldg32; ++jj) row[jj] = 0.f;
+    }
     if (j == 0) {
       double sc = 0.0;
       for (int k = 0; k < K; ++k) sc += zc(Zg + k * qq, q, p, ycols, i);
@@ -126,12 +131,15 @@ cudaError_t launch_assemble(const double* Zg, int K, int q, int p, int ycols,
 
 namespace oem {
 
+// float32 copy with leading dimension ldg32 >= p; the padding columns are zero.
 __global__ void convert_g_kernel(const double* __restrict__ G64, int64_t p, float* G32, int ldg32) {
   const int b = blockIdx.y;
-  const int64_t pp = p * p;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < pp;
-       e += (int64_t)gridDim.x * blockDim.x)
-    G32[(int64_t)b * p * ldg32 + (e / p) * ldg32 + (e % p)] = (float)G64[b * pp + e];
+  const int64_t pl = p * ldg32;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < pl;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ldg32, j = e % ldg32;
+    G32[(int64_t)b * pl + e] = j < p ? (float)G64[b * p * p + i * p + j] : 0.f;
+  }
 }
 
 cudaError_t launch_convert_g(const double* G64, int64_t p, int B, float* G32, int ldg32,

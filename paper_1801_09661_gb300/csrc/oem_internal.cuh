@@ -116,6 +116,43 @@ struct DevPenalty {
   int32_t ngroups;
 };
 
+// Scalar updates of Section 2.2 (Eqs. lasso, net, mcp, scad); wl = w_j lambda.
+template <typename T>
+__device__ __forceinline__ T thr_scalar(int kind, T u, T wl, T alpha, T gamma, T d) {
+  const T au = fabs(u);
+  if (kind == OEM_LASSO) {
+    const T s = au - wl;
+    return s > T(0) ? copysign(s / d, u) : T(0);
+  }
+  if (kind == OEM_ENET) {
+    const T s = au - wl * alpha;
+    return s > T(0) ? copysign(s / (d + wl * (T(1) - alpha)), u) : T(0);
+  }
+  if (kind == OEM_MCP) {
+    if (au <= wl * gamma * d) {
+      const T s = au - wl;
+      return s > T(0) ? copysign(gamma * s / (gamma * d - T(1)), u) : T(0);
+    }
+    return u / d;
+  }
+  // SCAD
+  if (au <= (d + T(1)) * wl) {
+    const T s = au - wl;
+    return s > T(0) ? copysign(s / d, u) : T(0);
+  }
+  if (au <= wl * gamma * d)
+    return copysign(((gamma - T(1)) * au - wl * gamma) / ((gamma - T(1)) * d - T(1)), u);
+  return u / d;
+}
+
+// Plain form of the iteration (one launch per OEM iteration, one instance):
+// beta_new = threshold(c + d beta - G beta) with float64 dot products of the
+// float32 Gram rows; red[0] = max|beta_new - beta|, red[1] = max|beta_new|
+// (float64 bit patterns, must start at zero).
+cudaError_t launch_plain_iter(int p, const float* G32, int ldg, const double* c, double d,
+                              const double* beta, double* beta_new, const DevPenalty* pen,
+                              double lam, unsigned long long* red, cudaStream_t s);
+
 // Lambda grid: lam[pen][l] from c (full data).
 cudaError_t launch_lambda_grid(const double* c, int p, const DevPenalty* pens, int npen,
                                int nlambda, double ratio, double* lam, cudaStream_t s);

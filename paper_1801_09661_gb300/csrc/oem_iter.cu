@@ -19,54 +19,26 @@
 //   2. thresholds (group norms first for group penalties) and forms the new
 //      dbeta_i;
 //   3. writes its dbeta rows into the shared memory of every CTA of the
-//      cluster (DSMEM) and folds its max|dbeta|, max|beta| into every CTA's
-//      reduction slot with DSMEM atomics.
-// One cluster barrier per iteration; then every thread takes the same
-// convergence decisions from the same slot. A launch may stop after a loop
-// budget and save its state (serving), to be resumed by a later launch.
+//      cluster (DSMEM).
+// The CTA then folds its warps' max|dbeta|, max|beta| (one block barrier)
+// and one warp stores the CTA's maxima into every CTA's reduction table
+// (DSMEM vector stores). One cluster barrier per iteration; then every warp
+// reduces the table and takes the same convergence decisions. A launch may
+// stop after a loop budget and save its state (serving), to be resumed by a
+// later launch.
 #include "oem_internal.cuh"
 
 #include <cooperative_groups.h>
-
-#include <type_traits>
 
 namespace cg = cooperative_groups;
 
 namespace oem {
 
-constexpr int kIterThreads = 256;
-constexpr int kIterWarps = kIterThreads / 32;
-
 int oem_iter_mpad(int npen) { return npen <= 1 ? 1 : npen <= 2 ? 2 : npen <= 4 ? 4 : 8; }
 
-// Scalar updates of Section 2.2 (Eqs. lasso, net, mcp, scad); wl = w_j lambda.
-template <typename T>
-__device__ __forceinline__ T thr_scalar(int kind, T u, T wl, T alpha, T gamma, T d) {
-  const T au = fabs(u);
-  if (kind == OEM_LASSO) {
-    const T s = au - wl;
-    return s > T(0) ? copysign(s / d, u) : T(0);
-  }
-  if (kind == OEM_ENET) {
-    const T s = au - wl * alpha;
-    return s > T(0) ? copysign(s / (d + wl * (T(1) - alpha)), u) : T(0);
-  }
-  if (kind == OEM_MCP) {
-    if (au <= wl * gamma * d) {
-      const T s = au - wl;
-      return s > T(0) ? copysign(gamma * s / (gamma * d - T(1)), u) : T(0);
-    }
-    return u / d;
-  }
-  // SCAD
-  if (au <= (d + T(1)) * wl) {
-    const T s = au - wl;
-    return s > T(0) ? copysign(s / d, u) : T(0);
-  }
-  if (au <= wl * gamma * d)
-    return copysign(((gamma - T(1)) * au - wl * gamma) / ((gamma - T(1)) * d - T(1)), u);
-  return u / d;
-}
+// Threads per CTA: 512 while the per-thread state is small, else 256.
+template <typename T, int M>
+constexpr int iter_threads() { return (sizeof(T) == 4 && M <= 4) ? 512 : 256; }
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -81,7 +53,7 @@ __device__ __forceinline__ T warp_max(T v) {
   return v;
 }
 
-// Load the M entries of row j of a [p][M] buffer.
+// Load the M entries of row j of a [rows][M] buffer.
 template <typename T, int M>
 __device__ __forceinline__ void load_col(const T* __restrict__ D, int j, T (&v)[M]) {
   const T* s = D + (size_t)j * M;
@@ -124,26 +96,24 @@ __device__ __forceinline__ void store_col(T* __restrict__ dst, const T* __restri
   }
 }
 
-// Order-preserving 32-bit images of non-negative maxima for the DSMEM
-// atomicMax (32-bit atomics only across the cluster). A float64 value is
-// rounded up to float32 first, so a max|dbeta| is never under-stated and no
-// convergence is declared early; max|beta| moves by at most 2^-24 relative.
-__device__ __forceinline__ unsigned int max_bits(float v) { return __float_as_uint(v); }
-__device__ __forceinline__ unsigned int max_bits(double v) { return __float_as_uint(__double2float_ru(v)); }
-__device__ __forceinline__ float from_bits(unsigned int b, float) { return __uint_as_float(b); }
-__device__ __forceinline__ double from_bits(unsigned int b, double) { return (double)__uint_as_float(b); }
+// The reduction table holds float32 maxima; a float64 value is rounded up
+// first, so a max|dbeta| is never under-stated and no convergence is declared
+// early (max|beta| moves by at most 2^-24 relative).
+__device__ __forceinline__ float to_red(float v) { return v; }
+__device__ __forceinline__ float to_red(double v) { return __double2float_ru(v); }
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Shared-memory carve-up (byte offsets, 16-byte aligned).
+// Shared-memory carve-up (byte offsets, 16-byte aligned). The dbeta buffers
+// have ldgs = round_up(p, 4) rows; rows p.. stay zero.
 struct IterSmem {
-  size_t dbuf, uhi, ulo, beta, w, gn, cgr, glen, st, red, gs, total;
+  size_t dbuf, uhi, ulo, beta, w, gn, cgr, glen, st, lred, red, gs, total;
 };
 __host__ __device__ inline IterSmem iter_smem_layout(int p, int M, int maxR, int tsz, int smem_rows) {
   const int ldgs = (p + 3) & ~3;
   IterSmem L;
   size_t o = 0;
-  L.dbuf = o;  o = al16(o + (size_t)2 * p * M * tsz);
+  L.dbuf = o;  o = al16(o + (size_t)2 * ldgs * M * tsz);
   L.uhi = o;   o = al16(o + (size_t)M * maxR * tsz);
   L.ulo = o;   o = al16(o + (size_t)M * maxR * tsz);
   L.beta = o;  o = al16(o + (size_t)M * maxR * tsz);
@@ -152,15 +122,16 @@ __host__ __device__ inline IterSmem iter_smem_layout(int p, int M, int maxR, int
   L.cgr = o;   o = al16(o + (size_t)M * maxR * tsz);
   L.glen = o;  o = al16(o + (size_t)M * maxR * 4);
   L.st = o;    o = al16(o + (size_t)maxR * M * tsz);
-  L.red = o;   o = al16(o + (size_t)3 * M * 2 * 8);
+  L.lred = o;  o = al16(o + (size_t)16 * M * 2 * 4);
+  L.red = o;   o = al16(o + (size_t)2 * kMaxCluster * M * 2 * 4);
   L.gs = o;    o = al16(o + (size_t)smem_rows * ldgs * tsz);
   L.total = o;
   return L;
 }
 
-template <typename T, int M>
-__global__ void __launch_bounds__(kIterThreads, 1) oem_iter_kernel(IterLaunch P) {
-  using U = unsigned int;
+template <typename T, int M, int NT>
+__global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
+  constexpr int NW = NT / 32;
   cg::cluster_group cluster = cg::this_cluster();
   const int C = P.C;
   const int rank = (int)cluster.block_rank();
@@ -182,7 +153,8 @@ __global__ void __launch_bounds__(kIterThreads, 1) oem_iter_kernel(IterLaunch P)
   T* cgr = reinterpret_cast<T*>(smem + Ls.cgr);
   int* glen = reinterpret_cast<int*>(smem + Ls.glen);
   T* st = reinterpret_cast<T*>(smem + Ls.st);
-  U* red = reinterpret_cast<U*>(smem + Ls.red);
+  float* lred = reinterpret_cast<float*>(smem + Ls.lred);  // [warp][2M]
+  float* red = reinterpret_cast<float*>(smem + Ls.red);    // [2][C][2M]
   T* Gs = reinterpret_cast<T*>(smem + Ls.gs);
 
   const T* Gglob = kF32 ? reinterpret_cast<const T*>(tk.G32) : reinterpret_cast<const T*>(tk.G64);
@@ -221,10 +193,10 @@ __global__ void __launch_bounds__(kIterThreads, 1) oem_iter_kernel(IterLaunch P)
   // ---- this warp's contiguous row block, aligned to allowed boundaries
   int wlo, whi;
   {
-    const int per = (R + kIterWarps - 1) / kIterWarps;
+    const int per = (R + NW - 1) / NW;
     auto bound = [&](int wi) {
       if (wi <= 0) return 0;
-      if (wi >= kIterWarps) return R;
+      if (wi >= NW) return R;
       int b = min(R, wi * per);
       if (tk.allowed) while (b < R && !tk.allowed[i0 + b]) ++b;
       return b;
@@ -234,7 +206,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) oem_iter_kernel(IterLaunch P)
   }
 
   // ---- initialise u, beta, weights, groups, the G rows kept in shared memory
-  for (int e = tid; e < M * maxR; e += kIterThreads) {
+  for (int e = tid; e < M * maxR; e += NT) {
     const int k = e / maxR, i = e % maxR;
     T hi = T(0), lo = T(0), wt = T(1), cgv = T(0), b0 = T(0);
     int gl = 0;
@@ -264,9 +236,9 @@ __global__ void __launch_bounds__(kIterThreads, 1) oem_iter_kernel(IterLaunch P)
     }
     uhi[e] = hi; ulo[e] = lo; bet[e] = b0; wv[e] = wt; cgr[e] = cgv; glen[e] = gl; gn[e] = T(0);
   }
-  for (int e = tid; e < 2 * p * M; e += kIterThreads) Dbuf[e] = T(0);
-  for (int e = tid; e < 3 * M * 2; e += kIterThreads) red[e] = (U)0;
-  for (int e = tid; e < tk.smem_rows * ldgs; e += kIterThreads) {
+  for (int e = tid; e < 2 * ldgs * M; e += NT) Dbuf[e] = T(0);
+  for (int e = tid; e < 2 * kMaxCluster * M * 2; e += NT) red[e] = 0.f;
+  for (int e = tid; e < tk.smem_rows * ldgs; e += NT) {
     const int i = e / ldgs, j = e % ldgs;
     Gs[e] = (i < R && j < p) ? Gglob[(size_t)(i0 + i) * ldgg + j] : T(0);
   }
@@ -280,7 +252,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) oem_iter_kernel(IterLaunch P)
   int t = 0;
   while (!all_done) {
     const int cur = t & 1, nxt = cur ^ 1;
-    const T* Dc = Dbuf + (size_t)cur * p * M;
+    const T* Dc = Dbuf + (size_t)cur * ldgs * M;
     // ---- 1. mat-vec on the warp's rows and the compensated u update
     if (!skip_mv) {
       for (int ib = wlo; ib < whi; ib += 2) {
@@ -290,12 +262,31 @@ __global__ void __launch_bounds__(kIterThreads, 1) oem_iter_kernel(IterLaunch P)
         T acc0[M], acc1[M];
 #pragma unroll
         for (int k = 0; k < M; ++k) { acc0[k] = T(0); acc1[k] = T(0); }
-        for (int j = lane; j < p; j += 32) {
-          T dv[M];
-          load_col<T, M>(Dc, j, dv);
-          const T ga = g0[j], gb = g1[j];
+        if constexpr (kF32) {
+          // four columns per lane per step (rows are zero-padded to ldgs)
+          for (int j = lane * 4; j < p; j += 128) {
+            const float4 ga = *reinterpret_cast<const float4*>(g0 + j);
+            const float4 gb = *reinterpret_cast<const float4*>(g1 + j);
+            const float gav[4] = {ga.x, ga.y, ga.z, ga.w}, gbv[4] = {gb.x, gb.y, gb.z, gb.w};
 #pragma unroll
-          for (int k = 0; k < M; ++k) { acc0[k] = fma(ga, dv[k], acc0[k]); acc1[k] = fma(gb, dv[k], acc1[k]); }
+            for (int q = 0; q < 4; ++q) {
+              T dv[M];
+              load_col<T, M>(Dc, j + q, dv);
+#pragma unroll
+              for (int k = 0; k < M; ++k) {
+                acc0[k] = fma(gav[q], dv[k], acc0[k]);
+                acc1[k] = fma(gbv[q], dv[k], acc1[k]);
+              }
+            }
+          }
+        } else {
+          for (int j = lane; j < p; j += 32) {
+            T dv[M];
+            load_col<T, M>(Dc, j, dv);
+            const T ga = g0[j], gb = g1[j];
+#pragma unroll
+            for (int k = 0; k < M; ++k) { acc0[k] = fma(ga, dv[k], acc0[k]); acc1[k] = fma(gb, dv[k], acc1[k]); }
+          }
         }
 #pragma unroll
         for (int k = 0; k < M; ++k) { acc0[k] = warp_sum(acc0[k]); acc1[k] = warp_sum(acc1[k]); }
@@ -303,13 +294,11 @@ __global__ void __launch_bounds__(kIterThreads, 1) oem_iter_kernel(IterLaunch P)
         if (lane < 2 * M) {
           const int rr = lane / M, k = lane % M;
           const int row = rr ? ib1 : ib;
-          T v = T(0);
+          T v = T(0), dkk = T(1);
 #pragma unroll
-          for (int kk = 0; kk < M; ++kk) if (kk == k) v = rr ? acc1[kk] : acc0[kk];
+          for (int kk = 0; kk < M; ++kk)
+            if (kk == k) { v = rr ? acc1[kk] : acc0[kk]; dkk = dk[kk]; }
           if (!(rr && ib1 == ib)) {
-            T dkk = T(1);
-#pragma unroll
-            for (int kk = 0; kk < M; ++kk) if (kk == k) dkk = dk[kk];
             const int idx = k * maxR + row;
             const T incr = fma(dkk, Dc[(size_t)(i0 + row) * M + k], -v);
             if (kF32) {
@@ -329,9 +318,10 @@ __global__ void __launch_bounds__(kIterThreads, 1) oem_iter_kernel(IterLaunch P)
       __syncwarp();
     }
     // ---- 2a. group norms ||u_g|| over the warp's rows
+    const int nr = whi - wlo;
     if (has_group) {
-      for (int e = lane; e < M * (whi - wlo); e += 32) {
-        const int k = e / (whi - wlo), i = wlo + e % (whi - wlo);
+      for (int e = lane; e < M * nr; e += 32) {
+        const int k = e / nr, i = wlo + e % nr;
         const int idx = k * maxR + i;
         const int len = glen[idx];
         if (len > 0) {
@@ -347,7 +337,6 @@ __global__ void __launch_bounds__(kIterThreads, 1) oem_iter_kernel(IterLaunch P)
     T mx_d[M], mx_b[M];
 #pragma unroll
     for (int k = 0; k < M; ++k) { mx_d[k] = T(0); mx_b[k] = T(0); }
-    const int nr = whi - wlo;
     for (int e = lane; e < M * nr; e += 32) {
       const int k = e / nr, i = wlo + e % nr;
       const int idx = k * maxR + i;
@@ -377,34 +366,55 @@ __global__ void __launch_bounds__(kIterThreads, 1) oem_iter_kernel(IterLaunch P)
       st[(size_t)i * M + k] = dn;
     }
     __syncwarp();
-    // ---- 3. DSMEM: dbeta rows to every CTA, maxima into every CTA's slot
+    // ---- 3. DSMEM: dbeta rows to every CTA; warp maxima to the block table
     {
-      T* Dn = Dbuf + (size_t)nxt * p * M;
+      T* Dn = Dbuf + (size_t)nxt * ldgs * M;
       for (int e = lane; e < nr * C; e += 32) {
         const int i = wlo + e / C, r = e % C;
         store_col<T, M>(cluster.map_shared_rank(Dn + (size_t)(i0 + i) * M, r), st + (size_t)i * M);
       }
 #pragma unroll
       for (int k = 0; k < M; ++k) { mx_d[k] = warp_max(mx_d[k]); mx_b[k] = warp_max(mx_b[k]); }
-      U* slot = red + (size_t)(t % 3) * M * 2;
-      for (int e = lane; e < C * M * 2; e += 32) {
-        const int r = e / (M * 2), q = e % (M * 2), k = q >> 1;
-        T val = T(0);
+      if (lane == 0) {
 #pragma unroll
-        for (int kk = 0; kk < M; ++kk) if (kk == k) val = (q & 1) ? mx_b[kk] : mx_d[kk];
-        if (val > T(0)) atomicMax(cluster.map_shared_rank(slot + q, r), max_bits(val));
+        for (int k = 0; k < M; ++k) {
+          lred[(warp * M + k) * 2] = to_red(mx_d[k]);
+          lred[(warp * M + k) * 2 + 1] = to_red(mx_b[k]);
+        }
+      }
+    }
+    __syncthreads();
+    // ---- 3b. warp 0: the block's maxima to every CTA's table, slot [rank]
+    if (warp == 0) {
+      float v = 0.f;
+      if (lane < 2 * M)
+        for (int w = 0; w < NW; ++w) v = fmax(v, lred[w * 2 * M + lane]);
+      float vals[2 * M];
+#pragma unroll
+      for (int q = 0; q < 2 * M; ++q) vals[q] = __shfl_sync(0xffffffffu, v, q);
+      if (lane < C) {
+        float* dst = cluster.map_shared_rank(red + ((size_t)nxt * kMaxCluster + rank) * 2 * M, lane);
+#pragma unroll
+        for (int q = 0; q < 2 * M; ++q) dst[q] = vals[q];
       }
     }
     cluster.sync();
     // ---- 4. decisions (every thread, same data, same result)
     {
-      const U* slot = red + (size_t)(t % 3) * M * 2;
+      // lane r < C holds CTA r's entries; reduce over the lanes
+      const float* tab = red + (size_t)nxt * kMaxCluster * 2 * M;
+      float mv[2 * M];
+#pragma unroll
+      for (int q = 0; q < 2 * M; ++q) {
+        float v = lane < C ? tab[lane * 2 * M + q] : 0.f;
+        mv[q] = warp_max(v);
+      }
       int anyd = 0;
       all_done = 1;
 #pragma unroll
       for (int k = 0; k < M; ++k) {
         if (k >= m || done[k]) continue;
-        const T md = from_bits(slot[2 * k], T(0)), mb = from_bits(slot[2 * k + 1], T(0));
+        const T md = (T)mv[2 * k], mb = (T)mv[2 * k + 1];
         if (md > T(0)) anyd = 1;
         const int it = ++its[k];
         const bool conv = md <= tol * fmax(T(1), mb);
@@ -426,8 +436,6 @@ __global__ void __launch_bounds__(kIterThreads, 1) oem_iter_kernel(IterLaunch P)
         all_done &= done[k];
       }
       skip_mv = !anyd;
-      // the slot read two iterations from now starts from zero
-      if (tid < M * 2) red[(size_t)((t + 2) % 3) * M * 2 + tid] = (U)0;
     }
     ++t;
     ++loops;
@@ -436,17 +444,31 @@ __global__ void __launch_bounds__(kIterThreads, 1) oem_iter_kernel(IterLaunch P)
   // ---- save the state for a later launch (serving): apply the pending dbeta
   if (tk.st_u) {
     if (!all_done && !skip_mv) {
-      const T* Dc = Dbuf + (size_t)(t & 1) * p * M;
+      const T* Dc = Dbuf + (size_t)(t & 1) * ldgs * M;
       for (int ib = wlo; ib < whi; ++ib) {
         const T* g0 = (ib < tk.smem_rows) ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
         T acc[M];
 #pragma unroll
         for (int k = 0; k < M; ++k) acc[k] = T(0);
-        for (int j = lane; j < p; j += 32) {
-          T dv[M];
-          load_col<T, M>(Dc, j, dv);
+        if constexpr (kF32) {
+          for (int j = lane * 4; j < p; j += 128) {
+            const float4 ga = *reinterpret_cast<const float4*>(g0 + j);
+            const float gav[4] = {ga.x, ga.y, ga.z, ga.w};
 #pragma unroll
-          for (int k = 0; k < M; ++k) acc[k] = fma(g0[j], dv[k], acc[k]);
+            for (int q = 0; q < 4; ++q) {
+              T dv[M];
+              load_col<T, M>(Dc, j + q, dv);
+#pragma unroll
+              for (int k = 0; k < M; ++k) acc[k] = fma(gav[q], dv[k], acc[k]);
+            }
+          }
+        } else {
+          for (int j = lane; j < p; j += 32) {
+            T dv[M];
+            load_col<T, M>(Dc, j, dv);
+#pragma unroll
+            for (int k = 0; k < M; ++k) acc[k] = fma(g0[j], dv[k], acc[k]);
+          }
         }
 #pragma unroll
         for (int k = 0; k < M; ++k) acc[k] = warp_sum(acc[k]);
@@ -507,14 +529,15 @@ size_t oem_iter_smem_per_row(int p, int precision) {
 
 template <typename T, int M>
 static cudaError_t launch_t(const IterLaunch& P, cudaStream_t s, bool query, int* out) {
-  auto kfn = oem_iter_kernel<T, M>;
+  constexpr int NT = iter_threads<T, M>();
+  auto kfn = oem_iter_kernel<T, M, NT>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(P.ntasks * P.C));
-  cfg.blockDim = dim3(kIterThreads);
+  cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = P.smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];

@@ -298,3 +298,47 @@ def serving_requests(num: int, seed: int, rate_per_s: float = 50.0,
             "gamma": 3.0, "nlambda": nlambda, "seed": int(seed * 100003 + i),
         })
     return reqs
+
+
+def ar1_coefficients(p: int, rho: float) -> np.ndarray:
+    """The p x p lower-triangular C with x = C e for the AR(rho) recurrence
+    x_1 = e_1, x_j = rho x_{j-1} + sqrt(1 - rho^2) e_j."""
+    s = math.sqrt(1.0 - rho * rho)
+    j = np.arange(p)
+    C = np.power(rho, np.maximum(j[:, None] - j[None, :], 0).astype(np.float64))
+    C = np.tril(C)
+    C[:, 1:] *= s
+    return C
+
+
+def device_ar1_base(n: int, p: int, rho: float, seed: int, device="cuda", chunk: int = 1 << 18):
+    """n x p float32 AR(rho) rows drawn on the GPU (torch), X = E C^T block by
+    block. Any row window and column prefix of it is again an AR(rho) sample."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    Ct = torch.from_numpy(ar1_coefficients(p, rho).T.copy()).to(device=device, dtype=torch.float32)
+    X = torch.empty((n, p), dtype=torch.float32, device=device)
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        E = torch.randn((r1 - r0, p), generator=g, device=device, dtype=torch.float32)
+        X[r0:r1] = E @ Ct
+    return X
+
+
+def device_request_data(base, req: dict, beta_head=(-0.5, -0.5, 0.5, 0.5, 1.0), sigma=2.0):
+    """X (a row window / column prefix view of a base matrix), y = X beta +
+    sigma eps and fold labels on the device for one serving request."""
+    import torch
+    n, p, K, seed = req["n"], req["p"], req["K"], req["seed"]
+    N = base.shape[0]
+    r0 = (seed * 7919) % max(1, N - n + 1)
+    X = base[r0:r0 + n, :p]
+    g = torch.Generator(device=base.device)
+    g.manual_seed(int(seed))
+    beta = torch.zeros(p, dtype=torch.float32, device=base.device)
+    h = torch.tensor(beta_head[:p], dtype=torch.float32, device=base.device)
+    beta[:h.numel()] = h
+    y = X @ beta + sigma * torch.randn(n, generator=g, device=base.device, dtype=torch.float32)
+    fold = torch.randint(0, K, (n,), generator=g, device=base.device, dtype=torch.uint8) if K else None
+    return X, y.contiguous(), fold
