@@ -413,13 +413,16 @@ inline int check_opts(oem_ctx* ctx, const oem_options* o) {
 
 // Row slices of p rows over a cluster of C CTAs: even boundaries moved forward
 // to the next row where a slice may start (group starts for group penalties).
+// Slice boundaries are multiples of 4 rows (the iteration kernel moves whole
+// 16-byte rows of 4 float32 between CTAs) and allowed rows (group starts).
 inline void make_slices(int64_t p, int C, const std::vector<char>& allowed, int32_t* slice, int* max_rows) {
   slice[0] = 0;
   slice[C] = (int32_t)p;
   for (int r = 1; r < C; ++r) {
     int64_t bnd = std::max<int64_t>(slice[r - 1], (p * r) / C);
-    while (bnd < p && !allowed[bnd]) ++bnd;
-    slice[r] = (int32_t)bnd;
+    bnd = (bnd + 3) & ~(int64_t)3;
+    while (bnd < p && (!allowed[bnd] || (bnd & 3))) ++bnd;
+    slice[r] = (int32_t)std::min<int64_t>(bnd, p);
   }
   int mr = 1;
   for (int r = 0; r < C; ++r) mr = std::max(mr, slice[r + 1] - slice[r]);

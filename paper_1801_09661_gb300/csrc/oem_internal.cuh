@@ -119,30 +119,26 @@ struct DevPenalty {
 // Scalar updates of Section 2.2 (Eqs. lasso, net, mcp, scad); wl = w_j lambda.
 template <typename T>
 __device__ __forceinline__ T thr_scalar(int kind, T u, T wl, T alpha, T gamma, T d) {
+  // Every branch is sign(u) num / den for one (num, den) pair and zero where
+  // |u| does not pass the threshold; the pair is chosen by selects, so lanes
+  // of a warp that hold different penalties do not diverge. In the regions
+  // |u| > gamma wl d (MCP) and |u| > (d + 1) wl (SCAD) the update is u / d
+  // and s > 0 holds there (gamma d > 1).
   const T au = fabs(u);
-  if (kind == OEM_LASSO) {
-    const T s = au - wl;
-    return s > T(0) ? copysign(s / d, u) : T(0);
-  }
+  const T s = au - (kind == OEM_ENET ? wl * alpha : wl);
+  T num = s, den = d;
   if (kind == OEM_ENET) {
-    const T s = au - wl * alpha;
-    return s > T(0) ? copysign(s / (d + wl * (T(1) - alpha)), u) : T(0);
-  }
-  if (kind == OEM_MCP) {
-    if (au <= wl * gamma * d) {
-      const T s = au - wl;
-      return s > T(0) ? copysign(gamma * s / (gamma * d - T(1)), u) : T(0);
+    den = d + wl * (T(1) - alpha);
+  } else if (kind == OEM_MCP) {
+    if (au <= wl * gamma * d) { num = gamma * s; den = gamma * d - T(1); }
+    else num = au;
+  } else if (kind == OEM_SCAD) {
+    if (au > (d + T(1)) * wl) {
+      if (au <= wl * gamma * d) { num = (gamma - T(1)) * au - wl * gamma; den = (gamma - T(1)) * d - T(1); }
+      else num = au;
     }
-    return u / d;
   }
-  // SCAD
-  if (au <= (d + T(1)) * wl) {
-    const T s = au - wl;
-    return s > T(0) ? copysign(s / d, u) : T(0);
-  }
-  if (au <= wl * gamma * d)
-    return copysign(((gamma - T(1)) * au - wl * gamma) / ((gamma - T(1)) * d - T(1)), u);
-  return u / d;
+  return s > T(0) ? copysign(num / den, u) : T(0);
 }
 
 // Plain form of the iteration (one launch per OEM iteration, one instance):

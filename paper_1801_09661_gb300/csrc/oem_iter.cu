@@ -13,19 +13,20 @@
 // slice[r+1]) of G, u and beta; inside the CTA every warp owns a contiguous
 // block of those rows (aligned to group starts for the group lasso). Per
 // iteration a warp, on its own rows and with no block-wide barrier:
-//   1. forms (G dbeta)_i for all instances of the task at once (G is read
-//      once for all of them; rows resident in shared memory, the rest read
-//      from L2) and updates u_i;
-//   2. thresholds (group norms first for group penalties) and forms the new
-//      dbeta_i;
+//   1. forms (G dbeta)_i for all instances of the task at once, 16 / M rows
+//      at a time so that one pass over dbeta serves the group (lane l reads
+//      columns l, l + 32, ...; G rows resident in shared memory, the rest read
+//      from L2); a reduce-scatter leaves each (row, instance) sum in one lane
+//      pair, which updates u_i and, without groups, applies the threshold;
+//   2. for group penalties, forms the group norms and thresholds afterwards;
 //   3. writes its dbeta rows into the shared memory of every CTA of the
-//      cluster (DSMEM).
-// The CTA then folds its warps' max|dbeta|, max|beta| (one block barrier)
-// and one warp stores the CTA's maxima into every CTA's reduction table
-// (DSMEM vector stores). One cluster barrier per iteration; then every warp
-// reduces the table and takes the same convergence decisions. A launch may
-// stop after a loop budget and save its state (serving), to be resumed by a
-// later launch.
+//      cluster (DSMEM stores) and its max|dbeta|, max|beta| per instance
+//      into the block's table.
+// One block barrier, then one warp stores the CTA's maxima into its entry of
+// every CTA's cluster table (DSMEM vector stores); one cluster barrier per
+// iteration; then every thread reduces the cluster table and takes the same
+// convergence decisions. A launch may stop after a loop
+// budget and save its state (serving), to be resumed by a later launch.
 #include "oem_internal.cuh"
 
 #include <cooperative_groups.h>
@@ -36,9 +37,11 @@ namespace oem {
 
 int oem_iter_mpad(int npen) { return npen <= 1 ? 1 : npen <= 2 ? 2 : npen <= 4 ? 4 : 8; }
 
-// Threads per CTA: 512 while the per-thread state is small, else 256.
+// Threads per CTA. Every warp reads the whole dbeta once per group of its
+// rows, so more warps than needed to spread a CTA's rows only add
+// shared-memory traffic.
 template <typename T, int M>
-constexpr int iter_threads() { return (sizeof(T) == 4 && M <= 4) ? 512 : 256; }
+constexpr int iter_threads() { return 256; }
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -51,6 +54,26 @@ __device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
+}
+
+// Reduce-scatter of 16 per-lane values over the warp: returns, in lane l,
+// the warp sum of value (l >> 1) & 15 (both lanes of a pair hold it). Each
+// level halves the values a lane keeps: 8 + 4 + 2 + 1 + 1 shuffles.
+template <typename T>
+__device__ __forceinline__ T reduce_scatter16(const T (&a)[16], int lane) {
+  T b8[8], b4[4], b2[2];
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    b8[q] = (h4 ? a[q + 8] : a[q]) + __shfl_xor_sync(0xffffffffu, h4 ? a[q] : a[q + 8], 16);
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    b4[q] = (h3 ? b8[q + 4] : b8[q]) + __shfl_xor_sync(0xffffffffu, h3 ? b8[q] : b8[q + 4], 8);
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+    b2[q] = (h2 ? b4[q + 2] : b4[q]) + __shfl_xor_sync(0xffffffffu, h2 ? b4[q] : b4[q + 2], 4);
+  T b1 = (h1 ? b2[1] : b2[0]) + __shfl_xor_sync(0xffffffffu, h1 ? b2[0] : b2[1], 2);
+  return b1 + __shfl_xor_sync(0xffffffffu, b1, 1);
 }
 
 // Load the M entries of row j of a [rows][M] buffer.
@@ -96,9 +119,9 @@ __device__ __forceinline__ void store_col(T* __restrict__ dst, const T* __restri
   }
 }
 
-// The reduction table holds float32 maxima; a float64 value is rounded up
-// first, so a max|dbeta| is never under-stated and no convergence is declared
-// early (max|beta| moves by at most 2^-24 relative).
+// The tables hold float32 maxima; a float64 value is rounded up first, so a
+// max|dbeta| is never under-stated and no convergence is declared early
+// (max|beta| moves by at most 2^-24 relative).
 __device__ __forceinline__ float to_red(float v) { return v; }
 __device__ __forceinline__ float to_red(double v) { return __double2float_ru(v); }
 
@@ -109,6 +132,7 @@ __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15
 struct IterSmem {
   size_t dbuf, uhi, ulo, beta, w, gn, cgr, glen, st, lred, red, gs, total;
 };
+constexpr int kIterMaxWarps = 16;
 __host__ __device__ inline IterSmem iter_smem_layout(int p, int M, int maxR, int tsz, int smem_rows) {
   const int ldgs = (p + 3) & ~3;
   IterSmem L;
@@ -122,7 +146,7 @@ __host__ __device__ inline IterSmem iter_smem_layout(int p, int M, int maxR, int
   L.cgr = o;   o = al16(o + (size_t)M * maxR * tsz);
   L.glen = o;  o = al16(o + (size_t)M * maxR * 4);
   L.st = o;    o = al16(o + (size_t)maxR * M * tsz);
-  L.lred = o;  o = al16(o + (size_t)16 * M * 2 * 4);
+  L.lred = o;  o = al16(o + (size_t)kIterMaxWarps * M * 2 * 4);
   L.red = o;   o = al16(o + (size_t)2 * kMaxCluster * M * 2 * 4);
   L.gs = o;    o = al16(o + (size_t)smem_rows * ldgs * tsz);
   L.total = o;
@@ -138,7 +162,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   const IterTask& tk = P.tasks[blockIdx.x / C];
   const int p = tk.p, L = tk.L, m = tk.npen, maxR = tk.max_rows;
   const int i0 = tk.slice[rank], R = tk.slice[rank + 1] - i0;
-  const int ldgs = (p + 3) & ~3;
+  const int ldgs = (p + 3) & ~3, smem_rows = tk.smem_rows;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr bool kF32 = sizeof(T) == 4;
 
@@ -153,10 +177,9 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   T* cgr = reinterpret_cast<T*>(smem + Ls.cgr);
   int* glen = reinterpret_cast<int*>(smem + Ls.glen);
   T* st = reinterpret_cast<T*>(smem + Ls.st);
-  float* lred = reinterpret_cast<float*>(smem + Ls.lred);  // [warp][2M]
-  float* red = reinterpret_cast<float*>(smem + Ls.red);    // [2][C][2M]
+  float* lred = reinterpret_cast<float*>(smem + Ls.lred);  // [warp][2M] block table
+  float* red = reinterpret_cast<float*>(smem + Ls.red);    // [2][rank][2M] cluster table
   T* Gs = reinterpret_cast<T*>(smem + Ls.gs);
-
   const T* Gglob = kF32 ? reinterpret_cast<const T*>(tk.G32) : reinterpret_cast<const T*>(tk.G64);
   const int ldgg = kF32 ? tk.ldg : p;
   const double* cb = tk.c;
@@ -238,11 +261,28 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   }
   for (int e = tid; e < 2 * ldgs * M; e += NT) Dbuf[e] = T(0);
   for (int e = tid; e < 2 * kMaxCluster * M * 2; e += NT) red[e] = 0.f;
-  for (int e = tid; e < tk.smem_rows * ldgs; e += NT) {
+  for (int e = tid; e < smem_rows * ldgs; e += NT) {
     const int i = e / ldgs, j = e % ldgs;
     Gs[e] = (i < R && j < p) ? Gglob[(size_t)(i0 + i) * ldgg + j] : T(0);
   }
   cluster.sync();  // every CTA initialised before any DSMEM access
+
+  // Lane roles in the row-group mat-vec: a group is RG = 16 / M rows; after
+  // the reduce-scatter, lane l holds the sum of value v = (l >> 1) & 15, i.e.
+  // row rsub = v / M of the group and instance kq = v % M (even lanes act).
+  constexpr int RG = 16 / M;
+  const int vq = (lane >> 1) & 15, rsub = vq / M, kq = vq % M;
+  const bool even = (lane & 1) == 0;
+  int my_kind = OEM_LASSO;
+  T my_alpha = T(1), my_gamma = T(3), my_d = T(1), my_lam = T(0);
+  int my_done = 1;
+#pragma unroll
+  for (int k = 0; k < M; ++k)
+    if (k == kq) {
+      my_kind = kind[k]; my_alpha = alpha[k]; my_gamma = gamma[k]; my_d = dk[k];
+      my_lam = lamv[k]; my_done = done[k];
+    }
+  const bool my_inst = kq < m;
 
   const T tol = (T)P.tol;
   int skip_mv = 1;      // dbeta of the previous iteration is all zero
@@ -253,161 +293,197 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   while (!all_done) {
     const int cur = t & 1, nxt = cur ^ 1;
     const T* Dc = Dbuf + (size_t)cur * ldgs * M;
-    // ---- 1. mat-vec on the warp's rows and the compensated u update
-    if (!skip_mv) {
-      for (int ib = wlo; ib < whi; ib += 2) {
-        const int ib1 = (ib + 1 < whi) ? ib + 1 : ib;
-        const T* g0 = (ib < tk.smem_rows) ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
-        const T* g1 = (ib1 < tk.smem_rows) ? Gs + (size_t)ib1 * ldgs : Gglob + (size_t)(i0 + ib1) * ldgg;
-        T acc0[M], acc1[M];
+    const int nr = whi - wlo;
+    T lmd = T(0), lmb = T(0);  // this lane's running max |dbeta|, |beta| (instance kq)
+    // ---- 1. per group of RG rows: y = G dbeta for all instances (one pass
+    // over dbeta for the group), u update and, without groups, the threshold
+    for (int gb = wlo; gb < whi; gb += RG) {
+      const int nv = min(RG, whi - gb);
+      T y = T(0);
+      if (!skip_mv) {
+        T acc[16];
 #pragma unroll
-        for (int k = 0; k < M; ++k) { acc0[k] = T(0); acc1[k] = T(0); }
-        if constexpr (kF32) {
-          // four columns per lane per step (rows are zero-padded to ldgs)
-          for (int j = lane * 4; j < p; j += 128) {
-            const float4 ga = *reinterpret_cast<const float4*>(g0 + j);
-            const float4 gb = *reinterpret_cast<const float4*>(g1 + j);
-            const float gav[4] = {ga.x, ga.y, ga.z, ga.w}, gbv[4] = {gb.x, gb.y, gb.z, gb.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              T dv[M];
-              load_col<T, M>(Dc, j + q, dv);
-#pragma unroll
-              for (int k = 0; k < M; ++k) {
-                acc0[k] = fma(gav[q], dv[k], acc0[k]);
-                acc1[k] = fma(gbv[q], dv[k], acc1[k]);
-              }
-            }
-          }
-        } else {
+        for (int q = 0; q < 16; ++q) acc[q] = T(0);
+        if (gb + nv <= smem_rows) {
+          const T* g0 = Gs + (size_t)gb * ldgs;
           for (int j = lane; j < p; j += 32) {
             T dv[M];
             load_col<T, M>(Dc, j, dv);
-            const T ga = g0[j], gb = g1[j];
 #pragma unroll
-            for (int k = 0; k < M; ++k) { acc0[k] = fma(ga, dv[k], acc0[k]); acc1[k] = fma(gb, dv[k], acc1[k]); }
+            for (int r = 0; r < RG; ++r) {
+              const T g = r < nv ? g0[(size_t)r * ldgs + j] : T(0);
+#pragma unroll
+              for (int k = 0; k < M; ++k) acc[r * M + k] = fma(g, dv[k], acc[r * M + k]);
+            }
           }
-        }
+        } else {
+          const T* gr[RG];
 #pragma unroll
-        for (int k = 0; k < M; ++k) { acc0[k] = warp_sum(acc0[k]); acc1[k] = warp_sum(acc1[k]); }
-        // lane l < 2M updates (row ib + l / M, instance l % M)
-        if (lane < 2 * M) {
-          const int rr = lane / M, k = lane % M;
-          const int row = rr ? ib1 : ib;
-          T v = T(0), dkk = T(1);
+          for (int r = 0; r < RG; ++r) {
+            const int ib = gb + min(r, nv - 1);
+            gr[r] = ib < smem_rows ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
+          }
+          for (int j = lane; j < p; j += 32) {
+            T dv[M];
+            load_col<T, M>(Dc, j, dv);
 #pragma unroll
-          for (int kk = 0; kk < M; ++kk)
-            if (kk == k) { v = rr ? acc1[kk] : acc0[kk]; dkk = dk[kk]; }
-          if (!(rr && ib1 == ib)) {
-            const int idx = k * maxR + row;
-            const T incr = fma(dkk, Dc[(size_t)(i0 + row) * M + k], -v);
-            if (kF32) {
-              const T h = uhi[idx];
-              const T s = h + incr, bb = s - h;
-              const T e = (h - (s - bb)) + (incr - bb);
-              const T lo = ulo[idx] + e;
-              const T hi2 = s + lo;
-              ulo[idx] = lo - (hi2 - s);
-              uhi[idx] = hi2;
-            } else {
-              uhi[idx] += incr;
+            for (int r = 0; r < RG; ++r) {
+              const T g = r < nv ? gr[r][j] : T(0);
+#pragma unroll
+              for (int k = 0; k < M; ++k) acc[r * M + k] = fma(g, dv[k], acc[r * M + k]);
             }
           }
         }
+        y = reduce_scatter16(acc, lane);
       }
-      __syncwarp();
+      const int i = gb + rsub;  // this lane's row (local index)
+      if (even && i < whi) {
+        const int idx = kq * maxR + i;
+        if (my_inst && !skip_mv) {
+          const T incr = fma(my_d, Dc[(size_t)(i0 + i) * M + kq], -y);
+          if (kF32) {
+            const T h = uhi[idx];
+            const T s1 = h + incr, bb = s1 - h;
+            const T e = (h - (s1 - bb)) + (incr - bb);
+            const T lo = ulo[idx] + e;
+            const T hi2 = s1 + lo;
+            ulo[idx] = lo - (hi2 - s1);
+            uhi[idx] = hi2;
+          } else {
+            uhi[idx] += incr;
+          }
+        }
+        if (!has_group) {
+          T dn = T(0);
+          if (my_inst) {
+            if (!my_done) {
+              const T bn = thr_scalar<T>(my_kind, uhi[idx], wv[idx] * my_lam, my_alpha, my_gamma, my_d);
+              dn = bn - bet[idx];
+              bet[idx] = bn;
+              lmd = fmax(lmd, fabs(dn));
+              lmb = fmax(lmb, fabs(bn));
+            } else {
+              lmb = fmax(lmb, fabs(bet[idx]));
+            }
+          }
+          st[(size_t)i * M + kq] = dn;
+        }
+      }
     }
-    // ---- 2a. group norms ||u_g|| over the warp's rows
-    const int nr = whi - wlo;
+    __syncwarp();
     if (has_group) {
+      // ---- 2a. group norms ||u_g|| over the warp's rows
       for (int e = lane; e < M * nr; e += 32) {
         const int k = e / nr, i = wlo + e % nr;
         const int idx = k * maxR + i;
         const int len = glen[idx];
         if (len > 0) {
-          T s = T(0);
-          for (int q = 0; q < len; ++q) s = fma(uhi[idx + q], uhi[idx + q], s);
-          s = sqrt(s);
-          for (int q = 0; q < len; ++q) gn[idx + q] = s;
+          T s2 = T(0);
+          for (int q = 0; q < len; ++q) s2 = fma(uhi[idx + q], uhi[idx + q], s2);
+          s2 = sqrt(s2);
+          for (int q = 0; q < len; ++q) gn[idx + q] = s2;
         }
       }
       __syncwarp();
-    }
-    // ---- 2b. thresholds and the new dbeta (rows of this warp)
-    T mx_d[M], mx_b[M];
+      // ---- 2b. thresholds and the new dbeta (rows of this warp)
+      T mx_d[M], mx_b[M];
 #pragma unroll
-    for (int k = 0; k < M; ++k) { mx_d[k] = T(0); mx_b[k] = T(0); }
-    for (int e = lane; e < M * nr; e += 32) {
-      const int k = e / nr, i = wlo + e % nr;
-      const int idx = k * maxR + i;
-      T dn = T(0);
+      for (int k = 0; k < M; ++k) { mx_d[k] = T(0); mx_b[k] = T(0); }
+      for (int e = lane; e < M * nr; e += 32) {
+        const int k = e / nr, i = wlo + e % nr;
+        const int idx = k * maxR + i;
+        T dn = T(0);
 #pragma unroll
-      for (int kk = 0; kk < M; ++kk) {
-        if (kk == k) {
-          if (!done[kk]) {
-            const T u = uhi[idx];
-            T bn;
-            if (kind[kk] == OEM_GROUP_LASSO) {
-              const T nrm = gn[idx];
-              const T f = nrm > T(0) ? T(1) - cgr[idx] * lamv[kk] / nrm : T(0);
-              bn = f > T(0) ? u / dk[kk] * f : T(0);
+        for (int kk = 0; kk < M; ++kk) {
+          if (kk == k && kk < m) {
+            if (!done[kk]) {
+              const T u = uhi[idx];
+              T bn;
+              if (kind[kk] == OEM_GROUP_LASSO) {
+                const T nrm = gn[idx];
+                const T f = nrm > T(0) ? T(1) - cgr[idx] * lamv[kk] / nrm : T(0);
+                bn = f > T(0) ? u / dk[kk] * f : T(0);
+              } else {
+                bn = thr_scalar<T>(kind[kk], u, wv[idx] * lamv[kk], alpha[kk], gamma[kk], dk[kk]);
+              }
+              dn = bn - bet[idx];
+              bet[idx] = bn;
+              mx_d[kk] = fmax(mx_d[kk], fabs(dn));
+              mx_b[kk] = fmax(mx_b[kk], fabs(bn));
             } else {
-              bn = thr_scalar<T>(kind[kk], u, wv[idx] * lamv[kk], alpha[kk], gamma[kk], dk[kk]);
+              mx_b[kk] = fmax(mx_b[kk], fabs(bet[idx]));
             }
-            dn = bn - bet[idx];
-            bet[idx] = bn;
-            mx_d[kk] = fmax(mx_d[kk], fabs(dn));
-            mx_b[kk] = fmax(mx_b[kk], fabs(bn));
-          } else {
-            mx_b[kk] = fmax(mx_b[kk], fabs(bet[idx]));
           }
         }
+        st[(size_t)i * M + k] = dn;
       }
-      st[(size_t)i * M + k] = dn;
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        const T a1 = warp_max(mx_d[k]), a2 = warp_max(mx_b[k]);
+        if (k == kq) { lmd = a1; lmb = a2; }
+      }
+      __syncwarp();
     }
-    __syncwarp();
-    // ---- 3. DSMEM: dbeta rows to every CTA; warp maxima to the block table
+    // ---- 3. DSMEM: dbeta rows to every CTA, maxima into every CTA's slot
     {
       T* Dn = Dbuf + (size_t)nxt * ldgs * M;
       for (int e = lane; e < nr * C; e += 32) {
         const int i = wlo + e / C, r = e % C;
         store_col<T, M>(cluster.map_shared_rank(Dn + (size_t)(i0 + i) * M, r), st + (size_t)i * M);
       }
+      // instance kq's warp maxima end in lane 2 kq (lanes of one instance
+      // differ in the row bits 2M .. 16 of the lane index)
 #pragma unroll
-      for (int k = 0; k < M; ++k) { mx_d[k] = warp_max(mx_d[k]); mx_b[k] = warp_max(mx_b[k]); }
-      if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < M; ++k) {
-          lred[(warp * M + k) * 2] = to_red(mx_d[k]);
-          lred[(warp * M + k) * 2 + 1] = to_red(mx_b[k]);
-        }
+      for (int o = 2 * M; o < 32; o <<= 1) {
+        lmd = fmax(lmd, __shfl_xor_sync(0xffffffffu, lmd, o));
+        lmb = fmax(lmb, __shfl_xor_sync(0xffffffffu, lmb, o));
+      }
+      if (even && rsub == 0) {
+        lred[(warp * M + kq) * 2] = to_red(lmd);
+        lred[(warp * M + kq) * 2 + 1] = to_red(lmb);
       }
     }
     __syncthreads();
-    // ---- 3b. warp 0: the block's maxima to every CTA's table, slot [rank]
+    // ---- 3b. warp 0: the block's maxima into entry [rank] of every CTA's
+    // cluster table (buffer t & 1; rewritten two iterations later, after the
+    // next cluster barrier, when every CTA has read it)
     if (warp == 0) {
+      constexpr int E = 2 * M;  // floats per entry
       float v = 0.f;
-      if (lane < 2 * M)
-        for (int w = 0; w < NW; ++w) v = fmax(v, lred[w * 2 * M + lane]);
-      float vals[2 * M];
-#pragma unroll
-      for (int q = 0; q < 2 * M; ++q) vals[q] = __shfl_sync(0xffffffffu, v, q);
-      if (lane < C) {
-        float* dst = cluster.map_shared_rank(red + ((size_t)nxt * kMaxCluster + rank) * 2 * M, lane);
-#pragma unroll
-        for (int q = 0; q < 2 * M; ++q) dst[q] = vals[q];
+      if (lane < E)
+        for (int w = 0; w < NW; ++w) v = fmax(v, lred[w * E + lane]);
+      float* ent = red + ((size_t)(t & 1) * kMaxCluster + rank) * E;
+      if constexpr (E >= 4) {
+        // lane l: peer l / (E / 4), float4 part l % (E / 4)
+        constexpr int V = E / 4;
+        for (int base = 0; base < C * V; base += 32) {
+          const int e = base + lane, part = e % V;
+          float4 q4;
+          q4.x = __shfl_sync(0xffffffffu, v, 4 * part);
+          q4.y = __shfl_sync(0xffffffffu, v, 4 * part + 1);
+          q4.z = __shfl_sync(0xffffffffu, v, 4 * part + 2);
+          q4.w = __shfl_sync(0xffffffffu, v, 4 * part + 3);
+          if (e < C * V)
+            *reinterpret_cast<float4*>(cluster.map_shared_rank(ent + 4 * part, e / V)) = q4;
+        }
+      } else {
+        float2 q2;
+        q2.x = __shfl_sync(0xffffffffu, v, 0);
+        q2.y = __shfl_sync(0xffffffffu, v, 1);
+        if (lane < C) *reinterpret_cast<float2*>(cluster.map_shared_rank(ent, lane)) = q2;
       }
     }
     cluster.sync();
     // ---- 4. decisions (every thread, same data, same result)
     {
-      // lane r < C holds CTA r's entries; reduce over the lanes
-      const float* tab = red + (size_t)nxt * kMaxCluster * 2 * M;
-      float mv[2 * M];
+      constexpr int E = 2 * M;
+      const float* tab = red + (size_t)(t & 1) * kMaxCluster * E;
+      float mv[E];
 #pragma unroll
-      for (int q = 0; q < 2 * M; ++q) {
-        float v = lane < C ? tab[lane * 2 * M + q] : 0.f;
-        mv[q] = warp_max(v);
+      for (int q = 0; q < E; ++q) mv[q] = 0.f;
+      for (int r = 0; r < C; ++r) {
+#pragma unroll
+        for (int q = 0; q < E; ++q) mv[q] = fmax(mv[q], tab[r * E + q]);
       }
       int anyd = 0;
       all_done = 1;
@@ -436,6 +512,9 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
         all_done &= done[k];
       }
       skip_mv = !anyd;
+#pragma unroll
+      for (int k = 0; k < M; ++k)
+        if (k == kq) { my_lam = lamv[k]; my_done = done[k]; }
     }
     ++t;
     ++loops;
@@ -446,29 +525,18 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
     if (!all_done && !skip_mv) {
       const T* Dc = Dbuf + (size_t)(t & 1) * ldgs * M;
       for (int ib = wlo; ib < whi; ++ib) {
-        const T* g0 = (ib < tk.smem_rows) ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
+        const T* g0 = (ib < smem_rows) ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
         T acc[M];
 #pragma unroll
         for (int k = 0; k < M; ++k) acc[k] = T(0);
-        if constexpr (kF32) {
-          for (int j = lane * 4; j < p; j += 128) {
-            const float4 ga = *reinterpret_cast<const float4*>(g0 + j);
-            const float gav[4] = {ga.x, ga.y, ga.z, ga.w};
+        // same column order and lane tree as the loop's mat-vec, so a resumed
+        // path is the same as an uninterrupted one
+        for (int j = lane; j < p; j += 32) {
+          T dv[M];
+          load_col<T, M>(Dc, j, dv);
+          const T g = g0[j];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              T dv[M];
-              load_col<T, M>(Dc, j + q, dv);
-#pragma unroll
-              for (int k = 0; k < M; ++k) acc[k] = fma(gav[q], dv[k], acc[k]);
-            }
-          }
-        } else {
-          for (int j = lane; j < p; j += 32) {
-            T dv[M];
-            load_col<T, M>(Dc, j, dv);
-#pragma unroll
-            for (int k = 0; k < M; ++k) acc[k] = fma(g0[j], dv[k], acc[k]);
-          }
+          for (int k = 0; k < M; ++k) acc[k] = fma(g, dv[k], acc[k]);
         }
 #pragma unroll
         for (int k = 0; k < M; ++k) acc[k] = warp_sum(acc[k]);
