@@ -22,11 +22,12 @@
 //   3. writes its dbeta rows into the shared memory of every CTA of the
 //      cluster (DSMEM stores) and its max|dbeta|, max|beta| per instance
 //      into the block's table.
-// One block barrier, then one warp stores the CTA's maxima into its entry of
-// every CTA's cluster table (DSMEM vector stores); one cluster barrier per
-// iteration; then every thread reduces the cluster table and takes the same
-// convergence decisions. A launch may stop after a loop
-// budget and save its state (serving), to be resumed by a later launch.
+// One block barrier, then one warp folds the CTA's maxima into every CTA's
+// reduction slot (DSMEM atomic max on order-preserving 32-bit images, one
+// per peer and value); one cluster barrier per iteration; then every thread
+// takes the same convergence decisions from the same slot. A launch may stop
+// after a loop budget and save its state (serving), to be resumed by a later
+// launch.
 #include "oem_internal.cuh"
 
 #include <cooperative_groups.h>
@@ -119,11 +120,14 @@ __device__ __forceinline__ void store_col(T* __restrict__ dst, const T* __restri
   }
 }
 
-// The tables hold float32 maxima; a float64 value is rounded up first, so a
-// max|dbeta| is never under-stated and no convergence is declared early
-// (max|beta| moves by at most 2^-24 relative).
+// Order-preserving 32-bit images of non-negative maxima for the block table
+// and the DSMEM atomic max (32-bit atomics only across the cluster). A
+// float64 value is rounded up to float32 first, so a max|dbeta| is never
+// under-stated and no convergence is declared early; max|beta| moves by at
+// most 2^-24 relative.
 __device__ __forceinline__ float to_red(float v) { return v; }
 __device__ __forceinline__ float to_red(double v) { return __double2float_ru(v); }
+__device__ __forceinline__ float from_red(unsigned int b) { return __uint_as_float(b); }
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -147,7 +151,7 @@ __host__ __device__ inline IterSmem iter_smem_layout(int p, int M, int maxR, int
   L.glen = o;  o = al16(o + (size_t)M * maxR * 4);
   L.st = o;    o = al16(o + (size_t)maxR * M * tsz);
   L.lred = o;  o = al16(o + (size_t)kIterMaxWarps * M * 2 * 4);
-  L.red = o;   o = al16(o + (size_t)2 * kMaxCluster * M * 2 * 4);
+  L.red = o;   o = al16(o + (size_t)3 * M * 2 * 4);
   L.gs = o;    o = al16(o + (size_t)smem_rows * ldgs * tsz);
   L.total = o;
   return L;
@@ -178,7 +182,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   int* glen = reinterpret_cast<int*>(smem + Ls.glen);
   T* st = reinterpret_cast<T*>(smem + Ls.st);
   float* lred = reinterpret_cast<float*>(smem + Ls.lred);  // [warp][2M] block table
-  float* red = reinterpret_cast<float*>(smem + Ls.red);    // [2][rank][2M] cluster table
+  unsigned int* red = reinterpret_cast<unsigned int*>(smem + Ls.red);  // [3][2M] slots
   T* Gs = reinterpret_cast<T*>(smem + Ls.gs);
   const T* Gglob = kF32 ? reinterpret_cast<const T*>(tk.G32) : reinterpret_cast<const T*>(tk.G64);
   const int ldgg = kF32 ? tk.ldg : p;
@@ -260,7 +264,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
     uhi[e] = hi; ulo[e] = lo; bet[e] = b0; wv[e] = wt; cgr[e] = cgv; glen[e] = gl; gn[e] = T(0);
   }
   for (int e = tid; e < 2 * ldgs * M; e += NT) Dbuf[e] = T(0);
-  for (int e = tid; e < 2 * kMaxCluster * M * 2; e += NT) red[e] = 0.f;
+  for (int e = tid; e < 3 * M * 2; e += NT) red[e] = 0u;
   for (int e = tid; e < smem_rows * ldgs; e += NT) {
     const int i = e / ldgs, j = e % ldgs;
     Gs[e] = (i < R && j < p) ? Gglob[(size_t)(i0 + i) * ldgg + j] : T(0);
@@ -444,53 +448,31 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
       }
     }
     __syncthreads();
-    // ---- 3b. warp 0: the block's maxima into entry [rank] of every CTA's
-    // cluster table (buffer t & 1; rewritten two iterations later, after the
-    // next cluster barrier, when every CTA has read it)
+    // ---- 3b. warp 0: the block's maxima into slot t % 3 of every CTA (the
+    // slot is zeroed after its decisions, two iterations before its reuse)
     if (warp == 0) {
-      constexpr int E = 2 * M;  // floats per entry
+      constexpr int E = 2 * M;  // values per slot
       float v = 0.f;
       if (lane < E)
         for (int w = 0; w < NW; ++w) v = fmax(v, lred[w * E + lane]);
-      float* ent = red + ((size_t)(t & 1) * kMaxCluster + rank) * E;
-      if constexpr (E >= 4) {
-        // lane l: peer l / (E / 4), float4 part l % (E / 4)
-        constexpr int V = E / 4;
-        for (int base = 0; base < C * V; base += 32) {
-          const int e = base + lane, part = e % V;
-          float4 q4;
-          q4.x = __shfl_sync(0xffffffffu, v, 4 * part);
-          q4.y = __shfl_sync(0xffffffffu, v, 4 * part + 1);
-          q4.z = __shfl_sync(0xffffffffu, v, 4 * part + 2);
-          q4.w = __shfl_sync(0xffffffffu, v, 4 * part + 3);
-          if (e < C * V)
-            *reinterpret_cast<float4*>(cluster.map_shared_rank(ent + 4 * part, e / V)) = q4;
-        }
-      } else {
-        float2 q2;
-        q2.x = __shfl_sync(0xffffffffu, v, 0);
-        q2.y = __shfl_sync(0xffffffffu, v, 1);
-        if (lane < C) *reinterpret_cast<float2*>(cluster.map_shared_rank(ent, lane)) = q2;
+      unsigned int* slot = red + (size_t)(t % 3) * E;
+      for (int base = 0; base < C * E; base += 32) {
+        const int e = base + lane, q = e % E;
+        const float val = __shfl_sync(0xffffffffu, v, q);
+        if (e < C * E && val > 0.f)
+          atomicMax(cluster.map_shared_rank(slot + q, e / E), __float_as_uint(val));
       }
     }
     cluster.sync();
     // ---- 4. decisions (every thread, same data, same result)
     {
-      constexpr int E = 2 * M;
-      const float* tab = red + (size_t)(t & 1) * kMaxCluster * E;
-      float mv[E];
-#pragma unroll
-      for (int q = 0; q < E; ++q) mv[q] = 0.f;
-      for (int r = 0; r < C; ++r) {
-#pragma unroll
-        for (int q = 0; q < E; ++q) mv[q] = fmax(mv[q], tab[r * E + q]);
-      }
+      const unsigned int* slot = red + (size_t)(t % 3) * M * 2;
       int anyd = 0;
       all_done = 1;
 #pragma unroll
       for (int k = 0; k < M; ++k) {
         if (k >= m || done[k]) continue;
-        const T md = (T)mv[2 * k], mb = (T)mv[2 * k + 1];
+        const T md = (T)from_red(slot[2 * k]), mb = (T)from_red(slot[2 * k + 1]);
         if (md > T(0)) anyd = 1;
         const int it = ++its[k];
         const bool conv = md <= tol * fmax(T(1), mb);
@@ -515,6 +497,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
 #pragma unroll
       for (int k = 0; k < M; ++k)
         if (k == kq) { my_lam = lamv[k]; my_done = done[k]; }
+      if (tid < M * 2) red[(size_t)((t + 2) % 3) * M * 2 + tid] = 0u;
     }
     ++t;
     ++loops;
