@@ -110,6 +110,17 @@ typedef struct oem_options {
   int32_t iter_precision;   /* OEM_ITER_F32 (default) or OEM_ITER_F64 */
   int32_t cluster_ctas;     /* CTAs cooperating on one Gram in the iteration
                                (0 = chosen by the library; else 1,2,4,8,16) */
+  int32_t instances_per_task; /* penalties of one Gram iterated together by
+                               one cluster (0 = chosen by the library; else
+                               1,2,4,8); results do not depend on it */
+  int32_t autotune;         /* 1 (default): when cluster_ctas and
+                               instances_per_task are both 0, the first call
+                               for a new (p, Grams, penalties, precision)
+                               shape times the candidate layouts for a few
+                               iterations on its own inputs (synchronising the
+                               stream once) and the context keeps the fastest;
+                               skipped while the stream is being captured.
+                               0: the library's fixed rule */
 } oem_options;
 
 /* Fill *opt with the defaults listed above. */

@@ -58,7 +58,8 @@ class oem_options(C.Structure):
                 ("lambdas", C.POINTER(C.c_double)), ("tol", C.c_double),
                 ("max_iter", C.c_int64), ("lanczos_steps", C.c_int32),
                 ("gram_mode", C.c_int32), ("iter_precision", C.c_int32),
-                ("cluster_ctas", C.c_int32)]
+                ("cluster_ctas", C.c_int32), ("instances_per_task", C.c_int32),
+                ("autotune", C.c_int32)]
 
 
 class oem_job(C.Structure):
@@ -165,7 +166,8 @@ class _PenArray:
 
 
 def make_options(nlambda=100, lambda_min_ratio=1e-3, lambdas=None, tol=1e-7, max_iter=10000,
-                 lanczos_steps=64, gram_mode="auto", iter_precision="f32", cluster_ctas=0):
+                 lanczos_steps=64, gram_mode="auto", iter_precision="f32", cluster_ctas=0,
+                 instances_per_task=0, autotune=True):
     o = oem_options()
     lib.oem_options_default(C.byref(o))
     o.nlambda = int(nlambda)
@@ -180,6 +182,8 @@ def make_options(nlambda=100, lambda_min_ratio=1e-3, lambdas=None, tol=1e-7, max
     o.gram_mode = MODE[gram_mode] if isinstance(gram_mode, str) else int(gram_mode)
     o.iter_precision = OEM_ITER_F64 if iter_precision == "f64" else OEM_ITER_F32
     o.cluster_ctas = int(cluster_ctas)
+    o.instances_per_task = int(instances_per_task)
+    o.autotune = 1 if autotune else 0
     o._keep = keep
     return o
 

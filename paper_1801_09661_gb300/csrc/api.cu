@@ -25,6 +25,8 @@ void oem_options_default(oem_options* o) {
   o->gram_mode = OEM_GRAM_AUTO;
   o->iter_precision = OEM_ITER_F32;
   o->cluster_ctas = 0;
+  o->instances_per_task = 0;
+  o->autotune = 1;
 }
 
 int oem_create(oem_ctx** out, int device, size_t budget) {

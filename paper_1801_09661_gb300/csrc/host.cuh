@@ -6,10 +6,12 @@
 #include "oem_internal.cuh"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <vector>
 
 using namespace oem;
@@ -31,6 +33,10 @@ struct oem_ctx {
   std::vector<Pending> pending;
   double prof_ms[OEM_PROF_NKERNELS] = {0};
   int64_t prof_n[OEM_PROF_NKERNELS] = {0};
+  // iteration layouts chosen by timing, per (p, Grams, penalties, precision,
+  // groups): cluster CTAs and instances per task
+  std::map<std::array<int64_t, 5>, std::pair<int, int>> iter_tuned;
+  int64_t tune_runs = 0;
 };
 
 namespace oem {
@@ -408,6 +414,11 @@ inline int check_opts(oem_ctx* ctx, const oem_options* o) {
   const int c = o->cluster_ctas;
   if (!(c == 0 || c == 1 || c == 2 || c == 4 || c == 8 || c == 16))
     return fail(ctx, OEM_EINVAL, "cluster_ctas=%d not in {0,1,2,4,8,16}", c);
+  const int g = o->instances_per_task;
+  if (!(g == 0 || g == 1 || g == 2 || g == 4 || g == 8))
+    return fail(ctx, OEM_EINVAL, "instances_per_task=%d not in {0,1,2,4,8}", g);
+  if (o->autotune != 0 && o->autotune != 1)
+    return fail(ctx, OEM_EINVAL, "autotune=%d not in {0,1}", o->autotune);
   return OEM_OK;
 }
 
@@ -434,33 +445,25 @@ constexpr size_t kIterSmemCap = 227 * 1024;
 // Iteration launch plan for B tasks of the same shape (a fit or the K+1
 // Grams of a cross validation): cluster size, slices, shared memory.
 struct IterPlan {
-  int C = 1, M = 1, max_rows = 0, smem_rows = 0;
+  int C = 1, M = 1, Mg = 1, max_rows = 0, smem_rows = 0;
   size_t smem = 0;
   int32_t slice[kMaxCluster + 1] = {0};
   bool groups = false;
+  bool tune = false;      // time the candidate layouts at the first run
+  int max_tasks = 0;      // task-table capacity (B x npen)
   IterTask* d_tasks = nullptr;
   uint8_t* d_allowed = nullptr;
 };
 
-inline int plan_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, const oem_options* o, IterPlan& I) {
-  const int prec = o->iter_precision;
-  I.M = oem_iter_mpad(P.npen);
-  I.groups = false;
-  for (int i = 0; i < P.npen; ++i) I.groups |= P.host[i].kind == OEM_GROUP_LASSO;
-  int C;
-  if (o->cluster_ctas > 0) {
-    C = o->cluster_ctas;
-  } else {
-    // about 32 rows per CTA, at most 16 CTAs, and the clusters of all B Grams
-    // resident at once
-    const int want = (int)std::min<int64_t>(16, std::max<int64_t>(1, (p + 31) / 32));
-    const int byB = std::max(1, ctx->num_sms / std::max(1, B));
-    C = 1;
-    while (C * 2 <= std::min(want, byB) && C < 16) C *= 2;
-  }
+// Cluster size C and Mg instances per task for B Grams of npen instances;
+// returns OEM_OK with the shared-memory plan, or an error when nothing fits.
+inline int layout_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, int prec, int C, int Mg,
+                       IterPlan& I) {
+  I.Mg = Mg;
+  I.M = oem_iter_mpad(Mg);
   for (;; C /= 2) {
     make_slices(p, C, P.allowed, I.slice, &I.max_rows);
-    const size_t fixed = oem_iter_smem_fixed((int)p, P.npen, I.max_rows, prec);
+    const size_t fixed = oem_iter_smem_fixed((int)p, Mg, I.max_rows, prec);
     if (fixed + 1024 > kIterSmemCap)
       return fail(ctx, OEM_EUNSUPPORTED, "p=%lld too large for the iteration kernel", (long long)p);
     const size_t per = oem_iter_smem_per_row((int)p, prec);
@@ -468,15 +471,140 @@ inline int plan_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, const oem
     I.smem = fixed + (size_t)I.smem_rows * per;
     I.C = C;
     IterLaunch probe{};
-    probe.ntasks = B; probe.C = C; probe.M = I.M; probe.precision = prec; probe.smem = I.smem;
+    probe.ntasks = B * ((P.npen + Mg - 1) / Mg); probe.C = C; probe.M = I.M; probe.precision = prec;
+    probe.smem = I.smem;
     if (oem_iter_max_cluster(probe) >= 1) return OEM_OK;
     if (C == 1) return fail(ctx, OEM_ECUDA, "no cluster configuration of the iteration kernel fits");
   }
 }
 
+inline std::array<int64_t, 5> tune_key(int64_t p, int B, const PenPlan& P, int prec, bool groups) {
+  return {p, (int64_t)B, (int64_t)P.npen, (int64_t)prec, (int64_t)groups};
+}
+
+// Default layout: about 32 rows per CTA (at most 16 CTAs per cluster, and the
+// clusters of all B Grams resident at once), then the fewest instances per
+// task whose clusters all fit on the device at once (more clusters share the
+// work of one Gram; each iterates fewer instances per step).
+inline int plan_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, const oem_options* o, IterPlan& I) {
+  const int prec = o->iter_precision;
+  I.groups = false;
+  for (int i = 0; i < P.npen; ++i) I.groups |= P.host[i].kind == OEM_GROUP_LASSO;
+  I.max_tasks = B * P.npen;
+  int C = o->cluster_ctas;
+  if (C <= 0) {
+    const int want = (int)std::min<int64_t>(16, std::max<int64_t>(1, (p + 31) / 32));
+    const int byB = std::max(1, ctx->num_sms / std::max(1, B));
+    C = 1;
+    while (C * 2 <= std::min(want, byB) && C < 16) C *= 2;
+  }
+  int Mg = o->instances_per_task;
+  if (Mg <= 0) {
+    Mg = oem_iter_mpad(P.npen);
+    while (Mg > 1 && (int64_t)B * ((P.npen + Mg / 2 - 1) / (Mg / 2)) * C <= ctx->num_sms) Mg /= 2;
+  }
+  Mg = std::min(Mg, std::max(1, P.npen));
+  auto it = ctx->iter_tuned.find(tune_key(p, B, P, prec, I.groups));
+  I.tune = false;
+  if (o->autotune && o->cluster_ctas <= 0 && o->instances_per_task <= 0) {
+    if (it != ctx->iter_tuned.end()) { C = it->second.first; Mg = it->second.second; }
+    else I.tune = true;
+  }
+  return layout_iter(ctx, p, B, P, prec, C, Mg, I);
+}
+
 inline void iter_request(Arena& A, int64_t p, int B, IterPlan& I) {
-  A.add(&I.d_tasks, (size_t)B);
+  A.add(&I.d_tasks, (size_t)std::max(B, I.max_tasks));
   if (I.groups) A.add(&I.d_allowed, (size_t)p + 1);
+}
+
+// Launch the iteration for B Grams with the layout in I (task table written
+// on stream s); max_loops > 0 stops every task after that many iterations.
+inline int launch_iter_layout(oem_ctx* ctx, int64_t p, int B, const float* G32, int ldg,
+                              const double* G64, const double* c, const double* d,
+                              const double* lam, PenPlan& P, const oem_options* o, IterPlan& I,
+                              double* beta, int32_t* iters, uint8_t* conv, int64_t max_loops,
+                              std::vector<IterTask>& tasks, cudaStream_t s) {
+  const int L = o->nlambda, npen = P.npen, Mg = I.Mg;
+  const int S = (npen + Mg - 1) / Mg;
+  tasks.assign((size_t)B * S, IterTask{});
+  for (int b = 0; b < B; ++b)
+    for (int q = 0; q < S; ++q) {
+      IterTask& t = tasks[(size_t)b * S + q];
+      const int k0 = q * Mg;
+      t.p = (int)p; t.npen = std::min(Mg, npen - k0); t.L = L; t.ldg = ldg;
+      t.max_rows = I.max_rows; t.smem_rows = I.smem_rows; t.resume = 0;
+      for (int r = 0; r <= kMaxCluster; ++r) t.slice[r] = r <= I.C ? I.slice[r] : (int32_t)p;
+      t.G32 = G32 ? G32 + (size_t)b * p * ldg : nullptr;
+      t.G64 = G64 ? G64 + (size_t)b * p * p : nullptr;
+      t.c = c + (size_t)b * p;
+      t.d = d + b;
+      t.lam = lam + (size_t)k0 * L;
+      t.pens = P.dpens + k0;
+      t.allowed = I.groups ? I.d_allowed : nullptr;
+      t.beta = beta + ((size_t)b * npen + k0) * L * p;
+      t.iters = iters + ((size_t)b * npen + k0) * L;
+      t.conv = conv + ((size_t)b * npen + k0) * L;
+    }
+  CU(cudaMemcpyAsync(I.d_tasks, tasks.data(), sizeof(IterTask) * tasks.size(), cudaMemcpyHostToDevice, s));
+  IterLaunch Lc{};
+  Lc.tasks = I.d_tasks; Lc.ntasks = (int)tasks.size(); Lc.C = I.C; Lc.M = I.M;
+  Lc.precision = o->iter_precision;
+  Lc.tol = o->tol; Lc.max_iter = o->max_iter; Lc.max_loops = max_loops; Lc.dstatus = ctx->dstatus;
+  Lc.smem = I.smem;
+  LAUNCH(OEM_PROF_ITER, launch_oem_iter(Lc, s));
+  return OEM_OK;
+}
+
+// Autotuner: time each candidate layout (cluster CTAs around the default, and
+// 1, 2, 4, 8 instances per task) for a fixed number of iterations on the real
+// inputs, keep the fastest for this shape in the context. The candidates'
+// partial outputs are overwritten by the full run that follows.
+inline int tune_iter(oem_ctx* ctx, int64_t p, int B, const float* G32, int ldg, const double* G64,
+                     const double* c, const double* d, const double* lam, PenPlan& P,
+                     const oem_options* o, IterPlan& I, double* beta, int32_t* iters,
+                     uint8_t* conv, cudaStream_t s) {
+  constexpr int64_t kLoops = 48;
+  std::vector<std::pair<int, int>> cand;
+  for (int C : {I.C / 2, I.C, I.C * 2})
+    for (int Mg : {1, 2, 4, 8})
+      if (C >= 1 && C <= kMaxCluster && Mg <= oem_iter_mpad(P.npen) && (Mg == 1 || Mg / 2 < P.npen))
+        cand.push_back({C, Mg});
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  std::vector<IterTask> tasks;
+  float best = 1e30f;
+  std::pair<int, int> pick{I.C, I.Mg};
+  const bool prof = ctx->prof;
+  ctx->prof = false;  // tuning launches are not part of the profile
+  int rc = OEM_OK;
+  for (auto [C, Mg] : cand) {
+    IterPlan J = I;
+    if (layout_iter(ctx, p, B, P, o->iter_precision, C, Mg, J) != OEM_OK || J.C != C) continue;
+    // once untimed (module load), once timed
+    if ((rc = launch_iter_layout(ctx, p, B, G32, ldg, G64, c, d, lam, P, o, J, beta, iters, conv,
+                                 2, tasks, s)))
+      break;
+    if (cudaEventRecord(e0, s) != cudaSuccess) { rc = fail(ctx, OEM_ECUDA, "event record failed"); break; }
+    if ((rc = launch_iter_layout(ctx, p, B, G32, ldg, G64, c, d, lam, P, o, J, beta, iters, conv,
+                                 kLoops, tasks, s)))
+      break;
+    float ms = 0.f;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = fail(ctx, OEM_ECUDA, "timing the iteration layouts failed");
+      break;
+    }
+    ++ctx->tune_runs;
+    if (ms < best) { best = ms; pick = {C, Mg}; }
+  }
+  ctx->prof = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  ctx->iter_tuned[tune_key(p, B, P, o->iter_precision, I.groups)] = pick;
+  return layout_iter(ctx, p, B, P, o->iter_precision, pick.first, pick.second, I);
 }
 
 // B tasks: Gram b uses G32 + b p ldg (or G64 + b p p), c + b p, d + b, and
@@ -485,36 +613,21 @@ inline int run_iter(oem_ctx* ctx, int64_t p, int B, const float* G32, int ldg, c
              const double* c, const double* d, const double* lam, PenPlan& P,
              const oem_options* o, IterPlan& I, double* beta, int32_t* iters, uint8_t* conv,
              cudaStream_t s) {
-  const int L = o->nlambda, npen = P.npen;
   if (I.groups) {
     std::vector<uint8_t> al(P.allowed.begin(), P.allowed.end());
     CU(cudaMemcpyAsync(I.d_allowed, al.data(), al.size(), cudaMemcpyHostToDevice, s));
   }
-  std::vector<IterTask> tasks(B);
-  for (int b = 0; b < B; ++b) {
-    IterTask& t = tasks[b];
-    t = IterTask{};
-    t.p = (int)p; t.npen = npen; t.L = L; t.ldg = ldg;
-    t.max_rows = I.max_rows; t.smem_rows = I.smem_rows; t.resume = 0;
-    for (int r = 0; r <= kMaxCluster; ++r) t.slice[r] = r <= I.C ? I.slice[r] : (int32_t)p;
-    t.G32 = G32 ? G32 + (size_t)b * p * ldg : nullptr;
-    t.G64 = G64 ? G64 + (size_t)b * p * p : nullptr;
-    t.c = c + (size_t)b * p;
-    t.d = d + b;
-    t.lam = lam;
-    t.pens = P.dpens;
-    t.allowed = I.groups ? I.d_allowed : nullptr;
-    t.beta = beta + (size_t)b * npen * L * p;
-    t.iters = iters + (size_t)b * npen * L;
-    t.conv = conv + (size_t)b * npen * L;
+  if (I.tune) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+      int r = tune_iter(ctx, p, B, G32, ldg, G64, c, d, lam, P, o, I, beta, iters, conv, s);
+      if (r) return r;
+    }
   }
-  CU(cudaMemcpyAsync(I.d_tasks, tasks.data(), sizeof(IterTask) * B, cudaMemcpyHostToDevice, s));
-  IterLaunch Lc{};
-  Lc.tasks = I.d_tasks; Lc.ntasks = B; Lc.C = I.C; Lc.M = I.M; Lc.precision = o->iter_precision;
-  Lc.tol = o->tol; Lc.max_iter = o->max_iter; Lc.max_loops = 0; Lc.dstatus = ctx->dstatus;
-  Lc.smem = I.smem;
-  LAUNCH(OEM_PROF_ITER, launch_oem_iter(Lc, s));
-  return OEM_OK;
+  std::vector<IterTask> tasks;
+  return launch_iter_layout(ctx, p, B, G32, ldg, G64, c, d, lam, P, o, I, beta, iters, conv, 0,
+                            tasks, s);
 }
 
 

@@ -345,7 +345,10 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
         const int idx = kq * maxR + i;
         if (my_inst && !skip_mv) {
           const T incr = fma(my_d, Dc[(size_t)(i0 + i) * M + kq], -y);
-          if (kF32) {
+          // an instance whose dbeta was zero (y == 0 exactly) keeps its u
+          // bit for bit, however the instances are grouped into tasks
+          if (incr == T(0)) {
+          } else if (kF32) {
             const T h = uhi[idx];
             const T s1 = h + incr, bb = s1 - h;
             const T e = (h - (s1 - bb)) + (incr - bb);
@@ -529,7 +532,8 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
             if (k >= m) continue;
             const int idx = k * maxR + ib;
             const T incr = fma(dk[k], Dc[(size_t)(i0 + ib) * M + k], -acc[k]);
-            if (kF32) {
+            if (incr == T(0)) {
+            } else if (kF32) {
               const T h = uhi[idx];
               const T s = h + incr, bb = s - h;
               const T e = (h - (s - bb)) + (incr - bb);

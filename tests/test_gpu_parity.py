@@ -287,3 +287,28 @@ def test_cv_matches_oracle(oem, ctx, mode):
             assert abs(ref.cvm[i, imin[i]] - ref.cvm[i, ref.idx_min[i]]) <= 1e-6 * ref.cvm[i].min()
     assert int(out["best_penalty"].cpu()[0]) == ref.best_penalty or \
         abs(ref.cvm[int(out["best_penalty"].cpu()[0])].min() - ref.cvm[ref.best_penalty].min()) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_iteration_layouts_give_identical_paths(oem, ctx, precision):
+    # Each (row, instance) sum is formed in the same order whatever the
+    # cluster size and however the penalties are grouped into tasks, so every
+    # layout, and the one the autotuner picks, returns the same bits.
+    p, n = 130, 4000
+    X, y = _data(n, p, 21, np.float64)
+    G, c, N, _ = oracle.gram_sums(X, y)
+    G, c = G / n, c / n
+    d = oracle.lanczos_d(G)[0]
+    gp, op = _pens(p, PENS)
+    runs = []
+    for ncl, mg, tune in [(4, 8, False), (1, 1, False), (16, 1, False), (2, 2, False),
+                          (8, 4, False), (0, 0, True), (0, 0, True), (0, 0, False)]:
+        out = oem.oem_fit_path(ctx, _dev(G), _dev(c), gp, d=d, nlambda=20, lambda_min_ratio=1e-2,
+                               tol=1e-8, cluster_ctas=ncl, instances_per_task=mg, autotune=tune,
+                               iter_precision=precision)
+        assert ctx.sync() == 0
+        runs.append([t.cpu().numpy() for t in out])
+    for r in runs[1:]:
+        for a, b in zip(runs[0], r):
+            np.testing.assert_array_equal(a, b)
+    _check_paths(*runs[0], G, c, d, op, 20, 1e-2, tol=1e-8)
