@@ -106,16 +106,28 @@ __global__ void __launch_bounds__(1024) lz_update_kernel(int64_t p, LanczosWork 
   }
 }
 
-// Number of eigenvalues of the symmetric tridiagonal (a, e) smaller than x
-// (Sturm sequence count).
+// Number of eigenvalues of the symmetric tridiagonal (a, e) smaller than x:
+// the sign changes along chi_0 = 1, chi_1, ..., chi_m, chi_k(x) = det(T_k - x I)
+// (Sturm sequence), from the three-term recurrence
+//   chi_k = (a_k - x) chi_{k-1} - e_{k-1}^2 chi_{k-2},
+// which needs no division (float64 division is slow on this part). The pair
+// (chi_{k-1}, chi_k) is rescaled by a power of two when it leaves
+// [2^-400, 2^400], which keeps every sign; an exact zero takes the sign of its
+// predecessor (the usual convention: a zero pivot counts as positive).
 __device__ int sturm_below(const double* a, const double* e, int m, double x) {
   int cnt = 0;
-  double q = a[0] - x;
-  if (q < 0) ++cnt;
+  double c0 = 1.0, c1 = a[0] - x;
+  if (c1 == 0.0) c1 = 0x1p-600;
+  if (c1 < 0.0) ++cnt;
   for (int i = 1; i < m; ++i) {
-    if (q == 0.0) q = 1e-300;
-    q = a[i] - x - e[i - 1] * e[i - 1] / q;
-    if (q < 0) ++cnt;
+    double c2 = fma(a[i] - x, c1, -(e[i - 1] * e[i - 1]) * c0);
+    if (c2 == 0.0) c2 = copysign(0x1p-600, c1) * fmax(fabs(c1), 0x1p-400);
+    if ((c2 < 0.0) != (c1 < 0.0)) ++cnt;
+    c0 = c1;
+    c1 = c2;
+    const double mag = fmax(fabs(c0), fabs(c1));
+    if (mag > 0x1p400) { c0 *= 0x1p-400; c1 *= 0x1p-400; }
+    else if (mag < 0x1p-400) { c0 *= 0x1p400; c1 *= 0x1p400; }
   }
   return cnt;
 }
@@ -141,13 +153,13 @@ __global__ void lz_finish_kernel(LanczosWork w, int steps, double* d) {
   // where the count crosses m (the interval shrinks 33-fold per round).
   const int lane = threadIdx.x;
   for (int it = 0; it < 40; ++it) {
-    const double w = (hi - lo) / 33.0;
-    const double x = lo + w * (lane + 1);
+    const double wd = (hi - lo) / 33.0;
+    const double x = lo + wd * (lane + 1);
     const bool above = (x < hi) && (x > lo) ? sturm_below(a, e, m, x) >= m : (x >= hi);
     const unsigned mask = __ballot_sync(0xffffffffu, above);
     const int first = mask ? __ffs(mask) - 1 : 32;  // first tested point above theta
-    const double nlo = first == 0 ? lo : lo + w * first;
-    const double nhi = first == 32 ? hi : lo + w * (first + 1);
+    const double nlo = first == 0 ? lo : lo + wd * first;
+    const double nhi = first == 32 ? hi : lo + wd * (first + 1);
     if (!(nhi - nlo < hi - lo)) break;  // no further progress in float64
     lo = nlo;
     hi = nhi;
@@ -155,26 +167,30 @@ __global__ void lz_finish_kernel(LanczosWork w, int steps, double* d) {
   if (lane != 0) return;
   const double theta = hi;
   // eigenvector of T_m for theta by inverse iteration with shift slightly
-  // above theta (T - sigma I is then negative definite: no pivoting needed)
+  // above theta (T - sigma I is then negative definite: no pivoting needed);
+  // one reciprocal per row of the Thomas sweep
   const double sigma = theta + 1e-12 * fmax(fabs(theta), fro) + 1e-300;
-  double x[kLzMax], cp[kLzMax], dp[kLzMax];
-  for (int i = 0; i < m; ++i) x[i] = 1.0;
-  for (int rep = 0; rep < 3; ++rep) {
-    // Thomas algorithm on (T - sigma I) y = x
+  double x[kLzMax], cp[kLzMax], rp[kLzMax];
+  {
     double den = a[0] - sigma;
-    cp[0] = e[0] / den;
-    dp[0] = x[0] / den;
+    rp[0] = 1.0 / den;
+    cp[0] = e[0] * rp[0];
     for (int i = 1; i < m; ++i) {
       den = (a[i] - sigma) - e[i - 1] * cp[i - 1];
-      cp[i] = (i < m - 1) ? e[i] / den : 0.0;
-      dp[i] = (x[i] - e[i - 1] * dp[i - 1]) / den;
+      rp[i] = 1.0 / den;
+      cp[i] = (i < m - 1) ? e[i] * rp[i] : 0.0;
     }
-    x[m - 1] = dp[m - 1];
-    for (int i = m - 2; i >= 0; --i) x[i] = dp[i] - cp[i] * x[i + 1];
+  }
+  for (int i = 0; i < m; ++i) x[i] = 1.0;
+  for (int rep = 0; rep < 2; ++rep) {
+    // forward: dp_i = (x_i - e_{i-1} dp_{i-1}) / den_i, kept in x
+    x[0] = x[0] * rp[0];
+    for (int i = 1; i < m; ++i) x[i] = (x[i] - e[i - 1] * x[i - 1]) * rp[i];
+    for (int i = m - 2; i >= 0; --i) x[i] = x[i] - cp[i] * x[i + 1];
     double nrm = 0.0;
     for (int i = 0; i < m; ++i) nrm = fma(x[i], x[i], nrm);
-    nrm = sqrt(nrm);
-    for (int i = 0; i < m; ++i) x[i] /= nrm;
+    const double inv = 1.0 / sqrt(nrm);
+    for (int i = 0; i < m; ++i) x[i] *= inv;
   }
   const double r = fabs(e[m - 1] * x[m - 1]);
   d[b] = theta + r;
