@@ -109,7 +109,11 @@ typedef struct oem_options {
   int32_t gram_mode;        /* OEM_GRAM_* (default OEM_GRAM_AUTO) */
   int32_t iter_precision;   /* OEM_ITER_F32 (default) or OEM_ITER_F64 */
   int32_t cluster_ctas;     /* CTAs cooperating on one Gram in the iteration
-                               (0 = chosen by the library; else 1,2,4,8,16) */
+                               (0 = chosen by the library; 1,2,4,8,16: one
+                               thread-block cluster exchanging through
+                               distributed shared memory; 17..4096: a group of
+                               that many CTAs of a cooperative launch, at most
+                               one per SM, exchanging through L2) */
   int32_t instances_per_task; /* penalties of one Gram iterated together by
                                one cluster (0 = chosen by the library; else
                                1,2,4,8); results do not depend on it */

@@ -34,8 +34,8 @@ struct oem_ctx {
   double prof_ms[OEM_PROF_NKERNELS] = {0};
   int64_t prof_n[OEM_PROF_NKERNELS] = {0};
   // iteration layouts chosen by timing, per (p, Grams, penalties, precision,
-  // groups): cluster CTAs and instances per task
-  std::map<std::array<int64_t, 5>, std::pair<int, int>> iter_tuned;
+  // groups): CTAs per task, instances per task, grid mode
+  std::map<std::array<int64_t, 5>, std::array<int, 3>> iter_tuned;
   int64_t tune_runs = 0;
 };
 
@@ -412,8 +412,8 @@ inline int check_opts(oem_ctx* ctx, const oem_options* o) {
   if (o->iter_precision != OEM_ITER_F32 && o->iter_precision != OEM_ITER_F64)
     return fail(ctx, OEM_EINVAL, "iter_precision=%d", o->iter_precision);
   const int c = o->cluster_ctas;
-  if (!(c == 0 || c == 1 || c == 2 || c == 4 || c == 8 || c == 16))
-    return fail(ctx, OEM_EINVAL, "cluster_ctas=%d not in {0,1,2,4,8,16}", c);
+  if (!(c == 0 || c == 1 || c == 2 || c == 4 || c == 8 || (c >= 16 && c <= 4096)))
+    return fail(ctx, OEM_EINVAL, "cluster_ctas=%d not in {0,1,2,4,8} or [16,4096]", c);
   const int g = o->instances_per_task;
   if (!(g == 0 || g == 1 || g == 2 || g == 4 || g == 8))
     return fail(ctx, OEM_EINVAL, "instances_per_task=%d not in {0,1,2,4,8}", g);
@@ -448,19 +448,56 @@ struct IterPlan {
   int C = 1, M = 1, Mg = 1, max_rows = 0, smem_rows = 0;
   size_t smem = 0;
   int32_t slice[kMaxCluster + 1] = {0};
+  bool grid = false;      // cooperative grid mode (C CTAs per task, any C)
+  std::vector<int32_t> gslice;  // grid mode: C + 1 row boundaries
   bool groups = false;
   bool tune = false;      // time the candidate layouts at the first run
   int max_tasks = 0;      // task-table capacity (B x npen)
   IterTask* d_tasks = nullptr;
   uint8_t* d_allowed = nullptr;
+  // grid mode exchange space: per task [2][ldgs][8] float64 dbeta + slots +
+  // barrier (sized for the widest case), and the row boundaries
+  unsigned char* d_xbuf = nullptr;
+  size_t xbuf_task = 0;
+  int32_t* d_gslice = nullptr;
+  int gslice_cap = 0;     // boundaries per task
 };
 
+inline size_t grid_xbuf_task_bytes(int64_t p) {
+  const size_t ldgs = (size_t)((p + 3) & ~3LL);
+  return ((2 * ldgs * 8 * sizeof(double) + 3 * 16 * 4 + 2 * 4) + 255) & ~(size_t)255;
+}
+
 // Cluster size C and Mg instances per task for B Grams of npen instances;
-// returns OEM_OK with the shared-memory plan, or an error when nothing fits.
+// returns OK with the shared-memory plan, or an error when nothing fits. In
+// grid mode C is the number of CTAs per task (one per SM, every task's CTAs
+// resident together) and every Gram row must fit in shared memory.
 inline int layout_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, int prec, int C, int Mg,
-                       IterPlan& I) {
+                       bool grid, IterPlan& I) {
   I.Mg = Mg;
   I.M = oem_iter_mpad(Mg);
+  I.grid = grid;
+  const int ntasks = B * ((P.npen + Mg - 1) / Mg);
+  if (grid) {
+    C = std::min<int>(C, ctx->num_sms / std::max(1, ntasks));
+    C = (int)std::min<int64_t>(C, (p + 3) / 4);
+    if (C < 2) return fail(ctx, OEM_EUNSUPPORTED, "grid mode needs at least 2 CTAs per task");
+    I.gslice.assign((size_t)C + 1, 0);
+    make_slices(p, C, P.allowed, I.gslice.data(), &I.max_rows);
+    const size_t fixed = oem_iter_smem_fixed((int)p, Mg, I.max_rows, prec);
+    const size_t per = oem_iter_smem_per_row((int)p, prec);
+    I.smem_rows = I.max_rows;
+    I.smem = fixed + (size_t)I.max_rows * per;
+    I.C = C;
+    if (I.smem + 1024 > kIterSmemCap)
+      return fail(ctx, OEM_EUNSUPPORTED, "grid mode: %d rows per CTA do not fit", I.max_rows);
+    IterLaunch probe{};
+    probe.ntasks = ntasks; probe.C = C; probe.M = I.M; probe.precision = prec;
+    probe.smem = I.smem; probe.grid = 1;
+    if (oem_iter_max_cluster(probe) < 1)
+      return fail(ctx, OEM_EUNSUPPORTED, "grid mode: no CTA fits on an SM");
+    return OEM_OK;
+  }
   for (;; C /= 2) {
     make_slices(p, C, P.allowed, I.slice, &I.max_rows);
     const size_t fixed = oem_iter_smem_fixed((int)p, Mg, I.max_rows, prec);
@@ -471,7 +508,7 @@ inline int layout_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, int pre
     I.smem = fixed + (size_t)I.smem_rows * per;
     I.C = C;
     IterLaunch probe{};
-    probe.ntasks = B * ((P.npen + Mg - 1) / Mg); probe.C = C; probe.M = I.M; probe.precision = prec;
+    probe.ntasks = ntasks; probe.C = C; probe.M = I.M; probe.precision = prec;
     probe.smem = I.smem;
     if (oem_iter_max_cluster(probe) >= 1) return OEM_OK;
     if (C == 1) return fail(ctx, OEM_ECUDA, "no cluster configuration of the iteration kernel fits");
@@ -486,6 +523,8 @@ inline std::array<int64_t, 5> tune_key(int64_t p, int B, const PenPlan& P, int p
 // clusters of all B Grams resident at once), then the fewest instances per
 // task whose clusters all fit on the device at once (more clusters share the
 // work of one Gram; each iterates fewer instances per step).
+// cluster_ctas above 16 selects grid mode with that many CTAs per task (at
+// most the SMs the tasks leave each).
 inline int plan_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, const oem_options* o, IterPlan& I) {
   const int prec = o->iter_precision;
   I.groups = false;
@@ -504,18 +543,37 @@ inline int plan_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, const oem
     while (Mg > 1 && (int64_t)B * ((P.npen + Mg / 2 - 1) / (Mg / 2)) * C <= ctx->num_sms) Mg /= 2;
   }
   Mg = std::min(Mg, std::max(1, P.npen));
+  bool grid = o->cluster_ctas > kMaxCluster;
+  I.gslice_cap = std::max(ctx->num_sms, o->cluster_ctas) + 1;
+  if (grid) C = o->cluster_ctas;
+  if (o->cluster_ctas <= 0) {
+    // grid mode when a cluster cannot keep all its Gram rows in shared
+    // memory but the whole device can
+    IterPlan J = I;
+    if (layout_iter(ctx, p, B, P, prec, C, Mg, false, J) == OEM_OK && J.smem_rows < J.max_rows) {
+      IterPlan K = I;
+      if (layout_iter(ctx, p, B, P, prec, ctx->num_sms, Mg, true, K) == OEM_OK) {
+        grid = true;
+        C = ctx->num_sms;
+      }
+    }
+  }
   auto it = ctx->iter_tuned.find(tune_key(p, B, P, prec, I.groups));
   I.tune = false;
   if (o->autotune && o->cluster_ctas <= 0 && o->instances_per_task <= 0) {
-    if (it != ctx->iter_tuned.end()) { C = it->second.first; Mg = it->second.second; }
+    if (it != ctx->iter_tuned.end()) { C = it->second[0]; Mg = it->second[1]; grid = it->second[2] != 0; }
     else I.tune = true;
   }
-  return layout_iter(ctx, p, B, P, prec, C, Mg, I);
+  return layout_iter(ctx, p, B, P, prec, C, Mg, grid, I);
 }
 
 inline void iter_request(Arena& A, int64_t p, int B, IterPlan& I) {
-  A.add(&I.d_tasks, (size_t)std::max(B, I.max_tasks));
+  const size_t T = (size_t)std::max(B, I.max_tasks);
+  A.add(&I.d_tasks, T);
   if (I.groups) A.add(&I.d_allowed, (size_t)p + 1);
+  I.xbuf_task = grid_xbuf_task_bytes(p);
+  A.add(&I.d_xbuf, T * I.xbuf_task);
+  A.add(&I.d_gslice, T * (size_t)I.gslice_cap);
 }
 
 // Launch the iteration for B Grams with the layout in I (task table written
@@ -545,13 +603,29 @@ inline int launch_iter_layout(oem_ctx* ctx, int64_t p, int B, const float* G32, 
       t.beta = beta + ((size_t)b * npen + k0) * L * p;
       t.iters = iters + ((size_t)b * npen + k0) * L;
       t.conv = conv + ((size_t)b * npen + k0) * L;
+      if (I.grid) {
+        const size_t ldgs = (size_t)((p + 3) & ~3LL);
+        unsigned char* x = I.d_xbuf + (size_t)(b * S + q) * I.xbuf_task;
+        t.xD = x;
+        t.xslot = reinterpret_cast<unsigned*>(x + 2 * ldgs * 8 * sizeof(double));
+        t.xbar = t.xslot + 3 * 16;
+        t.gslice = I.d_gslice;
+      }
     }
+  if (I.grid) {
+    if ((int)I.gslice.size() > I.gslice_cap || tasks.size() * I.xbuf_task == 0)
+      return fail(ctx, OEM_ECUDA, "grid mode buffers too small");
+    CU(cudaMemsetAsync(I.d_xbuf, 0, tasks.size() * I.xbuf_task, s));
+    CU(cudaMemcpyAsync(I.d_gslice, I.gslice.data(), sizeof(int32_t) * I.gslice.size(),
+                       cudaMemcpyHostToDevice, s));
+  }
   CU(cudaMemcpyAsync(I.d_tasks, tasks.data(), sizeof(IterTask) * tasks.size(), cudaMemcpyHostToDevice, s));
   IterLaunch Lc{};
   Lc.tasks = I.d_tasks; Lc.ntasks = (int)tasks.size(); Lc.C = I.C; Lc.M = I.M;
   Lc.precision = o->iter_precision;
   Lc.tol = o->tol; Lc.max_iter = o->max_iter; Lc.max_loops = max_loops; Lc.dstatus = ctx->dstatus;
   Lc.smem = I.smem;
+  Lc.grid = I.grid ? 1 : 0;
   LAUNCH(OEM_PROF_ITER, launch_oem_iter(Lc, s));
   return OEM_OK;
 }
@@ -565,23 +639,29 @@ inline int tune_iter(oem_ctx* ctx, int64_t p, int B, const float* G32, int ldg, 
                      const oem_options* o, IterPlan& I, double* beta, int32_t* iters,
                      uint8_t* conv, cudaStream_t s) {
   constexpr int64_t kLoops = 48;
-  std::vector<std::pair<int, int>> cand;
-  for (int C : {I.C / 2, I.C, I.C * 2})
-    for (int Mg : {1, 2, 4, 8})
-      if (C >= 1 && C <= kMaxCluster && Mg <= oem_iter_mpad(P.npen) && (Mg == 1 || Mg / 2 < P.npen))
-        cand.push_back({C, Mg});
+  std::vector<std::array<int, 3>> cand;  // (CTAs per task, instances per task, grid)
+  const int C0 = I.grid ? 16 : I.C;
+  for (int Mg : {1, 2, 4, 8}) {
+    if (!(Mg <= oem_iter_mpad(P.npen) && (Mg == 1 || Mg / 2 < P.npen))) continue;
+    for (int C : {C0 / 2, C0, C0 * 2})
+      if (C >= 1 && C <= kMaxCluster) cand.push_back({C, Mg, 0});
+    cand.push_back({ctx->num_sms, Mg, 1});
+  }
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   std::vector<IterTask> tasks;
   float best = 1e30f;
-  std::pair<int, int> pick{I.C, I.Mg};
+  std::array<int, 3> pick{I.C, I.Mg, I.grid ? 1 : 0};
   const bool prof = ctx->prof;
   ctx->prof = false;  // tuning launches are not part of the profile
   int rc = OEM_OK;
-  for (auto [C, Mg] : cand) {
+  for (auto cd : cand) {
+    const int C = cd[0], Mg = cd[1];
+    const bool grid = cd[2] != 0;
     IterPlan J = I;
-    if (layout_iter(ctx, p, B, P, o->iter_precision, C, Mg, J) != OEM_OK || J.C != C) continue;
+    if (layout_iter(ctx, p, B, P, o->iter_precision, C, Mg, grid, J) != OEM_OK) continue;
+    if (!grid && J.C != C) continue;
     // once untimed (module load), once timed
     if ((rc = launch_iter_layout(ctx, p, B, G32, ldg, G64, c, d, lam, P, o, J, beta, iters, conv,
                                  2, tasks, s)))
@@ -597,14 +677,14 @@ inline int tune_iter(oem_ctx* ctx, int64_t p, int B, const float* G32, int ldg, 
       break;
     }
     ++ctx->tune_runs;
-    if (ms < best) { best = ms; pick = {C, Mg}; }
+    if (ms < best) { best = ms; pick = {J.C, Mg, grid ? 1 : 0}; }
   }
   ctx->prof = prof;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
   ctx->iter_tuned[tune_key(p, B, P, o->iter_precision, I.groups)] = pick;
-  return layout_iter(ctx, p, B, P, o->iter_precision, pick.first, pick.second, I);
+  return layout_iter(ctx, p, B, P, o->iter_precision, pick[0], pick[1], pick[2] != 0, I);
 }
 
 // B tasks: Gram b uses G32 + b p ldg (or G64 + b p p), c + b p, d + b, and

@@ -177,10 +177,17 @@ struct IterTask {
   int32_t* st_ctl;       // [40]: per instance (lambda index, iterations, done, -);
                          // [32] = every instance done
   int32_t* fin_out;      // where the launch writes "every instance done" (or NULL)
+  // grid mode only (IterLaunch::grid): the C CTAs of the task exchange
+  // through global memory instead of a cluster's shared memory
+  const int32_t* gslice; // [C+1] CTA r owns rows [gslice[r], gslice[r+1])
+  void* xD;              // [2][round_up(p,4)][M] dbeta buffers (T), zeroed
+  unsigned* xslot;       // [3][2M] maxima slots, zeroed
+  unsigned* xbar;        // [2] barrier count and generation, zeroed
 };
 struct IterLaunch {
   const IterTask* tasks; // device array
   int32_t ntasks, C, M, precision;
+  int32_t grid;          // 1: cooperative launch, C CTAs per task, global-memory exchange
   double tol;
   int64_t max_iter;      // per lambda
   int64_t max_loops;     // per launch (<= 0: run to completion)
@@ -192,7 +199,8 @@ int oem_iter_mpad(int npen);
 // Shared memory needed besides the resident Gram rows, and per resident row.
 size_t oem_iter_smem_fixed(int p, int npen, int max_rows, int precision);
 size_t oem_iter_smem_per_row(int p, int precision);
-// Clusters of this configuration the device can co-schedule (0: none).
+// Clusters of this configuration the device can co-schedule (0: none); in
+// grid mode, CTAs per SM.
 int oem_iter_max_cluster(const IterLaunch& P);
 cudaError_t launch_oem_iter(const IterLaunch& P, cudaStream_t s);
 

@@ -28,6 +28,15 @@
 // takes the same convergence decisions from the same slot. A launch may stop
 // after a loop budget and save its state (serving), to be resumed by a later
 // launch.
+//
+// Grid mode (large p: the Gram rows of a task do not fit in the shared memory
+// of one cluster, at most 16 SMs, but fit in that of C > 16 CTAs): the C CTAs
+// of a task are an ordinary group of a cooperative launch, one per SM. Each
+// iteration a CTA reads the whole dbeta from global memory (L2) into its
+// shared memory, writes its own rows of the new dbeta back to global memory,
+// folds its maxima into a global slot with atomics, and waits at a
+// global-memory barrier of the group (bounded spin) instead of the cluster
+// barrier. The arithmetic is the same as in cluster mode.
 #include "oem_internal.cuh"
 
 #include <cooperative_groups.h>
@@ -131,6 +140,42 @@ __device__ __forceinline__ float from_red(unsigned int b) { return __uint_as_flo
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Barrier of the nctas CTAs of one task in a cooperative launch (all of them
+// resident): bar[0] counts arrivals, bar[1] is the generation; gen is the
+// caller's copy of the generation (thread 0). Every wait is bounded (about
+// 2 s at 2 GHz); returns false in every thread of the CTA on timeout.
+__device__ __forceinline__ bool group_barrier(unsigned* bar, unsigned nctas, unsigned& gen) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    const unsigned g = gen;
+    __threadfence();  // this CTA's global writes before its arrival
+    if (atomicAdd(&bar[0], 1u) == nctas - 1) {
+      atomicExch(&bar[0], 0u);  // nobody arrives again before the generation moves
+      __threadfence();
+      atomicExch(&bar[1], g + 1);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire_gpu(&bar[1]) == g)
+        if (clock64() - t0 > 4000000000LL) { ok = 0; break; }
+    }
+    __threadfence();
+    gen = g + 1;
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
 // Shared-memory carve-up (byte offsets, 16-byte aligned). The dbeta buffers
 // have ldgs = round_up(p, 4) rows; rows p.. stay zero.
 struct IterSmem {
@@ -157,15 +202,18 @@ __host__ __device__ inline IterSmem iter_smem_layout(int p, int M, int maxR, int
   return L;
 }
 
-template <typename T, int M, int NT>
+template <typename T, int M, int NT, bool kGrid>
 __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   constexpr int NW = NT / 32;
   cg::cluster_group cluster = cg::this_cluster();
   const int C = P.C;
-  const int rank = (int)cluster.block_rank();
+  const int rank = kGrid ? (int)(blockIdx.x % C) : (int)cluster.block_rank();
   const IterTask& tk = P.tasks[blockIdx.x / C];
   const int p = tk.p, L = tk.L, m = tk.npen, maxR = tk.max_rows;
-  const int i0 = tk.slice[rank], R = tk.slice[rank + 1] - i0;
+  const int i0 = kGrid ? tk.gslice[rank] : tk.slice[rank];
+  const int R = (kGrid ? tk.gslice[rank + 1] : tk.slice[rank + 1]) - i0;
+  T* const xD = reinterpret_cast<T*>(tk.xD);  // grid mode
+  unsigned bar_gen = 0;
   const int ldgs = (p + 3) & ~3, smem_rows = tk.smem_rows;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr bool kF32 = sizeof(T) == 4;
@@ -269,7 +317,14 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
     const int i = e / ldgs, j = e % ldgs;
     Gs[e] = (i < R && j < p) ? Gglob[(size_t)(i0 + i) * ldgg + j] : T(0);
   }
-  cluster.sync();  // every CTA initialised before any DSMEM access
+  if constexpr (kGrid) {
+    if (!group_barrier(tk.xbar, (unsigned)C, bar_gen)) {
+      if (tid == 0) atomicOr(P.dstatus, kStatTimeout);
+      return;
+    }
+  } else {
+    cluster.sync();  // every CTA initialised before any DSMEM access
+  }
 
   // Lane roles in the row-group mat-vec: a group is RG = 16 / M rows; after
   // the reduce-scatter, lane l holds the sum of value v = (l >> 1) & 15, i.e.
@@ -298,6 +353,17 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
     const int cur = t & 1, nxt = cur ^ 1;
     const T* Dc = Dbuf + (size_t)cur * ldgs * M;
     const int nr = whi - wlo;
+    if constexpr (kGrid) {
+      // the whole dbeta of the last iteration, from L2 (not L1: other SMs
+      // wrote it)
+      if (!skip_mv) {
+        const float4* src = reinterpret_cast<const float4*>(xD + (size_t)cur * ldgs * M);
+        float4* dst = reinterpret_cast<float4*>(Dbuf + (size_t)cur * ldgs * M);
+        const int nv4 = (int)((size_t)ldgs * M * sizeof(T) / 16);
+        for (int e = tid; e < nv4; e += NT) dst[e] = __ldcg(src + e);
+      }
+      __syncthreads();
+    }
     T lmd = T(0), lmb = T(0);  // this lane's running max |dbeta|, |beta| (instance kq)
     // ---- 1. per group of RG rows: y = G dbeta for all instances (one pass
     // over dbeta for the group), u update and, without groups, the threshold
@@ -433,10 +499,16 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
     }
     // ---- 3. DSMEM: dbeta rows to every CTA, maxima into every CTA's slot
     {
-      T* Dn = Dbuf + (size_t)nxt * ldgs * M;
-      for (int e = lane; e < nr * C; e += 32) {
-        const int i = wlo + e / C, r = e % C;
-        store_col<T, M>(cluster.map_shared_rank(Dn + (size_t)(i0 + i) * M, r), st + (size_t)i * M);
+      if constexpr (kGrid) {
+        T* Dn = xD + (size_t)nxt * ldgs * M;
+        for (int i = wlo + lane; i < whi; i += 32)
+          store_col<T, M>(Dn + (size_t)(i0 + i) * M, st + (size_t)i * M);
+      } else {
+        T* Dn = Dbuf + (size_t)nxt * ldgs * M;
+        for (int e = lane; e < nr * C; e += 32) {
+          const int i = wlo + e / C, r = e % C;
+          store_col<T, M>(cluster.map_shared_rank(Dn + (size_t)(i0 + i) * M, r), st + (size_t)i * M);
+        }
       }
       // instance kq's warp maxima end in lane 2 kq (lanes of one instance
       // differ in the row bits 2M .. 16 of the lane index)
@@ -458,15 +530,29 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
       float v = 0.f;
       if (lane < E)
         for (int w = 0; w < NW; ++w) v = fmax(v, lred[w * E + lane]);
-      unsigned int* slot = red + (size_t)(t % 3) * E;
-      for (int base = 0; base < C * E; base += 32) {
-        const int e = base + lane, q = e % E;
-        const float val = __shfl_sync(0xffffffffu, v, q);
-        if (e < C * E && val > 0.f)
-          atomicMax(cluster.map_shared_rank(slot + q, e / E), __float_as_uint(val));
+      if constexpr (kGrid) {
+        if (lane < E && v > 0.f) atomicMax(tk.xslot + (size_t)(t % 3) * E + lane, __float_as_uint(v));
+      } else {
+        unsigned int* slot = red + (size_t)(t % 3) * E;
+        for (int base = 0; base < C * E; base += 32) {
+          const int e = base + lane, q = e % E;
+          const float val = __shfl_sync(0xffffffffu, v, q);
+          if (e < C * E && val > 0.f)
+            atomicMax(cluster.map_shared_rank(slot + q, e / E), __float_as_uint(val));
+        }
       }
     }
-    cluster.sync();
+    if constexpr (kGrid) {
+      if (!group_barrier(tk.xbar, (unsigned)C, bar_gen)) {
+        if (tid == 0) atomicOr(P.dstatus, kStatTimeout);
+        break;
+      }
+      // the slot into this CTA's table (read below like the cluster slot)
+      if (tid < 2 * M) red[(size_t)(t % 3) * M * 2 + tid] = ld_relaxed_gpu(tk.xslot + (size_t)(t % 3) * M * 2 + tid);
+      __syncthreads();
+    } else {
+      cluster.sync();
+    }
     // ---- 4. decisions (every thread, same data, same result)
     {
       const unsigned int* slot = red + (size_t)(t % 3) * M * 2;
@@ -500,7 +586,10 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
 #pragma unroll
       for (int k = 0; k < M; ++k)
         if (k == kq) { my_lam = lamv[k]; my_done = done[k]; }
-      if (tid < M * 2) red[(size_t)((t + 2) % 3) * M * 2 + tid] = 0u;
+      if (tid < M * 2) {
+        red[(size_t)((t + 2) % 3) * M * 2 + tid] = 0u;
+        if (kGrid && rank == 0) tk.xslot[(size_t)((t + 2) % 3) * M * 2 + tid] = 0u;
+      }
     }
     ++t;
     ++loops;
@@ -568,7 +657,8 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
     }
   }
   if (tk.fin_out && rank == 0 && tid == 0) *tk.fin_out = all_done;
-  cluster.sync();  // no CTA leaves while a peer could still address its shared memory
+  if constexpr (!kGrid)
+    cluster.sync();  // no CTA leaves while a peer could still address its shared memory
 }
 
 size_t oem_iter_smem_fixed(int p, int npen, int max_rows, int precision) {
@@ -582,13 +672,11 @@ size_t oem_iter_smem_per_row(int p, int precision) {
   return (size_t)((p + 3) & ~3) * tsz;
 }
 
-template <typename T, int M>
+template <typename T, int M, bool kGrid>
 static cudaError_t launch_t(const IterLaunch& P, cudaStream_t s, bool query, int* out) {
   constexpr int NT = iter_threads<T, M>();
-  auto kfn = oem_iter_kernel<T, M, NT>;
+  auto kfn = oem_iter_kernel<T, M, NT, kGrid>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(P.ntasks * P.C));
@@ -596,10 +684,23 @@ static cudaError_t launch_t(const IterLaunch& P, cudaStream_t s, bool query, int
   cfg.dynamicSmemBytes = P.smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = P.C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
+  if constexpr (kGrid) {
+    if (query) {
+      int n = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kfn, NT, P.smem);
+      *out = (e == cudaSuccess) ? n : 0;
+      return e;
+    }
+    attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs resident, or no launch
+    attr[0].val.cooperative = 1;
+  } else {
+    e = cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = P.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+  }
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (query) {
@@ -611,13 +712,18 @@ static cudaError_t launch_t(const IterLaunch& P, cudaStream_t s, bool query, int
   return cudaLaunchKernelEx(&cfg, kfn, P);
 }
 
+template <typename T, int M>
+static cudaError_t dispatch_g(const IterLaunch& P, cudaStream_t s, bool q, int* out) {
+  return P.grid ? launch_t<T, M, true>(P, s, q, out) : launch_t<T, M, false>(P, s, q, out);
+}
+
 template <typename T>
 static cudaError_t dispatch_m(const IterLaunch& P, cudaStream_t s, bool q, int* out) {
   switch (P.M) {
-    case 1: return launch_t<T, 1>(P, s, q, out);
-    case 2: return launch_t<T, 2>(P, s, q, out);
-    case 4: return launch_t<T, 4>(P, s, q, out);
-    default: return launch_t<T, 8>(P, s, q, out);
+    case 1: return dispatch_g<T, 1>(P, s, q, out);
+    case 2: return dispatch_g<T, 2>(P, s, q, out);
+    case 4: return dispatch_g<T, 4>(P, s, q, out);
+    default: return dispatch_g<T, 8>(P, s, q, out);
   }
 }
 

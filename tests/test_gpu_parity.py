@@ -292,8 +292,9 @@ def test_cv_matches_oracle(oem, ctx, mode):
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_iteration_layouts_give_identical_paths(oem, ctx, precision):
     # Each (row, instance) sum is formed in the same order whatever the
-    # cluster size and however the penalties are grouped into tasks, so every
-    # layout, and the one the autotuner picks, returns the same bits.
+    # cluster size, cluster or grid mode, and however the penalties are
+    # grouped into tasks, so every layout, and the one the autotuner picks,
+    # returns the same bits.
     p, n = 130, 4000
     X, y = _data(n, p, 21, np.float64)
     G, c, N, _ = oracle.gram_sums(X, y)
@@ -302,7 +303,8 @@ def test_iteration_layouts_give_identical_paths(oem, ctx, precision):
     gp, op = _pens(p, PENS)
     runs = []
     for ncl, mg, tune in [(4, 8, False), (1, 1, False), (16, 1, False), (2, 2, False),
-                          (8, 4, False), (0, 0, True), (0, 0, True), (0, 0, False)]:
+                          (8, 4, False), (32, 1, False), (24, 8, False), (30, 2, False),
+                          (0, 0, True), (0, 0, True), (0, 0, False)]:
         out = oem.oem_fit_path(ctx, _dev(G), _dev(c), gp, d=d, nlambda=20, lambda_min_ratio=1e-2,
                                tol=1e-8, cluster_ctas=ncl, instances_per_task=mg, autotune=tune,
                                iter_precision=precision)
