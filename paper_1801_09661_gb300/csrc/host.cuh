@@ -208,6 +208,11 @@ struct GramPlan {
   int max_chunks;
   int K;
   bool sorted;
+  // TMA-fed tensor-core path (split-BF16 / bfloat16): packed copy of Z
+  bool tma = false;
+  int32_t qp = 0;
+  int64_t rows_cap = 0;
+  int pmax_chunks = 0;
 };
 
 inline GramPlan plan_gram(oem_ctx* ctx, int64_t n, int64_t p, int K, int32_t mode, bool sorted) {
@@ -229,6 +234,17 @@ inline GramPlan plan_gram(oem_ctx* ctx, int64_t n, int64_t p, int K, int32_t mod
   g.chunk_rows = cr;
   g.max_chunks = (int)((n + cr - 1) / cr + K);
   g.nblk = (n + 1023) / 1024;
+  // the TMA path needs a bfloat16 copy of Z (hi, and lo in split mode); it
+  // is taken while that copy uses at most half of the context's budget,
+  // otherwise the converting kernel reads X directly
+  if (mode == OEM_GRAM_SPLIT_BF16 || mode == OEM_GRAM_BF16) {
+    g.qp = (g.q + 127) / 128 * 128;
+    g.rows_cap = n + 32 * (int64_t)K;
+    g.pmax_chunks = (int)((g.rows_cap + cr - 1) / cr + K);
+    const size_t bytes = (size_t)g.rows_cap * g.qp * 2 * (mode == OEM_GRAM_SPLIT_BF16 ? 2 : 1);
+    const size_t partial = (size_t)g.pmax_chunks * g.ntiles * g.T * g.T * sizeof(double);
+    g.tma = bytes + partial <= ctx->budget / 2;
+  }
   return g;
 }
 
@@ -237,6 +253,8 @@ struct GramBufs {
   ChunkTable ct{};
   double* partial = nullptr;
   double* Zg = nullptr;
+  TmaBufs t{};
+  uint16_t *zhi = nullptr, *zlo = nullptr;
 };
 
 inline void gram_request(Arena& A, const GramPlan& g, int64_t n, GramBufs& b) {
@@ -251,8 +269,18 @@ inline void gram_request(Arena& A, const GramPlan& g, int64_t n, GramBufs& b) {
   A.add(&b.ct.count, 1);
   A.add(&b.ct.fold_c0, (size_t)g.K + 1);
   A.add(&b.ct.fold_off, (size_t)g.K + 1);
-  A.add(&b.partial, (size_t)g.max_chunks * g.ntiles * g.T * g.T);
+  A.add(&b.partial, (size_t)(g.tma ? g.pmax_chunks : g.max_chunks) * g.ntiles * g.T * g.T);
   A.add(&b.Zg, (size_t)g.K * g.q * g.q);
+  if (g.tma) {
+    A.add(&b.zhi, (size_t)g.rows_cap * g.qp);
+    if (g.mode == OEM_GRAM_SPLIT_BF16) A.add(&b.zlo, (size_t)g.rows_cap * g.qp);
+    A.add(&b.t.pc.row0, (size_t)g.pmax_chunks);
+    A.add(&b.t.pc.row1, (size_t)g.pmax_chunks);
+    A.add(&b.t.pc.fold, (size_t)g.pmax_chunks);
+    A.add(&b.t.pc.count, 1);
+    A.add(&b.t.pc.fold_c0, (size_t)g.K + 1);
+    A.add(&b.t.pc.fold_off, (size_t)g.K + 1);
+  }
 }
 
 // fold sort (if any) -> chunk table -> Gram partials -> per-fold Z Grams.
@@ -272,6 +300,23 @@ inline int run_gram(oem_ctx* ctx, const GramPlan& g, GramBufs& b, const void* X,
   a.perm = g.sorted ? b.perm : nullptr;
   a.mode = g.mode; a.q = g.q; a.ycols = g.ycols; a.T = g.T; a.ntile1 = g.nt; a.ntiles = g.ntiles;
   a.ct = b.ct; a.max_chunks = g.max_chunks; a.partial = b.partial; a.dstatus = ctx->dstatus;
+  if (g.tma) {
+    b.t.zhi = b.zhi;
+    b.t.zlo = b.zlo;
+    b.t.qp = g.qp;
+    b.t.rows_cap = g.rows_cap;
+    b.t.max_chunks = g.pmax_chunks;
+    b.t.chunk_rows = g.chunk_rows;
+    // split mode (4 products) flushes every 64 rows, bfloat16 every 256 (see
+    // below)
+    const int flush = g.mode == OEM_GRAM_SPLIT_BF16 ? 64 : 256;
+    LAUNCH(OEM_PROF_GRAM_TC, launch_zpack(a, g.K, b.t, s));
+    LAUNCH(OEM_PROF_GRAM_TC, launch_gram_tma(a, b.t, flush, s));
+    GramArgs r = a;
+    r.ct.fold_c0 = b.t.pc.fold_c0;
+    LAUNCH(OEM_PROF_GRAM_REDUCE, launch_gram_reduce(r, g.K, b.Zg, s));
+    return OEM_OK;
+  }
   if (tc_mode(g.mode)) {
     // Rows summed in float32 tensor memory before the compensated flush. The
     // tensor cores' float32 accumulation rounds toward zero, so the error

@@ -54,6 +54,19 @@ struct GramArgs {
   unsigned* dstatus;
 };
 
+// Packed bfloat16 copy of Z for the TMA-fed Gram kernel (split-BF16 and
+// bfloat16 modes): every fold's rows padded with zero rows to a multiple of
+// 32, qp = round_up(q, 128) columns.
+struct TmaBufs {
+  void* zhi;            // [rows_cap][qp] bfloat16
+  void* zlo;            // [rows_cap][qp] bfloat16 (split mode) or NULL
+  int32_t qp;
+  int64_t rows_cap;     // n + 32 K
+  ChunkTable pc;        // chunks of packed rows; pc.fold_off = packed fold offsets
+  int32_t max_chunks;
+  int64_t chunk_rows;
+};
+
 // tile index -> (ti, tj), ti <= tj, row-major over the upper triangle
 __host__ __device__ inline void tile_coords(int t, int nt, int* ti, int* tj) {
   int i = 0, rem = t;
@@ -80,6 +93,10 @@ cudaError_t launch_check_finite(const void* X, int32_t xtype, int64_t n, int64_t
 
 // Reduce partials into per-fold raw Grams of Z (float64, full symmetric,
 // [K][q][q]).
+size_t gram_tma_smem_bytes();
+// packed chunk table + the packing pass (fold order, zero-padded folds)
+cudaError_t launch_zpack(const GramArgs& a, int K, const TmaBufs& t, cudaStream_t s);
+cudaError_t launch_gram_tma(const GramArgs& a, const TmaBufs& t, int flush_rows, cudaStream_t s);
 cudaError_t launch_gram_reduce(const GramArgs& a, int K, double* Zg, cudaStream_t s);
 
 // Extract per-fold X^T X, X^T y, y^T y from Z Grams (raw) in the public layout.

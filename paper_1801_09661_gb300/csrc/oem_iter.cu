@@ -376,6 +376,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
         for (int q = 0; q < 16; ++q) acc[q] = T(0);
         if (gb + nv <= smem_rows) {
           const T* g0 = Gs + (size_t)gb * ldgs;
+#pragma unroll 4
           for (int j = lane; j < p; j += 32) {
             T dv[M];
             load_col<T, M>(Dc, j, dv);
@@ -393,6 +394,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
             const int ib = gb + min(r, nv - 1);
             gr[r] = ib < smem_rows ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
           }
+#pragma unroll 4
           for (int j = lane; j < p; j += 32) {
             T dv[M];
             load_col<T, M>(Dc, j, dv);

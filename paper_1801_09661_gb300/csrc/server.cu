@@ -155,6 +155,9 @@ void plan_job(oem_server* S, SrvJob* J) {
   const int64_t n = j.n, p = j.p;
   const int L = j.nlambda, B = J->B;
   J->gp = plan_gram(S->ctx, n, p, J->K > 0 ? J->K : 1, J->gram_mode, J->K > 0);
+  // the converting Gram kernel reads X in place: no packed copy of X counts
+  // against the serving budget while jobs prepare
+  J->gp.tma = false;
   const GramPlan& g = J->gp;
   J->q = g.q;
   J->ycols = g.ycols;
