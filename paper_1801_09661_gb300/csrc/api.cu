@@ -172,11 +172,7 @@ int oem_spectral_d(oem_ctx* ctx, const double* G, int64_t p, int64_t ldg, int32_
   CU(cudaSetDevice(ctx->device));
   LanczosWork w{};
   Arena A;
-  A.add(&w.V, (size_t)batch * 3 * p);
-  A.add(&w.alpha, (size_t)batch * 128);
-  A.add(&w.beta, (size_t)batch * 128);
-  A.add(&w.fro, (size_t)batch);
-  A.add(&w.mlen, (size_t)batch);
+  lanczos_request(A, w, p, batch, steps);
   int r;
   if ((r = arena_commit(ctx, A, s))) return r;
   cudaError_t e = lanczos_prof(ctx, s, G, p, ldg, batch, strideG, steps, w, d, s, &ctx->launches);
@@ -234,11 +230,7 @@ int oem_fit_path(oem_ctx* ctx, const double* G, const double* c, int64_t p, doub
   Arena A;
   if (opt->iter_precision == OEM_ITER_F32) A.add(&G32, (size_t)p * ldg32);
   A.add(&dd, 1);
-  A.add(&w.V, (size_t)3 * p);
-  A.add(&w.alpha, 128);
-  A.add(&w.beta, 128);
-  A.add(&w.fro, 1);
-  A.add(&w.mlen, 1);
+  lanczos_request(A, w, p, 1, opt->lanczos_steps);
   pens_request(A, P);
   iter_request(A, p, 1, I);
   if ((r = arena_commit(ctx, A, s))) return r;
@@ -284,11 +276,7 @@ int oem_fit(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, in
   A.add(&N, 1);
   A.add(&cnt, 1);
   A.add(&dd, 1);
-  A.add(&w.V, (size_t)3 * p);
-  A.add(&w.alpha, 128);
-  A.add(&w.beta, 128);
-  A.add(&w.fro, 1);
-  A.add(&w.mlen, 1);
+  lanczos_request(A, w, p, 1, opt->lanczos_steps);
   pens_request(A, P);
   iter_request(A, p, 1, I);
   if ((r = arena_commit(ctx, A, s))) return r;
@@ -340,11 +328,7 @@ int oem_cv(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, int
   A.add(&N, (size_t)B);
   A.add(&cnt, (size_t)B);
   A.add(&dd, (size_t)B);
-  A.add(&w.V, (size_t)B * 3 * p);
-  A.add(&w.alpha, (size_t)B * 128);
-  A.add(&w.beta, (size_t)B * 128);
-  A.add(&w.fro, (size_t)B);
-  A.add(&w.mlen, (size_t)B);
+  lanczos_request(A, w, p, B, opt->lanczos_steps);
   A.add(&beta_all, (size_t)B * npen * L * p);
   A.add(&it_all, (size_t)B * npen * L);
   A.add(&cv_all, (size_t)B * npen * L);

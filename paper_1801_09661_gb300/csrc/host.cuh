@@ -107,7 +107,7 @@ inline cudaError_t lanczos_prof(oem_ctx* ctx, cudaStream_t s, const double* G, i
   const int64_t before = *launches;
   cudaEvent_t e0 = ctx->prof ? prof_event(ctx) : nullptr;
   if (e0) cudaEventRecord(e0, s);
-  cudaError_t e = launch_lanczos(G, p, ldg, batch, strideG, steps, w, d, s2, launches);
+  cudaError_t e = launch_lanczos(G, p, ldg, batch, strideG, steps, w, d, ctx->dstatus, s2, launches);
   if (e0) {
     cudaEvent_t e1 = prof_event(ctx);
     if (e1) {
@@ -131,6 +131,18 @@ struct Arena {
     return t;
   }
 };
+
+// Lanczos work space for `batch` Grams of order p.
+template <typename A>
+inline void lanczos_request(A& ar, LanczosWork& w, int64_t p, int batch, int steps) {
+  ar.add(&w.V, (size_t)batch * (lanczos_steps_eff(steps, p) + 3) * p);
+  ar.add(&w.alpha, (size_t)batch * 128);
+  ar.add(&w.beta, (size_t)batch * 128);
+  ar.add(&w.fro, (size_t)batch);
+  ar.add(&w.mlen, (size_t)batch);
+  ar.add(&w.bar, (size_t)batch * 2);
+  ar.add(&w.part, (size_t)batch * kLzGroupMax * kLzPartStride);
+}
 
 inline int arena_commit(oem_ctx* ctx, Arena& A, cudaStream_t s) {
   const size_t need = A.total();

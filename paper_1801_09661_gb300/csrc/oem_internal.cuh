@@ -111,15 +111,69 @@ cudaError_t launch_assemble(const double* Zg, int K, int q, int p, int ycols,
                             int ldg32, double* c, double* N, double* cnt, cudaStream_t s);
 
 // Lanczos d for a batch of float64 Grams.
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Barrier of the nctas CTAs of one task in a cooperative launch (all of them
+// resident): bar[0] counts arrivals, bar[1] is the generation; gen is the
+// caller's copy of the generation (thread 0). Every wait is bounded (about
+// 2 s at 2 GHz); returns false in every thread of the CTA on timeout.
+__device__ __forceinline__ bool group_barrier(unsigned* bar, unsigned nctas, unsigned& gen) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    const unsigned g = gen;
+    __threadfence();  // this CTA's global writes before its arrival
+    if (atomicAdd(&bar[0], 1u) == nctas - 1) {
+      atomicExch(&bar[0], 0u);  // nobody arrives again before the generation moves
+      __threadfence();
+      atomicExch(&bar[1], g + 1);
+    } else {
+      const long long t0 = clock64();
+      int spins = 0;
+      while (ld_acquire_gpu(&bar[1]) == g) {
+        if (++spins > 8) __nanosleep(32);  // fewer polls on the shared line
+        if (clock64() - t0 > 4000000000LL) { ok = 0; break; }
+      }
+    }
+    __threadfence();
+    gen = g + 1;
+  }
+  return __syncthreads_and(ok) != 0;
+}
+#endif
+
 struct LanczosWork {
-  double* V;       // [batch][3][p] rolling vectors
+  double* V;       // [batch][steps + 3][p]: basis v_0 .. v_steps, w by step parity
   double* alpha;   // [batch][steps]
   double* beta;    // [batch][steps]
   double* fro;     // [batch]
   int32_t* mlen;   // [batch] steps taken
+  unsigned* bar;   // [batch][2] barrier words of each Gram's CTA group
+  double* part;    // [batch][kLzGroupMax][kLzPartStride] per-CTA partial sums
 };
+constexpr int kLzGroupMax = 256;  // CTAs serving one Gram at most
+constexpr int kLzMax = 128;       // longest recurrence kept per Gram
+constexpr int kLzPartStride = 2 * kLzMax + 1;
+// Lanczos steps actually taken for a request of `steps` (0 = 64) at order p.
+inline int lanczos_steps_eff(int steps, int64_t p) {
+  if (steps <= 0) steps = 64;
+  if (steps > kLzMax) steps = kLzMax;
+  if (steps > p) steps = (int)p;
+  return steps < 1 ? 1 : steps;
+}
 cudaError_t launch_lanczos(const double* G, int64_t p, int64_t ldg, int batch, int64_t strideG,
-                           int steps, LanczosWork w, double* d, cudaStream_t s, int64_t* launches);
+                           int steps, LanczosWork w, double* d, unsigned* dstatus, cudaStream_t s,
+                           int64_t* launches);
 
 // Penalty descriptor on the device.
 struct DevPenalty {

@@ -140,41 +140,6 @@ __device__ __forceinline__ float from_red(unsigned int b) { return __uint_as_flo
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Barrier of the nctas CTAs of one task in a cooperative launch (all of them
-// resident): bar[0] counts arrivals, bar[1] is the generation; gen is the
-// caller's copy of the generation (thread 0). Every wait is bounded (about
-// 2 s at 2 GHz); returns false in every thread of the CTA on timeout.
-__device__ __forceinline__ bool group_barrier(unsigned* bar, unsigned nctas, unsigned& gen) {
-  __syncthreads();
-  int ok = 1;
-  if (threadIdx.x == 0) {
-    const unsigned g = gen;
-    __threadfence();  // this CTA's global writes before its arrival
-    if (atomicAdd(&bar[0], 1u) == nctas - 1) {
-      atomicExch(&bar[0], 0u);  // nobody arrives again before the generation moves
-      __threadfence();
-      atomicExch(&bar[1], g + 1);
-    } else {
-      const long long t0 = clock64();
-      while (ld_acquire_gpu(&bar[1]) == g)
-        if (clock64() - t0 > 4000000000LL) { ok = 0; break; }
-    }
-    __threadfence();
-    gen = g + 1;
-  }
-  return __syncthreads_and(ok) != 0;
-}
 
 // Shared-memory carve-up (byte offsets, 16-byte aligned). The dbeta buffers
 // have ldgs = round_up(p, 4) rows; rows p.. stay zero.

@@ -173,11 +173,7 @@ void plan_job(oem_server* S, SrvJob* J) {
   A.add(&J->G64, (size_t)B * p * p);
   A.add(&J->N, (size_t)B);
   A.add(&J->cnt, (size_t)B);
-  A.add(&J->lw.V, (size_t)B * 3 * p);
-  A.add(&J->lw.alpha, (size_t)B * 128);
-  A.add(&J->lw.beta, (size_t)B * 128);
-  A.add(&J->lw.fro, (size_t)B);
-  A.add(&J->lw.mlen, (size_t)B);
+  lanczos_request(A, J->lw, p, B, 64);
   Arena& R = J->res;
   R.req.clear();
   R.add(&J->ct.row0, (size_t)g.max_chunks);
