@@ -65,47 +65,76 @@ def penalties_of(w):
 
 
 class ClockSampler:
-    """nvidia-smi samples (200 ms) while the timed region runs."""
+    """nvidia-smi samples (every 100 ms) with host timestamps. start() waits
+    for the first sample so that the sampler is running when the timed region
+    begins; mark(t0, t1) records the timed region; stop() keeps the samples
+    inside it (or the nearest one when the region is shorter than the
+    sampling period, flagged)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
-        self.proc = None
+        import threading
+        self.proc, self.lines, self.t0, self.t1 = None, [], None, None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(gpu_index)],
+                 "-lms", "100", "-i", str(gpu_index)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        t_end = time.time() + 5.0
+        while not self.lines and time.time() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line))
+
+    def mark(self, t0, t1):
+        self.t0, self.t1 = t0, t1
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)  # one more period after the region
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-            out = ""
-        sm, smax, reasons = [], [], set()
+        self.thread.join(timeout=2)
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        for ts, line in self.lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                rows.append((ts, float(f[1]), float(f[2]), f[5:9]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
+        inside = [r for r in rows if self.t0 is not None and self.t0 <= r[0] <= self.t1 + 0.1]
+        nearest = False
+        if not inside and rows and self.t0 is not None:
+            mid = 0.5 * (self.t0 + self.t1)
+            inside = [min(rows, key=lambda r: abs(r[0] - mid))]
+            nearest = True
+        reasons = set()
+        for r in inside:
+            for nm, v in zip(names, r[3]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+        out = {"sm_mhz": statistics.median([r[1] for r in inside]) if inside else None,
+               "sm_max_mhz": max(r[2] for r in inside) if inside else None,
+               "samples": len(inside), "reasons": sorted(reasons)}
+        if nearest:
+            out["note"] = "timed region shorter than the 100 ms sampling period: nearest sample"
+        return out
 
 
 # ---------------------------------------------------------------------------
@@ -214,11 +243,13 @@ def run_ours(args, w, rank, world, local_rank):
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tw0 = time.time()
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks.mark(tw0, time.time())
     barrier()
     ms = e0.elapsed_time(e1)
     launches = ctx.launches() - l0
@@ -331,13 +362,29 @@ def run_ours(args, w, rank, world, local_rank):
         "converged_frac": float(conv_h.mean()),
         "datagen_s": t_gen,
     }
+    # serving: Poisson arrivals of mixed fit / CV jobs, served (batched) vs plain
+    if args.serving_requests > 0 and world == 1:
+        served, same, sclk = serving_measure(args, rank, local_rank, args.serving_requests,
+                                             args.plain_requests)
+        line["serving"] = {"requests": served["requests"], "rate_per_s": args.rate,
+                           "paths_per_s": served["paths_per_s"], "latency_ms": served["latency_ms"],
+                           "batched_over_plain": same["batched_over_plain"],
+                           "same_requests": same, "clocks": sclk}
     if not args.no_cpu_baseline:
+        # the oracle on the full workload, repeated (fresh seeds) until about
+        # 10 s of CPU work
         n_sample = min(w.n, args.cpu_sample_rows)
-        scaled, raw = oracle_step(w, n_sample)
+        tot_scaled, tot_raw, reps = 0.0, 0.0, 0
+        while reps == 0 or tot_raw < args.cpu_seconds:
+            scaled, raw = oracle_step(w, n_sample, seed_shift=reps)
+            tot_scaled += scaled
+            tot_raw += raw
+            reps += 1
         line["cpu_baseline"] = {
-            "value": npen / scaled, "unit": "paths/s", "cores": cpu_cores(), "kind": "oracle",
-            "sample": (f"Gram of the first {n_sample} of {w.n} rows (time scaled by n/{n_sample}),"
-                       f" then d and {npen} x {w.nlambda}-lambda paths; {raw:.1f} s of CPU work")}
+            "value": npen * reps / tot_scaled, "unit": "paths/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": (f"{reps} oracle steps, each the Gram of {n_sample} of {w.n} rows"
+                       + (f" (time scaled by n/{n_sample})" if n_sample < w.n else "")
+                       + f", d and {npen} x {w.nlambda}-lambda paths; {tot_raw:.1f} s of CPU work")}
     ctx.close()
     print(json.dumps(line), flush=True)
     return 0
@@ -347,19 +394,20 @@ def run_ours(args, w, rank, world, local_rank):
 # Serving: Poisson arrivals of mixed fit / CV jobs, served (batched) vs plain
 # ---------------------------------------------------------------------------
 
-def run_serving(args, rank, world, local_rank):
+def serving_measure(args, rank, local_rank, nreq, nplain):
     """Requests arrive as a Poisson stream (50/s); each has n log-uniform in
     [1e4, 2e6], p uniform in [20, 1000], float32 AR(0.5) rows, 30% 5-fold CV,
     lasso or MCP (gamma 3) with 50 lambdas. The batched server admits them
     under a 150 GB budget and runs them with continuous batching; latency is
     submission -> results in host memory. The plain per-job form runs the
-    first --plain-requests of them (submitted at once) for the throughput
-    comparison, against the batched form on the same requests."""
+    first nplain of them (submitted at once) for the throughput comparison,
+    against the batched form on the same requests. Returns (served,
+    same_requests, clocks)."""
     import torch
     import paper_1801_09661_gb300 as oem
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    reqs = synthgen.serving_requests(args.requests, seed=5 + 1000 * rank, rate_per_s=args.rate)
+    reqs = synthgen.serving_requests(nreq, seed=5 + 1000 * rank, rate_per_s=args.rate)
     n_max = max(r["n"] for r in reqs)
     bases = [synthgen.device_ar1_base(n_max, 1000, 0.5, 77 + b, device=dev) for b in range(2)]
     data = [synthgen.device_request_data(bases[r["id"] % 2], r) for r in reqs]
@@ -378,6 +426,7 @@ def run_serving(args, rank, world, local_rank):
     srv = oem.Server(local_rank, budget_bytes=int(args.budget_gb * (1 << 30)), form="batched",
                      iters_per_round=args.iters_per_round)
     clocks = ClockSampler(local_rank)
+    tw0 = time.time()
     t0 = time.perf_counter()
     ids = []
     for r, d in zip(reqs, data):
@@ -390,6 +439,7 @@ def run_serving(args, rank, world, local_rank):
         st, l, rc = srv.wait(i, 3600)
         lat.append(l)
     wall = time.perf_counter() - t0
+    clocks.mark(tw0, time.time())
     clk = clocks.stop()
     st_b = srv.stats()
     srv.close()
@@ -403,7 +453,7 @@ def run_serving(args, rank, world, local_rank):
               "peak_device_bytes": st_b["peak_bytes"]}
 
     # ---- throughput on the same requests: batched vs plain, all submitted at once
-    m = min(args.plain_requests, len(reqs))
+    m = min(nplain, len(reqs))
     out = {}
     for form in ("batched", "plain"):
         s2 = oem.Server(local_rank, budget_bytes=int(args.budget_gb * (1 << 30)), form=form,
@@ -422,21 +472,32 @@ def run_serving(args, rank, world, local_rank):
               for a, b in zip(out["batched"]["betas"], out["plain"]["betas"]))
     for f in out.values():
         f.pop("betas")
+    same = {"requests": m, "batched": out["batched"], "plain": out["plain"],
+            "batched_over_plain": out["batched"]["paths_per_s"] / out["plain"]["paths_per_s"],
+            "max_rel_beta_diff": acc}
+    del bases, data
+    torch.cuda.empty_cache()
+    return served, same, clk
+
+
+def run_serving(args, rank, world, local_rank):
+    """The serving workload on its own line (see serving_measure)."""
+    served, same, clk = serving_measure(args, rank, local_rank, args.requests, args.plain_requests)
     if rank != 0:
         return 0
+    wall = served["wall_s"]
+    nreq = served["requests"]
     line = {
         "metric": "fitted paths/s (served, Poisson arrivals)", "value": served["paths_per_s"],
-        "unit": "paths/s", "n_gpus": world, "steps": len(reqs), "warmup": 0,
-        "ms_per_step": 1000.0 * wall / len(reqs), "higher_is_better": True, "scaling": "weak",
+        "unit": "paths/s", "n_gpus": world, "steps": nreq, "warmup": 0,
+        "ms_per_step": 1000.0 * wall / nreq, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "serving", "requests": len(reqs), "rate_per_s": args.rate,
+        "config": {"workload": "serving", "requests": nreq, "rate_per_s": args.rate,
                    "n": "log-uniform [1e4, 2e6]", "p": "uniform [20, 1000]", "cv_frac": 0.3,
                    "K": 5, "nlambda": 50, "penalties": ["lasso", "mcp"],
                    "budget_gb": args.budget_gb, "iters_per_round": args.iters_per_round},
         "served": served,
-        "same_requests": {"requests": m, "batched": out["batched"], "plain": out["plain"],
-                          "batched_over_plain": out["batched"]["paths_per_s"] / out["plain"]["paths_per_s"],
-                          "max_rel_beta_diff": acc},
+        "same_requests": same,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -458,7 +519,12 @@ def main():
     ap.add_argument("--iters-per-round", type=int, default=1000)
     ap.add_argument("--gram-mode", default="auto",
                     choices=["auto", "split_bf16", "tf32", "fp32", "fp64", "bf16"])
-    ap.add_argument("--cpu-sample-rows", type=int, default=100_000)
+    ap.add_argument("--cpu-sample-rows", type=int, default=1_000_000,
+                    help="rows per oracle step of the CPU baseline (time scaled to n)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="CPU baseline: repeat oracle steps until this much CPU work")
+    ap.add_argument("--serving-requests", type=int, default=200,
+                    help="requests of the serving measurement added to the default line (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -191,20 +191,26 @@ __global__ void __launch_bounds__(kLzThreads) lz_steps_kernel(const double* __re
 // (chi_{k-1}, chi_k) is rescaled by a power of two when it leaves
 // [2^-400, 2^400], which keeps every sign; an exact zero takes the sign of its
 // predecessor (the usual convention: a zero pivot counts as positive).
-__device__ int sturm_below(const double* a, const double* e, int m, double x) {
+__device__ int sturm_below(const double* a, const double* e2, int m, double x) {
+  // e2[i] = e_i^2 (precomputed). Float64 work per step: one add, one
+  // multiply, one fma; the sign test reads the sign bits, and the rescaling
+  // test runs every 8 steps (a pair grows by at most (|a|+|x|+|e|)^8 between
+  // tests, far inside the 2^+-400 window).
   int cnt = 0;
   double c0 = 1.0, c1 = a[0] - x;
   if (c1 == 0.0) c1 = 0x1p-600;
-  if (c1 < 0.0) ++cnt;
+  cnt += __double2hiint(c1) < 0;
   for (int i = 1; i < m; ++i) {
-    double c2 = fma(a[i] - x, c1, -(e[i - 1] * e[i - 1]) * c0);
+    double c2 = fma(a[i] - x, c1, -e2[i - 1] * c0);
     if (c2 == 0.0) c2 = copysign(0x1p-600, c1) * fmax(fabs(c1), 0x1p-400);
-    if ((c2 < 0.0) != (c1 < 0.0)) ++cnt;
+    cnt += (__double2hiint(c2) ^ __double2hiint(c1)) < 0;
     c0 = c1;
     c1 = c2;
-    const double mag = fmax(fabs(c0), fabs(c1));
-    if (mag > 0x1p400) { c0 *= 0x1p-400; c1 *= 0x1p-400; }
-    else if (mag < 0x1p-400) { c0 *= 0x1p400; c1 *= 0x1p400; }
+    if ((i & 7) == 0) {
+      const int ex = max((__double2hiint(c0) >> 20) & 0x7FF, (__double2hiint(c1) >> 20) & 0x7FF);
+      if (ex > 1023 + 400) { c0 *= 0x1p-400; c1 *= 0x1p-400; }
+      else if (ex < 1023 - 400) { c0 *= 0x1p400; c1 *= 0x1p400; }
+    }
   }
   return cnt;
 }
@@ -251,6 +257,12 @@ __global__ void lz_finish_kernel(LanczosWork w, int steps, double* d) {
   // Coarse rounds in float32 down to a relative width of 1e-5, widened by a
   // margin and checked in float64; then float64 rounds.
   const int lane = threadIdx.x;
+  __shared__ double ad[kLzMax], e2d[kLzMax];
+  for (int i = lane; i < m; i += 32) {
+    ad[i] = a[i];
+    e2d[i] = e[i] * e[i];
+  }
+  __syncwarp();
   {
     __shared__ float af[kLzMax], e2f[kLzMax];
     for (int i = lane; i < m; i += 32) {
@@ -275,14 +287,14 @@ __global__ void lz_finish_kernel(LanczosWork w, int steps, double* d) {
     // widen by 1e-4 of the scale and keep it only if float64 counts confirm it
     const double mg = 1e-4 * (double)scale + 1e-300;
     const double tlo = fmax(lo, (double)flo - mg), thi = fmin(hi, (double)fhi + mg);
-    const bool ok_lo = lane == 0 ? sturm_below(a, e, m, tlo) < m : true;
-    const bool ok_hi = lane == 1 ? sturm_below(a, e, m, thi) >= m : true;
+    const bool ok_lo = lane == 0 ? sturm_below(ad, e2d, m, tlo) < m : true;
+    const bool ok_hi = lane == 1 ? sturm_below(ad, e2d, m, thi) >= m : true;
     if (__all_sync(0xffffffffu, ok_lo && ok_hi)) { lo = tlo; hi = thi; }
   }
   for (int it = 0; it < 40; ++it) {
     const double wd = (hi - lo) / 33.0;
     const double x = lo + wd * (lane + 1);
-    const bool above = (x < hi) && (x > lo) ? sturm_below(a, e, m, x) >= m : (x >= hi);
+    const bool above = (x < hi) && (x > lo) ? sturm_below(ad, e2d, m, x) >= m : (x >= hi);
     const unsigned mask = __ballot_sync(0xffffffffu, above);
     const int first = mask ? __ffs(mask) - 1 : 32;  // first tested point above theta
     const double nlo = first == 0 ? lo : lo + wd * first;
