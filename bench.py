@@ -34,6 +34,14 @@ sys.path.insert(0, ROOT)
 import synthgen  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one ncu
+# capture per kernel, for the bench workload's p = 500 at n = 200,000. The
+# iteration reads its Gram once per launch (independent of n); the Gram pass
+# moves bytes in proportion to n (scaled to the full n below). Set to None
+# whenever the kernel changes, until it is captured again.
+NCU_DRAM_BYTES = {"oem_iter_kernel": 1.0752e6,
+                  "gram_tma_kernel_per_row": (423.24096e6 + 63.771904e6) / 200_000}
+
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 WORKLOAD = "four_penalties_f32_n1e6_p500"
 
@@ -271,26 +279,41 @@ def run_ours(args, w, rank, world, local_rank):
     lh = torch.empty(lam.shape, dtype=lam.dtype).pin_memory()
     ih = torch.empty(its.shape, dtype=its.dtype).pin_memory()
     ch = torch.empty(conv.shape, dtype=conv.dtype).pin_memory()
-    Xe = torch.empty_like(Xd)
-    ye = torch.empty_like(yd)
+    # inputs double-buffered: the copy of step k + 1 (copy stream) overlaps
+    # the fit of step k (compute stream); a buffer is refilled only after the
+    # fit that read it; results are read back after each fit
+    cs = torch.cuda.Stream(dev)
+    xin = [(torch.empty_like(Xd), torch.empty_like(yd)) for _ in range(2)]
+    copied = [torch.cuda.Event() for _ in range(2)]
+    done = [torch.cuda.Event() for _ in range(2)]
+    for e in done:
+        e.record(stream)
 
-    def e2e_step():
-        Xe.copy_(Xh, non_blocking=True)
-        ye.copy_(yh, non_blocking=True)
-        oem.oem_fit(ctx, Xe, ye, pens, out=out, **opts)
+    def e2e_step(k):
+        b = k % 2
+        Xb, yb = xin[b]
+        with torch.cuda.stream(cs):
+            cs.wait_event(done[b])
+            Xb.copy_(Xh, non_blocking=True)
+            yb.copy_(yh, non_blocking=True)
+            copied[b].record(cs)
+        stream.wait_event(copied[b])
+        oem.oem_fit(ctx, Xb, yb, pens, out=out, stream=stream.cuda_stream, **opts)
         bh.copy_(beta, non_blocking=True)
         lh.copy_(lam, non_blocking=True)
         ih.copy_(its, non_blocking=True)
         ch.copy_(conv, non_blocking=True)
+        done[b].record(stream)
 
-    e2e_step()
+    e2e_step(0)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
+    cs.wait_event(f0)
+    for k in range(args.steps):
+        e2e_step(k)
     f1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -317,9 +340,10 @@ def run_ours(args, w, rank, world, local_rank):
     it_gbs = it_bytes / (it_ms_launch / 1000.0) / 1e9
     hbm = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
     # the Gram pass (tensor cores): useful flops n (p+1)(p+2)
-    gk = "gram_tc_kernel" if "gram_tc_kernel" in prof else "gram_simt_kernel"
+    gk = "gram_tc_pass" if "gram_tc_pass" in prof else "gram_simt_kernel"
     g_ms, g_n = prof.get(gk, (float("nan"), 0))
-    g_ms_launch = g_ms / max(1, g_n)
+    # one pass per step (the TMA path is two launches: packing + SYRK)
+    g_ms_launch = g_ms / max(1, args.steps)
     g_flops = w.n * (p + 1) * (p + 2)
     g_tf = g_flops / (g_ms_launch / 1000.0) / 1e12
     nprod = 4 if args.gram_mode in ("auto", "split_bf16") else 1
@@ -344,16 +368,20 @@ def run_ours(args, w, rank, world, local_rank):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "roofline": {"kernel": "oem_iter_kernel", "bound": "hbm", "achieved": it_gbs, "peak": hbm,
-                     "unit": "GB/s", "frac": it_gbs / hbm, "traffic": None,
+                     "unit": "GB/s", "frac": it_gbs / hbm,
+                     "traffic": NCU_DRAM_BYTES.get("oem_iter_kernel") if w.p == 500 else None,
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": it_bytes, "loop_iterations": loops,
                      "ms_per_launch": it_ms_launch},
         "roofline_gram": {"kernel": gk, "bound": "tensor", "achieved": g_tf, "peak": bf16,
-                          "unit": "TFLOP/s", "frac": g_tf / bf16, "traffic": None,
+                          "unit": "TFLOP/s", "frac": g_tf / bf16,
+                          "traffic": (NCU_DRAM_BYTES["gram_tma_kernel_per_row"] * w.n
+                                      if w.p == 500 and NCU_DRAM_BYTES.get("gram_tma_kernel_per_row")
+                                      and args.gram_mode in ("auto", "split_bf16") else None),
                           "peak_source": peak_src, "useful_flops": g_flops,
                           "mma_flops": mma_flops,
                           "mma_tflops": mma_flops / (g_ms_launch / 1000.0) / 1e12,
-                          "ms_per_launch": g_ms_launch,
+                          "ms_per_pass": g_ms_launch, "launches_per_pass": g_n / max(1, args.steps),
                           "hbm_gbs": X.nbytes / (g_ms_launch / 1000.0) / 1e9},
         "x_tx_tflops": g_tf,
         "kernels": kernels,

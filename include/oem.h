@@ -152,7 +152,9 @@ int64_t oem_kernel_launches(const oem_ctx* ctx);
  * bracketed by CUDA events on its stream; oem_profile_get() waits for the
  * pending events and returns the accumulated device milliseconds and launch
  * count of one kernel class (0 <= kernel < OEM_PROF_NKERNELS, names from
- * oem_profile_name). Enabling (again) clears the totals. */
+ * oem_profile_name). Enabling (again) clears the totals. OEM_PROF_GRAM_TC
+ * ("gram_tc_pass") covers the tensor-core Gram pass: the packing pass and
+ * the TMA-fed kernel, or the converting kernel. */
 enum {
   OEM_PROF_FOLD_SORT = 0, OEM_PROF_CHUNKS = 1, OEM_PROF_GRAM_SIMT = 2, OEM_PROF_GRAM_TC = 3,
   OEM_PROF_GRAM_REDUCE = 4, OEM_PROF_ASSEMBLE = 5, OEM_PROF_LANCZOS = 6, OEM_PROF_LAMBDA = 7,

@@ -97,7 +97,7 @@ int oem_profile_get(oem_ctx* ctx, int kernel, double* ms, int64_t* launches) {
 
 const char* oem_profile_name(int kernel) {
   static const char* names[OEM_PROF_NKERNELS] = {
-      "fold_sort", "chunk_table", "gram_simt_kernel", "gram_tc_kernel", "gram_reduce_kernel",
+      "fold_sort", "chunk_table", "gram_simt_kernel", "gram_tc_pass", "gram_reduce_kernel",
       "assemble", "lanczos", "lambda_grid_kernel", "oem_iter_kernel", "cv_score", "copy_paths"};
   return (kernel >= 0 && kernel < OEM_PROF_NKERNELS) ? names[kernel] : "unknown";
 }
