@@ -30,21 +30,26 @@ __all__ = [
     "gram_sums", "fold_gram_sums", "assemble_fold_grams",
     "lanczos_d", "effective_d", "lambda_max", "lambda_grid",
     "threshold", "threshold_lasso", "threshold_enet", "threshold_mcp",
-    "threshold_scad", "threshold_group_lasso",
+    "threshold_scad", "threshold_group_lasso", "threshold_group_mcp",
+    "threshold_group_scad", "threshold_sparse_group_lasso",
     "oem_path", "penalty_value", "objective", "kkt_violation",
     "cv_mse", "cv_select", "xval", "group_weights_default",
 ]
 
-KINDS = ("lasso", "enet", "mcp", "scad", "grp.lasso")
+KINDS = ("lasso", "enet", "mcp", "scad", "grp.lasso", "grp.mcp", "grp.scad", "sgl")
+GROUP_KINDS = ("grp.lasso", "grp.mcp", "grp.scad", "sgl")
 
 
 @dataclass
 class Penalty:
-    """One penalty of Table 1 (lasso, elastic net, MCP, SCAD, group lasso).
+    """One penalty of Table 1: lasso, elastic net, MCP, SCAD, group lasso,
+    group MCP ("grp.mcp"), group SCAD ("grp.scad"), sparse group lasso ("sgl").
 
     w: variable weights w_j (default 1). groups: group id per variable
-    (0..G-1) for the group lasso. cg: group weights c_k (default sqrt|g_k|,
-    the Yuan-Lin convention; the paper states no default).
+    (0..G-1) for the group penalties. cg: group weights c_k (default
+    sqrt|g_k|, the Yuan-Lin convention; the paper states no default). alpha:
+    elastic-net mixing; gamma: MCP / SCAD (and their group forms); tau: the
+    sparse group lasso's split between the l1 and the group terms.
     """
     kind: str
     alpha: float = 1.0
@@ -52,6 +57,7 @@ class Penalty:
     w: Optional[np.ndarray] = None
     groups: Optional[np.ndarray] = None
     cg: Optional[np.ndarray] = None
+    tau: float = 0.5
 
     def weights(self, p: int) -> np.ndarray:
         return np.ones(p) if self.w is None else np.asarray(self.w, dtype=np.float64)
@@ -180,9 +186,9 @@ def effective_d(d: float, pen: Penalty) -> float:
     (Eqs. for M and C in Section 2.2) divide by gamma d - 1 and
     (gamma - 1) d - 1, so d is raised to 1.01/gamma (MCP) or 1.01/(gamma - 1)
     (SCAD) when smaller; any d >= lambda_1 is valid (Section 2.1)."""
-    if pen.kind == "mcp":
+    if pen.kind in ("mcp", "grp.mcp"):
         return max(d, 1.01 / pen.gamma)
-    if pen.kind == "scad":
+    if pen.kind in ("scad", "grp.scad"):
         return max(d, 1.01 / (pen.gamma - 1.0))
     return d
 
@@ -202,10 +208,17 @@ def lambda_max(c: np.ndarray, pen: Penalty) -> float:
     """
     c = np.asarray(c, dtype=np.float64)
     p = c.size
-    if pen.kind == "grp.lasso":
+    if pen.kind in ("grp.lasso", "grp.mcp", "grp.scad"):
+        # group MCP / SCAD update the norm with M / C, which vanish iff
+        # ||u_g|| <= c_k lambda, like the group lasso
         members, cg = pen.group_list(p)
         vals = [np.linalg.norm(c[m]) / cg[k] for k, m in enumerate(members) if cg[k] > 0]
         return float(max(vals)) if vals else 0.0
+    if pen.kind == "sgl":
+        members, cg = pen.group_list(p)
+        w = pen.weights(p)
+        return float(max([_sgl_group_lambda(c[m], w[m], cg[k], pen.tau)
+                          for k, m in enumerate(members)] + [0.0]))
     w = pen.weights(p)
     pos = w > 0
     if not pos.any():
@@ -214,6 +227,42 @@ def lambda_max(c: np.ndarray, pen: Penalty) -> float:
     if pen.kind == "enet":
         lm /= max(pen.alpha, 1e-3)
     return lm
+
+
+def _sgl_group_lambda(cgrp, wgrp, ck, tau):
+    """Smallest lambda with a zero sparse-group-lasso update for one group at
+    beta = 0: ||S(c_g, lambda tau w_g)|| <= lambda (1 - tau) c_k, where S is
+    the soft threshold. The left side falls and the right side grows with
+    lambda, so the crossing is found by bisection (to float64 resolution)."""
+    a = np.abs(cgrp)
+    if tau > 0.0:
+        pos = wgrp > 0
+        if (~pos).any() and np.linalg.norm(a[~pos]) > 0 and (1.0 - tau) * ck <= 0:
+            return math.inf  # an unpenalised nonzero coordinate
+        hi = float(np.max(a[pos] / (tau * wgrp[pos]))) if pos.any() else 0.0
+    else:
+        hi = float(np.linalg.norm(a) / ck) if ck > 0 else math.inf
+    if not math.isfinite(hi):
+        return hi
+
+    def f(lam):
+        return float(np.linalg.norm(np.maximum(a - lam * tau * wgrp, 0.0))) - lam * (1.0 - tau) * ck
+
+    lo = 0.0
+    hi = max(hi, 1e-300)
+    for _ in range(2100):  # unpenalised coordinates can push the crossing up
+        if f(hi) <= 0.0:
+            break
+        hi *= 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if mid <= lo or mid >= hi:
+            break
+        if f(mid) > 0.0:
+            lo = mid
+        else:
+            hi = mid
+    return hi
 
 
 def lambda_grid(lmax: float, nlambda: int, ratio: float) -> np.ndarray:
@@ -267,13 +316,56 @@ def threshold_group_lasso(u, members, cl, d):
     return out
 
 
+def threshold_group_mcp(u, members, cl, gamma, d):
+    """Eq. (gmcp): beta_g = M(||u_g||, c_k lambda, gamma, d) u_g / ||u_g||;
+    ||u_g|| = 0 gives beta_g = 0."""
+    out = np.zeros_like(u)
+    for k, m in enumerate(members):
+        nrm = float(np.linalg.norm(u[m]))
+        if nrm > 0.0:
+            out[m] = float(threshold_mcp(np.array(nrm), cl[k], gamma, d)) * u[m] / nrm
+    return out
+
+
+def threshold_group_scad(u, members, cl, gamma, d):
+    """Eq. (gscad): beta_g = C(||u_g||, c_k lambda, gamma, d) u_g / ||u_g||."""
+    out = np.zeros_like(u)
+    for k, m in enumerate(members):
+        nrm = float(np.linalg.norm(u[m]))
+        if nrm > 0.0:
+            out[m] = float(threshold_scad(np.array(nrm), cl[k], gamma, d)) * u[m] / nrm
+    return out
+
+
+def threshold_sparse_group_lasso(u, members, wl_tau, cl_1mtau, d):
+    """Eq. (sglasso), reading: v = S(u, w lambda tau, d) (the lasso update),
+    then the group step of the prox of d/2 ||beta - u/d||^2 + P, which
+    shrinks v_g by c_k lambda (1 - tau) / d:
+    beta_g = v_g (1 - c_k lambda (1 - tau) / (d ||v_g||))_+.
+    (The paper writes G(v_g, c_k lambda (1 - tau), 1), which is this at d = 1.)"""
+    v = threshold_lasso(u, wl_tau, d)
+    out = np.zeros_like(u)
+    for k, m in enumerate(members):
+        nrm = float(np.linalg.norm(v[m]))
+        if nrm > 0.0:
+            out[m] = v[m] * max(1.0 - cl_1mtau[k] / (d * nrm), 0.0)
+    return out
+
+
 def threshold(u: np.ndarray, lam: float, d: float, pen: Penalty) -> np.ndarray:
     """Apply pen's update to u at tuning parameter lam (Section 2.2)."""
     p = u.size
     de = effective_d(d, pen)
-    if pen.kind == "grp.lasso":
+    if pen.kind in GROUP_KINDS:
         members, cg = pen.group_list(p)
-        return threshold_group_lasso(u, members, cg * lam, de)
+        if pen.kind == "grp.lasso":
+            return threshold_group_lasso(u, members, cg * lam, de)
+        if pen.kind == "grp.mcp":
+            return threshold_group_mcp(u, members, cg * lam, pen.gamma, de)
+        if pen.kind == "grp.scad":
+            return threshold_group_scad(u, members, cg * lam, pen.gamma, de)
+        return threshold_sparse_group_lasso(u, members, pen.weights(p) * lam * pen.tau,
+                                            cg * lam * (1.0 - pen.tau), de)
     wl = pen.weights(p) * lam
     if pen.kind == "lasso":
         return threshold_lasso(u, wl, de)
@@ -363,9 +455,17 @@ def _mcp_value(b, lam, gamma):
 def penalty_value(beta: np.ndarray, lam: float, pen: Penalty) -> float:
     """P_lambda(beta) for the forms of Table 1."""
     p = beta.size
-    if pen.kind == "grp.lasso":
+    if pen.kind in GROUP_KINDS:
         members, cg = pen.group_list(p)
-        return float(lam * sum(cg[k] * np.linalg.norm(beta[m]) for k, m in enumerate(members)))
+        nb = np.array([np.linalg.norm(beta[m]) for m in members])
+        if pen.kind == "grp.lasso":
+            return float(lam * np.sum(cg * nb))
+        if pen.kind == "grp.mcp":  # Table 1 (reading: one lambda, inside P)
+            return float(np.sum(_mcp_value(nb, lam * cg, pen.gamma)))
+        if pen.kind == "grp.scad":
+            return float(np.sum(_scad_value(nb, lam * cg, pen.gamma)))
+        return float(lam * (1.0 - pen.tau) * np.sum(cg * nb)
+                     + lam * pen.tau * np.sum(pen.weights(p) * np.abs(beta)))
     w = pen.weights(p)
     if pen.kind == "lasso":
         return float(lam * np.sum(w * np.abs(beta)))
@@ -397,15 +497,46 @@ def kkt_violation(G, c, beta, lam, pen: Penalty) -> float:
     beta = np.asarray(beta, dtype=np.float64)
     p = beta.size
     g = G @ beta - c
-    if pen.kind == "grp.lasso":
+    if pen.kind in ("grp.lasso", "grp.mcp", "grp.scad"):
+        # g_g + P'(||beta_g||) beta_g / ||beta_g|| = 0 on nonzero groups,
+        # ||g_g|| <= P'(0) = lambda c_k on zero groups
         members, cg = pen.group_list(p)
         v = 0.0
         for k, m in enumerate(members):
-            nb = np.linalg.norm(beta[m])
+            nb = float(np.linalg.norm(beta[m]))
+            lk = lam * cg[k]
             if nb > 0:
-                v = max(v, float(np.linalg.norm(g[m] + lam * cg[k] * beta[m] / nb)))
+                if pen.kind == "grp.lasso":
+                    dp = lk
+                elif pen.kind == "grp.mcp":
+                    dp = max(lk - nb / pen.gamma, 0.0)
+                else:
+                    dp = lk if nb <= lk else max(pen.gamma * lk - nb, 0.0) / (pen.gamma - 1.0)
+                v = max(v, float(np.linalg.norm(g[m] + dp * beta[m] / nb)))
             else:
-                v = max(v, float(np.linalg.norm(g[m])) - lam * cg[k])
+                v = max(v, float(np.linalg.norm(g[m])) - lk)
+        return max(v, 0.0)
+    if pen.kind == "sgl":
+        # nonzero group: g_j + lambda tau w_j sign(beta_j) + lambda (1 - tau)
+        # c_k beta_j / ||beta_g|| = 0 where beta_j != 0, |g_j| <= lambda tau
+        # w_j where beta_j = 0; zero group: ||S(g_g, lambda tau w_g)|| <=
+        # lambda (1 - tau) c_k
+        members, cg = pen.group_list(p)
+        wt = pen.weights(p) * lam * pen.tau
+        v = 0.0
+        for k, m in enumerate(members):
+            b = beta[m]
+            nb = float(np.linalg.norm(b))
+            lk = lam * (1.0 - pen.tau) * cg[k]
+            if nb > 0:
+                on = b != 0
+                r = g[m] + wt[m] * np.sign(b) + lk * b / nb
+                if on.any():
+                    v = max(v, float(np.max(np.abs(r[on]))))
+                if (~on).any():
+                    v = max(v, float(np.max(np.abs(g[m][~on]) - wt[m][~on])))
+            else:
+                v = max(v, float(np.linalg.norm(np.maximum(np.abs(g[m]) - wt[m], 0.0))) - lk)
         return max(v, 0.0)
     wl = pen.weights(p) * lam
     a = np.abs(beta)
