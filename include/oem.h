@@ -82,19 +82,28 @@ enum {
 };
 
 /* Penalties of Table 1 (Section 2.2 updates). */
-enum { OEM_LASSO = 0, OEM_ENET = 1, OEM_MCP = 2, OEM_SCAD = 3, OEM_GROUP_LASSO = 4 };
+enum {
+  OEM_LASSO = 0, OEM_ENET = 1, OEM_MCP = 2, OEM_SCAD = 3, OEM_GROUP_LASSO = 4,
+  OEM_GROUP_MCP = 5,            /* Eq. gmcp: M(||u_g||, c_k lambda, gamma, d) u_g / ||u_g|| */
+  OEM_GROUP_SCAD = 6,           /* Eq. gscad: C(||u_g||, c_k lambda, gamma, d) u_g / ||u_g|| */
+  OEM_SPARSE_GROUP_LASSO = 7    /* Eq. sglasso: v = S(u, w lambda tau, d), then
+                                   beta_g = v_g (1 - c_k lambda (1 - tau) / (d ||v_g||))_+ */
+};
 
 /* Precision of the OEM iteration: float32 mat-vec with a compensated
  * (float32 hi + lo) running u, or float64 throughout. */
 enum { OEM_ITER_F32 = 0, OEM_ITER_F64 = 1 };
 
 typedef struct oem_penalty {
-  int32_t kind;          /* OEM_LASSO .. OEM_GROUP_LASSO */
-  double alpha;          /* elastic net mixing alpha in [0,1] (Eq. net) */
-  double gamma;          /* MCP gamma > 1 (Eq. mcp), SCAD gamma > 2 (Eq. scad) */
-  const double* w;       /* host, p variable weights w_j >= 0, or NULL (all 1) */
-  const int32_t* group;  /* host, p group ids in [0, ngroups), group lasso only;
-                            each group's variables must be contiguous */
+  int32_t kind;          /* OEM_LASSO .. OEM_SPARSE_GROUP_LASSO */
+  double alpha;          /* elastic net mixing alpha in [0,1] (Eq. net); for the
+                            sparse group lasso its tau in [0,1] (Table 1) */
+  double gamma;          /* MCP and group MCP gamma > 1 (Eqs. mcp, gmcp), SCAD
+                            and group SCAD gamma > 2 (Eqs. scad, gscad) */
+  const double* w;       /* host, p variable weights w_j >= 0, or NULL (all 1);
+                            lasso, elastic net, MCP, SCAD, sparse group lasso */
+  const int32_t* group;  /* host, p group ids in [0, ngroups), group penalties
+                            only; each group's variables must be contiguous */
   const double* cg;      /* host, ngroups group weights c_k >= 0, or NULL (sqrt|g_k|) */
   int32_t ngroups;
 } oem_penalty;

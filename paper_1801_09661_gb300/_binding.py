@@ -32,10 +32,12 @@ OEM_F64, OEM_F32, OEM_BF16 = 0, 1, 2
 OEM_GRAM_FP64, OEM_GRAM_FP32, OEM_GRAM_TF32 = 0, 1, 2
 OEM_GRAM_BF16, OEM_GRAM_SPLIT_BF16, OEM_GRAM_AUTO = 3, 4, 5
 OEM_LASSO, OEM_ENET, OEM_MCP, OEM_SCAD, OEM_GROUP_LASSO = 0, 1, 2, 3, 4
+OEM_GROUP_MCP, OEM_GROUP_SCAD, OEM_SPARSE_GROUP_LASSO = 5, 6, 7
 OEM_ITER_F32, OEM_ITER_F64 = 0, 1
 
 KIND = {"lasso": OEM_LASSO, "enet": OEM_ENET, "mcp": OEM_MCP, "scad": OEM_SCAD,
-        "grp.lasso": OEM_GROUP_LASSO}
+        "grp.lasso": OEM_GROUP_LASSO, "grp.mcp": OEM_GROUP_MCP, "grp.scad": OEM_GROUP_SCAD,
+        "sgl": OEM_SPARSE_GROUP_LASSO}
 MODE = {"fp64": OEM_GRAM_FP64, "fp32": OEM_GRAM_FP32, "tf32": OEM_GRAM_TF32,
         "bf16": OEM_GRAM_BF16, "split_bf16": OEM_GRAM_SPLIT_BF16, "auto": OEM_GRAM_AUTO}
 
@@ -129,13 +131,15 @@ def _stream(stream) -> Optional[int]:
 
 @dataclass
 class Penalty:
-    """A penalty of Table 1 for the C call (host data)."""
+    """A penalty of Table 1 for the C call (host data). tau is the sparse
+    group lasso's split (passed in the ABI's alpha field)."""
     kind: str
     alpha: float = 1.0
     gamma: float = 3.0
     w: Optional[Sequence[float]] = None
     groups: Optional[Sequence[int]] = None
     cg: Optional[Sequence[float]] = None
+    tau: float = 0.5
 
 
 class _PenArray:
@@ -146,7 +150,7 @@ class _PenArray:
         arr = (oem_penalty * len(pens))()
         for i, p in enumerate(pens):
             arr[i].kind = KIND[p.kind]
-            arr[i].alpha = float(p.alpha)
+            arr[i].alpha = float(p.tau if p.kind == "sgl" else p.alpha)
             arr[i].gamma = float(p.gamma)
             if p.w is not None:
                 w = np.ascontiguousarray(p.w, dtype=np.float64)

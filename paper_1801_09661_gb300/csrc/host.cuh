@@ -377,21 +377,25 @@ inline int prepare_pens(oem_ctx* ctx, const oem_penalty* pens, int npen, int64_t
   P.allowed.assign((size_t)p + 1, 1);
   for (int i = 0; i < npen; ++i) {
     const oem_penalty& q = pens[i];
-    if (q.kind < OEM_LASSO || q.kind > OEM_GROUP_LASSO)
+    if (q.kind < OEM_LASSO || q.kind > OEM_SPARSE_GROUP_LASSO)
       return fail(ctx, OEM_EINVAL, "penalty %d: unknown kind %d", i, q.kind);
+    const bool grouped = q.kind >= OEM_GROUP_LASSO;
     if (q.kind == OEM_ENET && !(q.alpha >= 0.0 && q.alpha <= 1.0))
       return fail(ctx, OEM_EINVAL, "penalty %d: elastic net alpha=%g not in [0,1]", i, q.alpha);
-    if (q.kind == OEM_MCP && !(q.gamma > 1.0))
+    if ((q.kind == OEM_MCP || q.kind == OEM_GROUP_MCP) && !(q.gamma > 1.0))
       return fail(ctx, OEM_EINVAL, "penalty %d: MCP gamma=%g must exceed 1", i, q.gamma);
-    if (q.kind == OEM_SCAD && !(q.gamma > 2.0))
+    if ((q.kind == OEM_SCAD || q.kind == OEM_GROUP_SCAD) && !(q.gamma > 2.0))
       return fail(ctx, OEM_EINVAL, "penalty %d: SCAD gamma=%g must exceed 2", i, q.gamma);
+    if (q.kind == OEM_SPARSE_GROUP_LASSO && !(q.alpha >= 0.0 && q.alpha <= 1.0))
+      return fail(ctx, OEM_EINVAL, "penalty %d: sparse group lasso tau=%g not in [0,1]", i, q.alpha);
     DevPenalty d{};
     d.kind = q.kind;
-    d.alpha64 = q.kind == OEM_ENET ? q.alpha : 1.0;
-    d.gamma64 = (q.kind == OEM_MCP || q.kind == OEM_SCAD) ? q.gamma : 3.0;
+    d.alpha64 = (q.kind == OEM_ENET || q.kind == OEM_SPARSE_GROUP_LASSO) ? q.alpha : 1.0;
+    d.gamma64 = (q.kind == OEM_MCP || q.kind == OEM_SCAD || q.kind == OEM_GROUP_MCP ||
+                 q.kind == OEM_GROUP_SCAD) ? q.gamma : 3.0;
     d.alpha = (float)d.alpha64;
     d.gamma = (float)d.gamma64;
-    if (q.w && q.kind != OEM_GROUP_LASSO) {
+    if (q.w && (!grouped || q.kind == OEM_SPARSE_GROUP_LASSO)) {
       P.w64[i].assign(q.w, q.w + p);
       P.w32[i].resize(p);
       for (int64_t j = 0; j < p; ++j) {
@@ -400,9 +404,9 @@ inline int prepare_pens(oem_ctx* ctx, const oem_penalty* pens, int npen, int64_t
         P.w32[i][j] = (float)q.w[j];
       }
     }
-    if (q.kind == OEM_GROUP_LASSO) {
+    if (grouped) {
       if (!q.group || q.ngroups < 1)
-        return fail(ctx, OEM_EINVAL, "penalty %d: group lasso needs group ids and ngroups >= 1", i);
+        return fail(ctx, OEM_EINVAL, "penalty %d: a group penalty needs group ids and ngroups >= 1", i);
       P.grp[i].assign(q.group, q.group + p);
       std::vector<int> seen(q.ngroups, 0), cnt(q.ngroups, 0);
       for (int64_t j = 0; j < p; ++j) {
@@ -585,7 +589,7 @@ inline std::array<int64_t, 5> tune_key(int64_t p, int B, const PenPlan& P, int p
 inline int plan_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, const oem_options* o, IterPlan& I) {
   const int prec = o->iter_precision;
   I.groups = false;
-  for (int i = 0; i < P.npen; ++i) I.groups |= P.host[i].kind == OEM_GROUP_LASSO;
+  for (int i = 0; i < P.npen; ++i) I.groups |= P.host[i].kind >= OEM_GROUP_LASSO;
   I.max_tasks = B * P.npen;
   int C = o->cluster_ctas;
   if (C <= 0) {

@@ -14,8 +14,9 @@ __global__ void lambda_grid_kernel(const double* __restrict__ c, int p,
   __shared__ double red[32];
   const DevPenalty pen = pens[blockIdx.x];
   double m = 0.0;
-  if (pen.kind == OEM_GROUP_LASSO) {
-    // groups are contiguous: a thread owns each group start
+  if (pen.kind == OEM_GROUP_LASSO || pen.kind == OEM_GROUP_MCP || pen.kind == OEM_GROUP_SCAD) {
+    // groups are contiguous: a thread owns each group start. Group MCP /
+    // SCAD update the norm with M / C, which vanish iff ||u_g|| <= c_k lambda.
     for (int j = threadIdx.x; j < p; j += blockDim.x) {
       if (j == 0 || pen.grp[j] != pen.grp[j - 1]) {
         const int g = pen.grp[j];
@@ -24,6 +25,48 @@ __global__ void lambda_grid_kernel(const double* __restrict__ c, int p,
         const double cg = pen.cg[g];
         if (cg > 0.0) m = fmax(m, sqrt(s) / cg);
       }
+    }
+  } else if (pen.kind == OEM_SPARSE_GROUP_LASSO) {
+    // per group the smallest lambda with ||S(c_g, lambda tau w_g)|| <=
+    // lambda (1 - tau) c_k, by bisection (the left side falls, the right
+    // side grows with lambda)
+    const double tau = pen.alpha64;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+      if (!(j == 0 || pen.grp[j] != pen.grp[j - 1])) continue;
+      const int g = pen.grp[j];
+      int j1 = j;
+      while (j1 < p && pen.grp[j1] == g) ++j1;
+      const double ck = pen.cg[g];
+      auto f = [&](double lam) {
+        double s = 0.0;
+        for (int i = j; i < j1; ++i) {
+          const double w = pen.w64 ? pen.w64[i] : 1.0;
+          const double t = fmax(fabs(c[i]) - lam * tau * w, 0.0);
+          s = fma(t, t, s);
+        }
+        return sqrt(s) - lam * (1.0 - tau) * ck;
+      };
+      double hi = 0.0;
+      if (tau > 0.0) {
+        for (int i = j; i < j1; ++i) {
+          const double w = pen.w64 ? pen.w64[i] : 1.0;
+          if (w > 0.0) hi = fmax(hi, fabs(c[i]) / (tau * w));
+        }
+      } else {
+        double s = 0.0;
+        for (int i = j; i < j1; ++i) s = fma(c[i], c[i], s);
+        hi = ck > 0.0 ? sqrt(s) / ck : 0.0;
+      }
+      hi = fmax(hi, 1e-300);
+      for (int it = 0; it < 2100 && f(hi) > 0.0; ++it) hi *= 2.0;
+      double lo = 0.0;
+      for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (f(mid) > 0.0) lo = mid;
+        else hi = mid;
+      }
+      m = fmax(m, hi);
     }
   } else {
     for (int j = threadIdx.x; j < p; j += blockDim.x) {

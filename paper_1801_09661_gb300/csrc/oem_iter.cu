@@ -215,8 +215,9 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
       alpha[k] = kF32 ? (T)pen.alpha : (T)pen.alpha64;
       gamma[k] = kF32 ? (T)pen.gamma : (T)pen.gamma64;
       T de = dgram;
-      if (pen.kind == OEM_MCP) de = fmax(de, (T)(1.01 / pen.gamma64));
-      if (pen.kind == OEM_SCAD) de = fmax(de, (T)(1.01 / (pen.gamma64 - 1.0)));
+      if (pen.kind == OEM_MCP || pen.kind == OEM_GROUP_MCP) de = fmax(de, (T)(1.01 / pen.gamma64));
+      if (pen.kind == OEM_SCAD || pen.kind == OEM_GROUP_SCAD)
+        de = fmax(de, (T)(1.01 / (pen.gamma64 - 1.0)));
       dk[k] = de;
       done[k] = 0;
       if (tk.resume) {
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
     }
   }
   bool has_group = false;
-  for (int k = 0; k < m; ++k) has_group |= (tk.pens[k].kind == OEM_GROUP_LASSO);
+  for (int k = 0; k < m; ++k) has_group |= (tk.pens[k].kind >= OEM_GROUP_LASSO);
 
   // ---- this warp's contiguous row block, aligned to allowed boundaries
   int wlo, whi;
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
       }
       if (kF32) { if (pen.w32) wt = (T)pen.w32[i0 + i]; }
       else { if (pen.w64) wt = (T)pen.w64[i0 + i]; }
-      if (pen.kind == OEM_GROUP_LASSO) {
+      if (pen.kind >= OEM_GROUP_LASSO) {
         const int g = pen.grp[i0 + i];
         cgv = (T)pen.cg[g];
         if (i == 0 || pen.grp[i0 + i - 1] != g) {
@@ -412,14 +413,27 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
     }
     __syncwarp();
     if (has_group) {
-      // ---- 2a. group norms ||u_g|| over the warp's rows
+      // ---- 2a. group norms over the warp's rows: ||u_g||, or for the
+      // sparse group lasso ||v_g|| with v = S(u, w lambda tau) / d
       for (int e = lane; e < M * nr; e += 32) {
         const int k = e / nr, i = wlo + e % nr;
         const int idx = k * maxR + i;
         const int len = glen[idx];
         if (len > 0) {
+          int kd = OEM_LASSO;
+          T lt = T(0), dd = T(1);
+#pragma unroll
+          for (int kk = 0; kk < M; ++kk)
+            if (kk == k) { kd = kind[kk]; lt = lamv[kk] * alpha[kk]; dd = dk[kk]; }
           T s2 = T(0);
-          for (int q = 0; q < len; ++q) s2 = fma(uhi[idx + q], uhi[idx + q], s2);
+          if (kd == OEM_SPARSE_GROUP_LASSO) {
+            for (int q = 0; q < len; ++q) {
+              const T v = fmax(fabs(uhi[idx + q]) - wv[idx + q] * lt, T(0)) / dd;
+              s2 = fma(v, v, s2);
+            }
+          } else {
+            for (int q = 0; q < len; ++q) s2 = fma(uhi[idx + q], uhi[idx + q], s2);
+          }
           s2 = sqrt(s2);
           for (int q = 0; q < len; ++q) gn[idx + q] = s2;
         }
@@ -443,6 +457,20 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
                 const T nrm = gn[idx];
                 const T f = nrm > T(0) ? T(1) - cgr[idx] * lamv[kk] / nrm : T(0);
                 bn = f > T(0) ? u / dk[kk] * f : T(0);
+              } else if (kind[kk] == OEM_GROUP_MCP || kind[kk] == OEM_GROUP_SCAD) {
+                // Eqs. gmcp / gscad: the scalar rule on the norm, u's direction
+                const T nrm = gn[idx];
+                const T bnorm = nrm > T(0) ? thr_scalar<T>(kind[kk] == OEM_GROUP_MCP ? OEM_MCP : OEM_SCAD, nrm,
+                                                           cgr[idx] * lamv[kk], alpha[kk], gamma[kk], dk[kk])
+                                           : T(0);
+                bn = nrm > T(0) ? u * (bnorm / nrm) : T(0);
+              } else if (kind[kk] == OEM_SPARSE_GROUP_LASSO) {
+                // Eq. sglasso (reading: the group step shrinks v by
+                // c_k lambda (1 - tau) / d)
+                const T nrm = gn[idx];
+                const T v = copysign(fmax(fabs(u) - wv[idx] * lamv[kk] * alpha[kk], T(0)) / dk[kk], u);
+                const T f = nrm > T(0) ? T(1) - cgr[idx] * lamv[kk] * (T(1) - alpha[kk]) / (dk[kk] * nrm) : T(0);
+                bn = f > T(0) ? v * f : T(0);
               } else {
                 bn = thr_scalar<T>(kind[kk], u, wv[idx] * lamv[kk], alpha[kk], gamma[kk], dk[kk]);
               }

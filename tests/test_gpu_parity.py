@@ -153,7 +153,7 @@ def _pens(p, kinds, gsize=5):
     groups = np.arange(p) // gsize
     gp, op = [], []
     for k, kw in kinds:
-        g = groups if k == "grp.lasso" else None
+        g = groups if k in ("grp.lasso", "grp.mcp", "grp.scad", "sgl") else None
         gp.append(__import__("paper_1801_09661_gb300").Penalty(k, groups=g, **kw))
         op.append(oracle.Penalty(k, groups=g, **kw))
     return gp, op
@@ -314,3 +314,43 @@ def test_iteration_layouts_give_identical_paths(oem, ctx, precision):
         for a, b in zip(runs[0], r):
             np.testing.assert_array_equal(a, b)
     _check_paths(*runs[0], G, c, d, op, 20, 1e-2, tol=1e-8)
+
+
+GROUP_PENS = [("grp.lasso", {}), ("grp.mcp", {"gamma": 3.0}), ("grp.scad", {"gamma": 3.7}),
+              ("sgl", {"tau": 0.5}), ("sgl", {"tau": 0.2}), ("lasso", {})]
+
+
+@pytest.mark.parametrize("p,ncl", [(60, 0), (130, 4), (130, 40), (257, 16)])
+def test_group_penalties_match_oracle(oem, ctx, p, ncl):
+    # Eqs. gmcp, gscad, sglasso next to the group lasso and the lasso in one
+    # launch (groups of 5; grid mode at 40 CTAs)
+    n = 20 * p + 1000
+    X, y = _data(n, p, 300 + p, np.float64)
+    G, c, N, _ = oracle.gram_sums(X, y)
+    G, c = G / n, c / n
+    d = oracle.lanczos_d(G)[0]
+    gp, op = _pens(p, GROUP_PENS)
+    L, ratio = 25, 1e-2
+    # tol 1e-7: the float32 iteration resolves changes of beta to its ulp
+    beta, lam, its, conv = oem.oem_fit_path(ctx, _dev(G), _dev(c), gp, d=d, nlambda=L,
+                                            lambda_min_ratio=ratio, tol=1e-7, cluster_ctas=ncl)
+    assert ctx.sync() == 0
+    beta, lam, its, conv = (t.cpu().numpy() for t in (beta, lam, its, conv))
+    _check_paths(beta, lam, its, conv, G, c, d, op, L, ratio, tol=1e-7)
+    for i, pen in enumerate(op):
+        kt = max(1e-6, 10 * oracle.effective_d(d, pen) * 1e-7 * max(1.0, np.abs(beta[i]).max()))
+        for l in range(L):
+            assert oracle.kkt_violation(G, c, beta[i, l], lam[i, l], pen) <= kt, (pen.kind, l)
+
+
+def test_group_penalty_arguments_are_checked(oem, ctx):
+    p = 20
+    G, c = np.eye(p), np.ones(p)
+    bad = [oem.Penalty("sgl", groups=np.arange(p) // 5, tau=1.5),
+           oem.Penalty("grp.mcp", groups=np.arange(p) // 5, gamma=0.9),
+           oem.Penalty("grp.scad", groups=np.arange(p) // 5, gamma=1.9),
+           oem.Penalty("grp.mcp")]  # no groups
+    for pen in bad:
+        with pytest.raises(oem.OemError) as e:
+            oem.oem_fit_path(ctx, _dev(G), _dev(c), [pen], d=1.0, nlambda=5)
+        assert e.value.code == oem.OEM_EINVAL
