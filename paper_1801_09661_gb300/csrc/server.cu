@@ -573,7 +573,7 @@ int oem_server_submit(oem_server* S, const oem_job* job, int64_t* id) {
   if (!r && j.p > 4096) r = fail(ctx, OEM_EUNSUPPORTED, "p=%lld exceeds 4096 for serving", (long long)j.p);
   if (!r) r = prepare_pens(ctx, &j.pen, 1, j.p, J->P);
   if (!r) {
-    J->groups = j.pen.kind == OEM_GROUP_LASSO;
+    J->groups = j.pen.kind >= OEM_GROUP_LASSO;
     if (S->form == OEM_SERVE_PLAIN && J->groups)
       r = fail(ctx, OEM_EUNSUPPORTED, "the plain form serves lasso, elastic net, MCP and SCAD");
   }
