@@ -554,7 +554,7 @@ inline int layout_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, int pre
       return fail(ctx, OEM_EUNSUPPORTED, "grid mode: %d rows per CTA do not fit", I.max_rows);
     IterLaunch probe{};
     probe.ntasks = ntasks; probe.C = C; probe.M = I.M; probe.precision = prec;
-    probe.smem = I.smem; probe.grid = 1;
+    probe.smem = I.smem; probe.max_rows = I.max_rows; probe.grid = 1;
     if (oem_iter_max_cluster(probe) < 1)
       return fail(ctx, OEM_EUNSUPPORTED, "grid mode: no CTA fits on an SM");
     return OEM_OK;
@@ -570,7 +570,7 @@ inline int layout_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, int pre
     I.C = C;
     IterLaunch probe{};
     probe.ntasks = ntasks; probe.C = C; probe.M = I.M; probe.precision = prec;
-    probe.smem = I.smem;
+    probe.smem = I.smem; probe.max_rows = I.max_rows;
     if (oem_iter_max_cluster(probe) >= 1) return OEM_OK;
     if (C == 1) return fail(ctx, OEM_ECUDA, "no cluster configuration of the iteration kernel fits");
   }
@@ -687,6 +687,7 @@ inline int launch_iter_layout(oem_ctx* ctx, int64_t p, int B, const float* G32, 
   Lc.tol = o->tol; Lc.max_iter = o->max_iter; Lc.max_loops = max_loops; Lc.dstatus = ctx->dstatus;
   Lc.smem = I.smem;
   Lc.grid = I.grid ? 1 : 0;
+  Lc.max_rows = I.max_rows;
   LAUNCH(OEM_PROF_ITER, launch_oem_iter(Lc, s));
   return OEM_OK;
 }

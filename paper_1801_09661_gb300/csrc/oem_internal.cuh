@@ -259,6 +259,7 @@ struct IterLaunch {
   const IterTask* tasks; // device array
   int32_t ntasks, C, M, precision;
   int32_t grid;          // 1: cooperative launch, C CTAs per task, global-memory exchange
+  int32_t max_rows;      // longest CTA slice of the launch (picks the row group)
   double tol;
   int64_t max_iter;      // per lambda
   int64_t max_loops;     // per launch (<= 0: run to completion)

@@ -66,24 +66,32 @@ __device__ __forceinline__ T warp_max(T v) {
   return v;
 }
 
-// Reduce-scatter of 16 per-lane values over the warp: returns, in lane l,
-// the warp sum of value (l >> 1) & 15 (both lanes of a pair hold it). Each
-// level halves the values a lane keeps: 8 + 4 + 2 + 1 + 1 shuffles.
-template <typename T>
-__device__ __forceinline__ T reduce_scatter16(const T (&a)[16], int lane) {
-  T b8[8], b4[4], b2[2];
-  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
+// Reduce-scatter of V (4, 8 or 16) per-lane values over the warp: returns,
+// in lane l, the warp sum of value l / (32 / V) (the 32 / V lanes of a group
+// all hold it). The levels at lane offsets 16, 8, ... halve the values a lane
+// keeps until one is left; the remaining offsets add plainly. The pairing
+// tree of every value is the same as a full butterfly sum's.
+template <int V, typename T>
+__device__ __forceinline__ T reduce_scatter(const T (&a)[V], int lane) {
+  static_assert(V == 4 || V == 8 || V == 16, "V");
+  T b[V];
 #pragma unroll
-  for (int q = 0; q < 8; ++q)
-    b8[q] = (h4 ? a[q + 8] : a[q]) + __shfl_xor_sync(0xffffffffu, h4 ? a[q] : a[q + 8], 16);
+  for (int q = 0; q < V; ++q) b[q] = a[q];
+  int n = V, o = 16;
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-    b4[q] = (h3 ? b8[q + 4] : b8[q]) + __shfl_xor_sync(0xffffffffu, h3 ? b8[q] : b8[q + 4], 8);
+  for (int lv = 0; lv < 5; ++lv, o >>= 1) {
+    if (n > 1) {
+      const bool up = lane & o;
+      const int h = n >> 1;
 #pragma unroll
-  for (int q = 0; q < 2; ++q)
-    b2[q] = (h2 ? b4[q + 2] : b4[q]) + __shfl_xor_sync(0xffffffffu, h2 ? b4[q] : b4[q + 2], 4);
-  T b1 = (h1 ? b2[1] : b2[0]) + __shfl_xor_sync(0xffffffffu, h1 ? b2[0] : b2[1], 2);
-  return b1 + __shfl_xor_sync(0xffffffffu, b1, 1);
+      for (int q = 0; q < 8; ++q)
+        if (q < h) b[q] = (up ? b[q + h] : b[q]) + __shfl_xor_sync(0xffffffffu, up ? b[q] : b[q + h], o);
+      n = h;
+    } else {
+      b[0] += __shfl_xor_sync(0xffffffffu, b[0], o);
+    }
+  }
+  return b[0];
 }
 
 // Load the M entries of row j of a [rows][M] buffer.
@@ -129,6 +137,32 @@ __device__ __forceinline__ void store_col(T* __restrict__ dst, const T* __restri
   }
 }
 
+// Position of element (row i, instance k) in a dbeta buffer [rows][M]. In
+// the float32 path a lane reads 4 consecutive rows (M float4 units) at a
+// time; the 16-byte units are XOR-swizzled within each run of 8 units by
+// (unit / 8) mod M, so that the 8 lanes of a shared-memory wavefront hit 8
+// different bank groups. The float64 path keeps the plain layout.
+template <typename T, int M>
+__device__ __forceinline__ int dpos(int i, int k) {
+  const int f = i * M + k;
+  if constexpr (sizeof(T) == 4 && M > 1) {
+    const int u = f >> 2;
+    return ((u ^ ((u >> 3) & (M - 1))) << 2) | (f & 3);
+  } else {
+    return f;
+  }
+}
+// Store the M values of row i (src[0..M)) at their positions in D.
+template <typename T, int M>
+__device__ __forceinline__ void store_row(T* __restrict__ D, int i, const T* __restrict__ src) {
+  if constexpr (sizeof(T) == 4 && M == 8) {
+    store_col<T, 4>(D + dpos<T, M>(i, 0), src);
+    store_col<T, 4>(D + dpos<T, M>(i, 4), src + 4);
+  } else {
+    store_col<T, M>(D + dpos<T, M>(i, 0), src);
+  }
+}
+
 // Order-preserving 32-bit images of non-negative maxima for the block table
 // and the DSMEM atomic max (32-bit atomics only across the cluster). A
 // float64 value is rounded up to float32 first, so a max|dbeta| is never
@@ -167,7 +201,7 @@ __host__ __device__ inline IterSmem iter_smem_layout(int p, int M, int maxR, int
   return L;
 }
 
-template <typename T, int M, int NT, bool kGrid>
+template <typename T, int M, int NT, bool kGrid, int RG>
 __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   constexpr int NW = NT / 32;
   cg::cluster_group cluster = cg::this_cluster();
@@ -292,12 +326,14 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
     cluster.sync();  // every CTA initialised before any DSMEM access
   }
 
-  // Lane roles in the row-group mat-vec: a group is RG = 16 / M rows; after
-  // the reduce-scatter, lane l holds the sum of value v = (l >> 1) & 15, i.e.
-  // row rsub = v / M of the group and instance kq = v % M (even lanes act).
-  constexpr int RG = 16 / M;
-  const int vq = (lane >> 1) & 15, rsub = vq / M, kq = vq % M;
-  const bool even = (lane & 1) == 0;
+  // Lane roles in the row-group mat-vec: a group is RG rows (V = RG M sums);
+  // after the reduce-scatter lane l holds the sum of value v = l / S,
+  // S = 32 / V, i.e. row rsub = v / M of the group and instance kq = v % M
+  // (the first lane of each group of S acts).
+  constexpr int V = RG * M, S = 32 / V;
+  static_assert(V == 4 || V == 8 || V == 16, "row group");
+  const int vq = lane / S, rsub = vq / M, kq = vq % M;
+  const bool even = (lane % S) == 0;
   int my_kind = OEM_LASSO;
   T my_alpha = T(1), my_gamma = T(3), my_d = T(1), my_lam = T(0);
   int my_done = 1;
@@ -337,29 +373,47 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
       const int nv = min(RG, whi - gb);
       T y = T(0);
       if (!skip_mv) {
-        T acc[16];
+        T acc[V];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) acc[q] = T(0);
-        if (gb + nv <= smem_rows) {
-          const T* g0 = Gs + (size_t)gb * ldgs;
-#pragma unroll 4
-          for (int j = lane; j < p; j += 32) {
-            T dv[M];
-            load_col<T, M>(Dc, j, dv);
+        for (int q = 0; q < V; ++q) acc[q] = T(0);
+        const T* gr[RG];
 #pragma unroll
-            for (int r = 0; r < RG; ++r) {
-              const T g = r < nv ? g0[(size_t)r * ldgs + j] : T(0);
+        for (int r = 0; r < RG; ++r) {
+          const int ib = gb + min(r, nv - 1);
+          gr[r] = ib < smem_rows ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
+        }
+        if constexpr (kF32) {
+          // lane l takes columns 4l .. 4l+3, then + 128: one float4 of each
+          // G row and M float4 units of dbeta per step (rows are zero-padded
+          // to ldgs, a multiple of 4). Rows resident in shared memory are
+          // addressed from Gs (shared loads), the others through gr.
+          const float* g0 = Gs + (size_t)gb * ldgs;
+          auto matvec = [&](auto row) {
+            for (int j4 = lane * 4; j4 < p; j4 += 128) {
+              float dv[4][M];
 #pragma unroll
-              for (int k = 0; k < M; ++k) acc[r * M + k] = fma(g, dv[k], acc[r * M + k]);
+              for (int q = 0; q < M; ++q) {
+                const int u = (j4 * M >> 2) + q;
+                const float4 t = *reinterpret_cast<const float4*>(Dc + ((u ^ ((u >> 3) & (M - 1))) << 2));
+                const float tv[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) dv[(q * 4 + e) / M][(q * 4 + e) % M] = tv[e];
+              }
+#pragma unroll
+              for (int r = 0; r < RG; ++r) {
+                float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (r < nv) g4 = *reinterpret_cast<const float4*>(row(r) + j4);
+                const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                  for (int k = 0; k < M; ++k) acc[r * M + k] = fma(gv[c], dv[c][k], acc[r * M + k]);
+              }
             }
-          }
+          };
+          if (gb + nv <= smem_rows) matvec([&](int r) { return g0 + (size_t)r * ldgs; });
+          else matvec([&](int r) { return gr[r]; });
         } else {
-          const T* gr[RG];
-#pragma unroll
-          for (int r = 0; r < RG; ++r) {
-            const int ib = gb + min(r, nv - 1);
-            gr[r] = ib < smem_rows ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
-          }
 #pragma unroll 4
           for (int j = lane; j < p; j += 32) {
             T dv[M];
@@ -372,13 +426,13 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
             }
           }
         }
-        y = reduce_scatter16(acc, lane);
+        y = reduce_scatter<V>(acc, lane);
       }
       const int i = gb + rsub;  // this lane's row (local index)
       if (even && i < whi) {
         const int idx = kq * maxR + i;
         if (my_inst && !skip_mv) {
-          const T incr = fma(my_d, Dc[(size_t)(i0 + i) * M + kq], -y);
+          const T incr = fma(my_d, Dc[dpos<T, M>(i0 + i, kq)], -y);
           // an instance whose dbeta was zero (y == 0 exactly) keeps its u
           // bit for bit, however the instances are grouped into tasks
           if (incr == T(0)) {
@@ -496,19 +550,18 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
     {
       if constexpr (kGrid) {
         T* Dn = xD + (size_t)nxt * ldgs * M;
-        for (int i = wlo + lane; i < whi; i += 32)
-          store_col<T, M>(Dn + (size_t)(i0 + i) * M, st + (size_t)i * M);
+        for (int i = wlo + lane; i < whi; i += 32) store_row<T, M>(Dn, i0 + i, st + (size_t)i * M);
       } else {
         T* Dn = Dbuf + (size_t)nxt * ldgs * M;
         for (int e = lane; e < nr * C; e += 32) {
           const int i = wlo + e / C, r = e % C;
-          store_col<T, M>(cluster.map_shared_rank(Dn + (size_t)(i0 + i) * M, r), st + (size_t)i * M);
+          store_row<T, M>(cluster.map_shared_rank(Dn, r), i0 + i, st + (size_t)i * M);
         }
       }
-      // instance kq's warp maxima end in lane 2 kq (lanes of one instance
-      // differ in the row bits 2M .. 16 of the lane index)
+      // instance kq's warp maxima end in lane S kq (lanes of one instance
+      // differ in the row bits 32 / RG .. 16 of the lane index)
 #pragma unroll
-      for (int o = 2 * M; o < 32; o <<= 1) {
+      for (int o = 32 / RG; o < 32; o <<= 1) {
         lmd = fmax(lmd, __shfl_xor_sync(0xffffffffu, lmd, o));
         lmb = fmax(lmb, __shfl_xor_sync(0xffffffffu, lmb, o));
       }
@@ -601,12 +654,23 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
         for (int k = 0; k < M; ++k) acc[k] = T(0);
         // same column order and lane tree as the loop's mat-vec, so a resumed
         // path is the same as an uninterrupted one
-        for (int j = lane; j < p; j += 32) {
-          T dv[M];
-          load_col<T, M>(Dc, j, dv);
-          const T g = g0[j];
+        if constexpr (kF32) {
+          for (int j4 = lane * 4; j4 < p; j4 += 128) {
+            const float4 g4 = *reinterpret_cast<const float4*>(g0 + j4);
+            const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
-          for (int k = 0; k < M; ++k) acc[k] = fma(g, dv[k], acc[k]);
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int k = 0; k < M; ++k) acc[k] = fma(gv[c], Dc[dpos<T, M>(j4 + c, k)], acc[k]);
+          }
+        } else {
+          for (int j = lane; j < p; j += 32) {
+            T dv[M];
+            load_col<T, M>(Dc, j, dv);
+            const T g = g0[j];
+#pragma unroll
+            for (int k = 0; k < M; ++k) acc[k] = fma(g, dv[k], acc[k]);
+          }
         }
 #pragma unroll
         for (int k = 0; k < M; ++k) acc[k] = warp_sum(acc[k]);
@@ -615,7 +679,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
           for (int k = 0; k < M; ++k) {
             if (k >= m) continue;
             const int idx = k * maxR + ib;
-            const T incr = fma(dk[k], Dc[(size_t)(i0 + ib) * M + k], -acc[k]);
+            const T incr = fma(dk[k], Dc[dpos<T, M>(i0 + ib, k)], -acc[k]);
             if (incr == T(0)) {
             } else if (kF32) {
               const T h = uhi[idx];
@@ -667,10 +731,10 @@ size_t oem_iter_smem_per_row(int p, int precision) {
   return (size_t)((p + 3) & ~3) * tsz;
 }
 
-template <typename T, int M, bool kGrid>
+template <typename T, int M, bool kGrid, int RG>
 static cudaError_t launch_t(const IterLaunch& P, cudaStream_t s, bool query, int* out) {
   constexpr int NT = iter_threads<T, M>();
-  auto kfn = oem_iter_kernel<T, M, NT, kGrid>;
+  auto kfn = oem_iter_kernel<T, M, NT, kGrid, RG>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -707,9 +771,20 @@ static cudaError_t launch_t(const IterLaunch& P, cudaStream_t s, bool query, int
   return cudaLaunchKernelEx(&cfg, kfn, P);
 }
 
+// Row group: 16 / M rows, or 4 when no warp owns more than 4 rows (the
+// instances then fill fewer sums per lane and no load is wasted).
+template <typename T, int M, int RG>
+static cudaError_t dispatch_r(const IterLaunch& P, cudaStream_t s, bool q, int* out) {
+  return P.grid ? launch_t<T, M, true, RG>(P, s, q, out) : launch_t<T, M, false, RG>(P, s, q, out);
+}
 template <typename T, int M>
 static cudaError_t dispatch_g(const IterLaunch& P, cudaStream_t s, bool q, int* out) {
-  return P.grid ? launch_t<T, M, true>(P, s, q, out) : launch_t<T, M, false>(P, s, q, out);
+  constexpr int RGF = 16 / M;
+  if constexpr (RGF > 4) {
+    constexpr int NW = iter_threads<T, M>() / 32;
+    if ((P.max_rows + NW - 1) / NW <= 4) return dispatch_r<T, M, 4>(P, s, q, out);
+  }
+  return dispatch_r<T, M, RGF>(P, s, q, out);
 }
 
 template <typename T>

@@ -362,8 +362,11 @@ int run_round(oem_server* S, std::vector<SrvJob*>& ready) {
       }
     }
     smem = std::max<size_t>(smem, 1024);
+    int max_rows = 0;
+    for (int u = 0; u < T; ++u) max_rows = std::max(max_rows, tasks[u].max_rows);
     IterLaunch probe{};
     probe.ntasks = T; probe.C = C; probe.M = 1; probe.precision = OEM_ITER_F32; probe.smem = smem;
+    probe.max_rows = max_rows;
     if (oem_iter_max_cluster(probe) >= 1 || C == 1) {
       t = 0;
       for (SrvJob* J : ready) {
@@ -397,6 +400,7 @@ int run_round(oem_server* S, std::vector<SrvJob*>& ready) {
       Lc.max_loops = S->iters_per_round;
       Lc.dstatus = ctx->dstatus;
       Lc.smem = smem;
+      Lc.max_rows = max_rows;
       LAUNCH(OEM_PROF_ITER, launch_oem_iter(Lc, s));
       break;
     }
