@@ -548,7 +548,27 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
     }
     // ---- 3. DSMEM: dbeta rows to every CTA, maxima into every CTA's slot
     {
-      if constexpr (kGrid) {
+      if constexpr (kF32) {
+        // by 16-byte units of the buffer: a unit inside the warp's rows goes
+        // as one float4 store, a unit shared with a neighbour warp element by
+        // element (i0 is a multiple of 4, so st is unit-aligned)
+        const int f0 = (i0 + wlo) * M, f1 = (i0 + whi) * M;
+        const int u0 = f0 >> 2, nu = ((f1 + 3) >> 2) - u0;
+        T* Dn = (kGrid ? xD : Dbuf) + (size_t)nxt * ldgs * M;
+        const int CC = kGrid ? 1 : C;
+        for (int e = lane; e < nu * CC; e += 32) {
+          const int u = u0 + e / CC, r = e % CC;
+          float* dst = (kGrid ? Dn : cluster.map_shared_rank(Dn, r)) + ((u ^ ((u >> 3) & (M - 1))) << 2);
+          const float* src = st + (4 * u - i0 * M);
+          if (4 * u >= f0 && 4 * u + 4 <= f1) {
+            *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(src);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (4 * u + q >= f0 && 4 * u + q < f1) dst[q] = src[q];
+          }
+        }
+      } else if constexpr (kGrid) {
         T* Dn = xD + (size_t)nxt * ldgs * M;
         for (int i = wlo + lane; i < whi; i += 32) store_row<T, M>(Dn, i0 + i, st + (size_t)i * M);
       } else {
