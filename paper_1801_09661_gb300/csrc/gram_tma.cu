@@ -6,17 +6,19 @@
 //   1. zpack_kernel: one streaming pass over X in fold order writes Z as
 //      bfloat16 — hi = bf16(z) and, in split mode, lo = bf16(z - hi) — with
 //      q_pad = round_up(p + ycols, 128) columns and every fold's rows padded
-//      with zero rows to a multiple of 32, so that the Gram kernel reads
-//      whole 32-row boxes that never cross a fold;
+//      with zero rows to a multiple of 64, so that the Gram kernel reads
+//      whole boxes that never cross a fold;
 //   2. gram_tma_kernel: one CTA per SM (persistent); a work item is a
-//      128 x 128 tile (ti <= tj) over a chunk of packed rows. One thread
-//      issues the TMA loads of each 32-row stage (64-column boxes, 128-byte
-//      swizzle, the layout the tensor core reads as MN-major bfloat16), one
-//      thread issues tcgen05.mma (hi.hi + hi.lo + lo.hi + lo.lo in split
-//      mode, hi.hi for bfloat16 data) into a double-buffered float32
-//      accumulator in tensor memory, and 16 epilogue warps add each finished
-//      flush window into a (hi, lo) float32 TwoSum pair in tensor memory and
-//      write hi + lo as float64 at the end of the item.
+//      128 x 128 tile (ti <= tj) over a chunk of packed rows. Two producer
+//      warps issue the TMA loads of alternate 32 KB stages (32 rows of hi and
+//      lo in split mode, 64 rows of hi in bfloat16 mode; 64-column boxes,
+//      128-byte swizzle, the layout the tensor core reads as MN-major
+//      bfloat16); one thread issues tcgen05.mma: hi.hi into a double-buffered
+//      float32 accumulator in tensor memory, and in split mode the cross terms
+//      hi.lo + lo.hi + lo.lo, 2^-8 smaller, into a second accumulator that is
+//      emptied every 1,024 rows. Eight epilogue warps add each finished window
+//      into a running TwoSum pair per element — hi in a register, lo in
+//      tensor memory — and write hi + lo as float64 at the end of the item.
 // Every mbarrier wait is bounded; on expiry the kernel records a timeout in
 // the status word, drains its MMAs, frees tensor memory and returns.
 #include "tcgen05.cuh"
@@ -28,19 +30,25 @@ namespace oem {
 
 namespace tc {
 
-constexpr int kTK = 32;                 // rows per stage
-constexpr int kTNS = 4;                 // operand stages
-constexpr int kTStageBytes = 32768;     // I_hi, I_lo, J_hi, J_lo panels of 8 KB
-constexpr int kTEpiWarps = 16;          // warps 0..15
-constexpr int kTMmaWarp = 16;
-constexpr int kTProdWarp = 17;
-constexpr int kTThreads = 18 * 32;
+constexpr int kTNS = 6;                 // operand stages (even: two producers, three slots each)
+constexpr int kTStageBytes = 32768;     // split: I_hi, I_lo, J_hi, J_lo of 32 rows; bfloat16: I_hi, J_hi of 64
+constexpr int kTEpiWarps = 8;           // warps 0..7
+constexpr int kTMmaWarp = 8;
+constexpr int kTProdWarp = 9;           // warps 9, 10: producers of even / odd stages
+constexpr int kTThreads = 11 * 32;
+constexpr int kTEpiCols = 64;           // columns per epilogue thread
+constexpr int kTCrossStages = 32;       // cross-term window (1,024 rows)
+
+// Tensor-memory columns: the hi.hi accumulator (two buffers), in split mode
+// the cross-term accumulator hi.lo + lo.hi + lo.lo (one buffer), and the lo
+// half of each element's running TwoSum pair (its hi half is a register).
+constexpr uint32_t kTD1 = 0, kTD2 = 256, kTLo = 384;
 
 struct TBars {
   unsigned long long full[kTNS];
   unsigned long long empty[kTNS];
-  unsigned long long acc_full[2];
-  unsigned long long acc_empty[2];
+  unsigned long long d1_full[2], d1_empty[2];
+  unsigned long long d2_full, d2_empty;
   unsigned long long drain;
   unsigned tmem_base;
   int abort;
@@ -60,25 +68,44 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
+// Bounded wait that ignores the abort flag (used to drain copies in flight).
+__device__ __forceinline__ bool mbar_wait_drain(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
 
 struct TmaGramArgs {
   int32_t split;   // 1: four products from (hi, lo); 0: hi only
   int32_t ntile1, ntiles;
-  ChunkTable pc;   // chunks of packed rows (row0, row1 multiples of 32)
+  ChunkTable pc;   // chunks of packed rows (row0, row1 multiples of kGramPackRows)
   double* partial; // [chunks][ntiles][128][128]
   unsigned* dstatus;
 };
 
+// The hi.hi window of an item ends at st1; the cross-term window ends there
+// too when st1 is a multiple of kTCrossStages or the item's last stage.
+__device__ __forceinline__ bool cross_ends(int st1, int nst) {
+  return st1 == nst || st1 % kTCrossStages == 0;
+}
+
+// SPLIT: four products from (hi, lo), 32-row stages; otherwise hi.hi only,
+// 64-row stages.
+template <bool SPLIT>
 __global__ void __launch_bounds__(kTThreads, 1)
     gram_tma_kernel(const __grid_constant__ CUtensorMap zhi, const __grid_constant__ CUtensorMap zlo,
                     TmaGramArgs a, int flush_stages) {
+  constexpr int kRS = SPLIT ? 32 : 64;        // rows per stage
+  constexpr uint32_t kAtom = kRS * 128;       // bytes of one 64-column box
+  constexpr uint32_t kPanel = 2 * kAtom;      // 128 columns
+  constexpr int kKS = kRS / 16;               // MMA k-steps per stage
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   TBars* bars = reinterpret_cast<TBars*>(smem + kTNS * kTStageBytes);
   volatile int* abort_flag = &bars->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool split = a.split != 0;
-  const int nprod = split ? 4 : 1;
+  constexpr bool split = SPLIT;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kTNS; ++s) {
@@ -86,9 +113,11 @@ __global__ void __launch_bounds__(kTThreads, 1)
       mbar_init(su32(&bars->empty[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(su32(&bars->acc_full[b]), 1);
-      mbar_init(su32(&bars->acc_empty[b]), kTEpiWarps);
+      mbar_init(su32(&bars->d1_full[b]), 1);
+      mbar_init(su32(&bars->d1_empty[b]), kTEpiWarps);
     }
+    mbar_init(su32(&bars->d2_full), 1);
+    mbar_init(su32(&bars->d2_empty), kTEpiWarps);
     mbar_init(su32(&bars->drain), 1);
     bars->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -106,150 +135,193 @@ __global__ void __launch_bounds__(kTThreads, 1)
   const int nitems = *a.pc.count * a.ntiles;
   const uint32_t stage0 = su32(smem);
 
-  if (warp == kTProdWarp) {
-    // ------------------------------------------------------------ TMA producer
+  if (warp == kTProdWarp || warp == kTProdWarp + 1) {
+    // ------------------------------------------------ TMA producers (2 warps)
+    // producer q issues the stages u with u % 2 == q (slots q, q + 2, q + 4)
     if (lane == 0) {
+      const uint32_t q = (uint32_t)(warp - kTProdWarp);
       bool ok = true;
-      uint32_t u = 0;
+      uint32_t u0 = 0;
+      int64_t last0 = -1, last1 = -1, last2 = -1;  // last stage issued into each of this producer's slots
       for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
         const int chunk = item / a.ntiles, tile = item % a.ntiles;
         int ti, tj;
         tile_coords(tile, a.ntile1, &ti, &tj);
         const bool diag = ti == tj;
-        const int64_t r0 = a.pc.row0[chunk];
-        const int nst = (int)((a.pc.row1[chunk] - r0) / kTK);
-        const uint32_t bytes = (uint32_t)((diag ? 1 : 2) * (split ? 16384 : 8192));
-        for (int st = 0; st < nst; ++st, ++u) {
-          const int s = u % kTNS;
+        const int row0 = (int)a.pc.row0[chunk];
+        const int nst = (int)((a.pc.row1[chunk] - a.pc.row0[chunk]) / kRS);
+        const uint32_t bytes = (diag ? 1u : 2u) * 16384u;
+        const int ci = ti * kTile, cj = tj * kTile;
+        for (int st = (int)((u0 ^ q) & 1u); st < nst; st += 2) {
+          const uint32_t u = u0 + (uint32_t)st;
+          const uint32_t s = u % kTNS;
           if (!mbar_wait(su32(&bars->empty[s]), ((u / kTNS) & 1) ^ 1, abort_flag)) { ok = false; break; }
           const uint32_t bar = su32(&bars->full[s]);
           mbar_expect_tx(bar, bytes);
-          const uint32_t base = stage0 + s * kTStageBytes;
-          const int row = (int)(r0 + (int64_t)st * kTK);
-          for (int pan = 0; pan < (diag ? 1 : 2); ++pan) {
-            const int col = (pan == 0 ? ti : tj) * kTile;
-            const uint32_t pb = base + pan * 16384;
-            tma_load_2d(pb, &zhi, col, row, bar);
-            tma_load_2d(pb + 4096, &zhi, col + 64, row, bar);
+          if ((s >> 1) == 0) last0 = u; else if ((s >> 1) == 1) last1 = u; else last2 = u;
+          const uint32_t pb = stage0 + s * kTStageBytes;
+          const int row = row0 + st * kRS;
+          tma_load_2d(pb, &zhi, ci, row, bar);
+          tma_load_2d(pb + kAtom, &zhi, ci + 64, row, bar);
+          if (split) {
+            tma_load_2d(pb + kPanel, &zlo, ci, row, bar);
+            tma_load_2d(pb + kPanel + kAtom, &zlo, ci + 64, row, bar);
+          }
+          if (!diag) {
+            tma_load_2d(pb + 16384, &zhi, cj, row, bar);
+            tma_load_2d(pb + 16384 + kAtom, &zhi, cj + 64, row, bar);
             if (split) {
-              tma_load_2d(pb + 8192, &zlo, col, row, bar);
-              tma_load_2d(pb + 8192 + 4096, &zlo, col + 64, row, bar);
+              tma_load_2d(pb + 16384 + kPanel, &zlo, cj, row, bar);
+              tma_load_2d(pb + 16384 + kPanel + kAtom, &zlo, cj + 64, row, bar);
             }
           }
         }
+        u0 += (uint32_t)nst;
       }
-      if (!ok) { bars->abort = 1; atomicOr(a.dstatus, kStatTimeout); }
+      if (!ok) {
+        bars->abort = 1;
+        atomicOr(a.dstatus, kStatTimeout);
+        // let this producer's copies in flight land before the CTA exits
+        if (last0 >= 0) mbar_wait_drain(su32(&bars->full[(uint32_t)last0 % kTNS]), ((uint32_t)last0 / kTNS) & 1);
+        if (last1 >= 0) mbar_wait_drain(su32(&bars->full[(uint32_t)last1 % kTNS]), ((uint32_t)last1 / kTNS) & 1);
+        if (last2 >= 0) mbar_wait_drain(su32(&bars->full[(uint32_t)last2 % kTNS]), ((uint32_t)last2 / kTNS) & 1);
+      }
     }
     __syncwarp();
   } else if (warp == kTMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t idesc = make_idesc(1u, 1u);  // bfloat16, MN-major
-      uint32_t u = 0, v = 0;
+      // descriptor of stage 0's first panel; other panels add their offset / 16
+      const uint64_t desc0 = make_desc(stage0, kAtom, 1024);
+      uint32_t u = 0, v1 = 0, v2 = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
         const int chunk = item / a.ntiles, tile = item % a.ntiles;
         int ti, tj;
         tile_coords(tile, a.ntile1, &ti, &tj);
-        const bool diag = ti == tj;
-        const int nst = (int)((a.pc.row1[chunk] - a.pc.row0[chunk]) / kTK);
-        for (int st0 = 0; st0 < nst && ok; st0 += flush_stages, ++v) {
-          const int buf = v & 1;
-          if (!mbar_wait(su32(&bars->acc_empty[buf]), ((v >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
+        const uint32_t joff = ti == tj ? 0u : 16384u;
+        const int nst = (int)((a.pc.row1[chunk] - a.pc.row0[chunk]) / kRS);
+        bool d2_fresh = true;
+        for (int st0 = 0; st0 < nst && ok; st0 += flush_stages, ++v1) {
+          const uint32_t b1 = v1 & 1;
+          if (!mbar_wait(su32(&bars->d1_empty[b1]), ((v1 >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
+          if (split && d2_fresh) {
+            if (!mbar_wait(su32(&bars->d2_empty), (v2 & 1) ^ 1, abort_flag)) { ok = false; break; }
+          }
           tc_fence_after();
-          const uint32_t d = tmem + (uint32_t)(buf * kTile);
+          const uint32_t d1 = tmem + kTD1 + b1 * kTile;
+          const uint32_t d2 = tmem + kTD2;
           const int st1 = min(nst, st0 + flush_stages);
           for (int st = st0; st < st1; ++st, ++u) {
-            const int s = u % kTNS;
+            const uint32_t s = u % kTNS;
             if (!mbar_wait(su32(&bars->full[s]), (u / kTNS) & 1, abort_flag)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t base = stage0 + s * kTStageBytes;
-            const uint32_t ihi = base, ilo = base + 8192;
-            const uint32_t jhi = diag ? ihi : base + 16384, jlo = diag ? ilo : base + 24576;
+            const uint64_t ihi = desc0 + ((s * kTStageBytes) >> 4);
+            const uint64_t ilo = ihi + (kPanel >> 4);
+            const uint64_t jhi = ihi + (joff >> 4), jlo = jhi + (kPanel >> 4);
 #pragma unroll
-            for (int ks = 0; ks < kTK / 16; ++ks) {
-              for (int pr = 0; pr < nprod; ++pr) {
-                const uint32_t pa = (pr >= 2) ? ilo : ihi;
-                const uint32_t pb = (pr & 1) ? jlo : jhi;
-                const uint64_t ad = make_desc(pa + ks * 2048, 4096, 1024);
-                const uint64_t bd = make_desc(pb + ks * 2048, 4096, 1024);
-                mma_f16(d, ad, bd, idesc, (st > st0 || ks > 0 || pr > 0) ? 1u : 0u);
+            for (int ks = 0; ks < kKS; ++ks) {
+              const uint64_t kof = (uint64_t)((ks * 2048) >> 4);
+              mma_f16(d1, ihi + kof, jhi + kof, idesc, (st > st0 || ks > 0) ? 1u : 0u);
+              if (split) {
+                mma_f16(d2, ihi + kof, jlo + kof, idesc, d2_fresh ? 0u : 1u);
+                mma_f16(d2, ilo + kof, jhi + kof, idesc, 1u);
+                mma_f16(d2, ilo + kof, jlo + kof, idesc, 1u);
+                d2_fresh = false;
               }
             }
             tc_commit(su32(&bars->empty[s]));
           }
           if (!ok) break;
-          tc_commit(su32(&bars->acc_full[buf]));
+          tc_commit(su32(&bars->d1_full[b1]));
+          if (split && cross_ends(st1, nst)) {
+            tc_commit(su32(&bars->d2_full));
+            ++v2;
+            d2_fresh = true;
+          }
         }
       }
       tc_commit(su32(&bars->drain));
       if (!mbar_wait(su32(&bars->drain), 0, abort_flag) && !*abort_flag) ok = false;
-      if (!ok) { bars->abort = 1; atomicOr(a.dstatus, kStatTimeout); }
+      if (!ok) {
+        bars->abort = 1;
+        atomicOr(a.dstatus, kStatTimeout);
+        mbar_wait_drain(su32(&bars->drain), 0);  // MMAs in flight finish before tensor memory is freed
+      }
     }
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
-    // warp w reads lanes 32 (w % 4) .. +31 and columns [32 (w / 4), +32)
+    // warp w owns lanes 32 (w % 4) .. +31 and columns [64 (w / 4), +64); the
+    // hi half of each of its 64 running TwoSum pairs stays in a register for
+    // the whole item, the lo half in tensor memory
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-    const int c0 = (warp >> 2) * 32;
-    uint32_t v = 0;
+    const uint32_t c0 = (uint32_t)(warp >> 2) * kTEpiCols;
+    uint32_t v1 = 0, v2 = 0;
     bool ok = true;
+    uint32_t h[kTEpiCols];
+    const uint32_t tlo = tmem + lane_base + kTLo + c0;
+    // adds the 64 float32 values of one finished window at taddr
+    auto add_window = [&](uint32_t taddr) {
+#pragma unroll
+      for (int q = 0; q < kTEpiCols / 8; ++q) {
+        uint32_t r[8], lo[8];
+        tmem_ld8(taddr + q * 8, r);
+        tmem_ld8(tlo + q * 8, lo);
+        tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) two_sum_x2(h[q * 8 + i], h[q * 8 + i + 1], lo[i], lo[i + 1], r[i], r[i + 1]);
+        tmem_st8(tlo + q * 8, lo);
+      }
+      tmem_st_wait();
+    };
     for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
       const int chunk = item / a.ntiles, tile = item % a.ntiles;
-      const int nst = (int)((a.pc.row1[chunk] - a.pc.row0[chunk]) / kTK);
-      bool first = true;
-      for (int st0 = 0; st0 < nst; st0 += flush_stages, ++v) {
-        const int buf = v & 1;
-        if (!mbar_wait(su32(&bars->acc_full[buf]), (v >> 1) & 1, abort_flag)) { ok = false; break; }
-        tc_fence_after();
-        const uint32_t acc = tmem + lane_base + (uint32_t)(buf * kTile);
-        const uint32_t thi = tmem + lane_base + 256u, tlo = tmem + lane_base + 384u;
+      const int nst = (int)((a.pc.row1[chunk] - a.pc.row0[chunk]) / kRS);
 #pragma unroll
-        for (int cb = c0; cb < c0 + 32; cb += 16) {
-          uint32_t ra[16], rh[16], rl[16];
-          tmem_ld16(acc + cb, ra);
-          if (!first) { tmem_ld16(thi + cb, rh); tmem_ld16(tlo + cb, rl); }
-          tmem_ld_wait();
-          if (first) {
+      for (int i = 0; i < kTEpiCols; ++i) h[i] = 0u;
+      {
+        const uint32_t z[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
-            for (int i = 0; i < 16; ++i) { rh[i] = ra[i]; rl[i] = 0u; }
-          } else {
-#pragma unroll
-            for (int i = 0; i < 16; i += 2) two_sum_x2(rh[i], rh[i + 1], rl[i], rl[i + 1], ra[i], ra[i + 1]);
-          }
-          tmem_st16(thi + cb, rh);
-          tmem_st16(tlo + cb, rl);
-        }
+        for (int q = 0; q < kTEpiCols / 8; ++q) tmem_st8(tlo + q * 8, z);
         tmem_st_wait();
+      }
+      for (int st0 = 0; st0 < nst; st0 += flush_stages, ++v1) {
+        const uint32_t b1 = v1 & 1;
+        if (!mbar_wait(su32(&bars->d1_full[b1]), (v1 >> 1) & 1, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        add_window(tmem + lane_base + kTD1 + b1 * kTile + c0);
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(su32(&bars->acc_empty[buf]));
-        first = false;
+        if (lane == 0) mbar_arrive(su32(&bars->d1_empty[b1]));
+        const int st1 = min(nst, st0 + flush_stages);
+        if (split && cross_ends(st1, nst)) {
+          if (!mbar_wait(su32(&bars->d2_full), v2 & 1, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          add_window(tmem + lane_base + kTD2 + c0);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(su32(&bars->d2_empty));
+          ++v2;
+        }
       }
       if (!ok) break;
       double* out = a.partial + ((int64_t)chunk * a.ntiles + tile) * (kTile * kTile) +
-                    (int64_t)((warp & 3) * 32 + lane) * kTile;
-      const uint32_t thi = tmem + lane_base + 256u, tlo = tmem + lane_base + 384u;
+                    (int64_t)((warp & 3) * 32 + lane) * kTile + c0;
 #pragma unroll
-      for (int cb = c0; cb < c0 + 32; cb += 16) {
-        uint32_t rh[16], rl[16];
-        if (nst > 0) {
-          tmem_ld16(thi + cb, rh);
-          tmem_ld16(tlo + cb, rl);
-          tmem_ld_wait();
-        } else {
+      for (int q = 0; q < kTEpiCols / 8; ++q) {
+        uint32_t lo[8];
+        tmem_ld8(tlo + q * 8, lo);
+        tmem_ld_wait();
 #pragma unroll
-          for (int i = 0; i < 16; ++i) { rh[i] = 0u; rl[i] = 0u; }
-        }
-#pragma unroll
-        for (int i = 0; i < 16; i += 2) {
+        for (int i = 0; i < 8; i += 2) {
           double2 w;
-          w.x = (double)__uint_as_float(rh[i]) + (double)__uint_as_float(rl[i]);
-          w.y = (double)__uint_as_float(rh[i + 1]) + (double)__uint_as_float(rl[i + 1]);
-          *reinterpret_cast<double2*>(out + cb + i) = w;
+          w.x = (double)__uint_as_float(h[q * 8 + i]) + (double)__uint_as_float(lo[i]);
+          w.y = (double)__uint_as_float(h[q * 8 + i + 1]) + (double)__uint_as_float(lo[i + 1]);
+          *reinterpret_cast<double2*>(out + q * 8 + i) = w;
         }
       }
-      tc_fence_before();
     }
     if (!ok) { bars->abort = 1; atomicOr(a.dstatus, kStatTimeout); }
   }
@@ -268,14 +340,14 @@ __global__ void __launch_bounds__(kTThreads, 1)
 
 // Chunks of the packed row space: fold k holds packed rows
 // [poff[k], poff[k] + round_up(n_k, 32)), cut into chunks of chunk_rows (a
-// multiple of 32). One thread; K <= 64.
+// multiple of kGramPackRows). One thread; K <= 64.
 __global__ void packed_chunks_kernel(const int64_t* __restrict__ fold_off, int K, int64_t chunk_rows,
                                      ChunkTable pc, int max_chunks, unsigned* dstatus) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   int64_t off = 0;
   int c = 0;
   for (int k = 0; k < K; ++k) {
-    const int64_t np = (fold_off[k + 1] - fold_off[k] + 31) / 32 * 32;
+    const int64_t np = (fold_off[k + 1] - fold_off[k] + kGramPackRows - 1) / kGramPackRows * kGramPackRows;
     pc.fold_off[k] = off;
     pc.fold_c0[k] = c;
     for (int64_t r = 0; r < np; r += chunk_rows) {
@@ -377,7 +449,7 @@ __global__ void __launch_bounds__(256) zpack_kernel(ZPackArgs a) {
 
 size_t gram_tma_smem_bytes() { return (size_t)tc::kTNS * tc::kTStageBytes + sizeof(tc::TBars) + 1024; }
 
-static cudaError_t encode_z_map(CUtensorMap* m, void* base, int64_t rows, int qp) {
+static cudaError_t encode_z_map(CUtensorMap* m, void* base, int64_t rows, int qp, int box_rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -389,7 +461,7 @@ static cudaError_t encode_z_map(CUtensorMap* m, void* base, int64_t rows, int qp
   }
   const cuuint64_t dims[2] = {(cuuint64_t)qp, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)qp * 2};
-  const cuuint32_t box[2] = {64, (cuuint32_t)tc::kTK};
+  const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -416,20 +488,26 @@ cudaError_t launch_zpack(const GramArgs& a, int K, const TmaBufs& t, cudaStream_
 
 cudaError_t launch_gram_tma(const GramArgs& a, const TmaBufs& t, int flush_rows, cudaStream_t s) {
   if (flush_rows <= 0) flush_rows = 256;
-  const int flush_stages = (flush_rows + tc::kTK - 1) / tc::kTK;
+  const bool split = t.zlo != nullptr;
+  const int rs = split ? 32 : 64;  // rows per stage
+  // hi.hi windows of a power-of-two number of stages that divides the
+  // cross-term window, so both windows end together
+  int flush_stages = 1;
+  while (flush_stages * 2 * rs <= flush_rows && flush_stages * 2 <= tc::kTCrossStages) flush_stages *= 2;
   CUtensorMap mhi, mlo;
-  cudaError_t e = encode_z_map(&mhi, t.zhi, t.rows_cap, t.qp);
+  cudaError_t e = encode_z_map(&mhi, t.zhi, t.rows_cap, t.qp, rs);
   if (e != cudaSuccess) return e;
-  e = encode_z_map(&mlo, t.zlo ? (void*)t.zlo : (void*)t.zhi, t.rows_cap, t.qp);
+  e = encode_z_map(&mlo, split ? t.zlo : t.zhi, t.rows_cap, t.qp, rs);
   if (e != cudaSuccess) return e;
   const size_t smem = gram_tma_smem_bytes();
-  e = cudaFuncSetAttribute(tc::gram_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = split ? tc::gram_tma_kernel<true> : tc::gram_tma_kernel<false>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = kNumSMsHint;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   tc::TmaGramArgs g{};
-  g.split = t.zlo ? 1 : 0;
+  g.split = split ? 1 : 0;
   g.ntile1 = a.ntile1;
   g.ntiles = a.ntiles;
   g.pc = t.pc;
@@ -437,7 +515,7 @@ cudaError_t launch_gram_tma(const GramArgs& a, const TmaBufs& t, int flush_rows,
   g.dstatus = a.dstatus;
   const int64_t items = (int64_t)t.max_chunks * a.ntiles;
   const int grid = (int)(items < sms ? items : sms);
-  tc::gram_tma_kernel<<<grid, tc::kTThreads, smem, s>>>(mhi, mlo, g, flush_stages);
+  kern<<<grid, tc::kTThreads, smem, s>>>(mhi, mlo, g, flush_stages);
   return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 #include "oem_internal.cuh"
 
 #include <algorithm>
+#include <numeric>
 #include <array>
 #include <cmath>
 #include <cstdarg>
@@ -251,11 +252,23 @@ inline GramPlan plan_gram(oem_ctx* ctx, int64_t n, int64_t p, int K, int32_t mod
   // otherwise the converting kernel reads X directly
   if (mode == OEM_GRAM_SPLIT_BF16 || mode == OEM_GRAM_BF16) {
     g.qp = (g.q + 127) / 128 * 128;
-    g.rows_cap = n + 32 * (int64_t)K;
-    g.pmax_chunks = (int)((g.rows_cap + cr - 1) / cr + K);
+    g.rows_cap = n + kGramPackRows * (int64_t)K;
+    // The persistent kernel takes items (chunk, tile) in turn; a chunk count
+    // that is a multiple of sms / gcd(ntiles, sms) gives every SM the same
+    // number of items.
+    const int64_t sms = ctx->num_sms;
+    const int64_t unit = sms / std::gcd((int64_t)g.ntiles, sms);
+    const int64_t want = std::max<int64_t>(1, (target_items / g.ntiles + unit / 2) / unit) * unit;
+    int64_t tcr = (g.rows_cap + want - 1) / want;
+    tcr = std::max<int64_t>(1024, (tcr + 127) / 128 * 128);
+    g.pmax_chunks = (int)((g.rows_cap + tcr - 1) / tcr + K);
     const size_t bytes = (size_t)g.rows_cap * g.qp * 2 * (mode == OEM_GRAM_SPLIT_BF16 ? 2 : 1);
     const size_t partial = (size_t)g.pmax_chunks * g.ntiles * g.T * g.T * sizeof(double);
     g.tma = bytes + partial <= ctx->budget / 2;
+    if (g.tma) {
+      g.chunk_rows = tcr;
+      g.max_chunks = (int)((n + tcr - 1) / tcr + K);
+    }
   }
   return g;
 }
@@ -319,9 +332,10 @@ inline int run_gram(oem_ctx* ctx, const GramPlan& g, GramBufs& b, const void* X,
     b.t.rows_cap = g.rows_cap;
     b.t.max_chunks = g.pmax_chunks;
     b.t.chunk_rows = g.chunk_rows;
-    // split mode (4 products) flushes every 64 rows, bfloat16 every 256 (see
-    // below)
-    const int flush = g.mode == OEM_GRAM_SPLIT_BF16 ? 64 : 256;
+    // The hi.hi product is summed over 128 rows (split mode) or 256 rows
+    // (bfloat16) in float32 tensor memory before it is added to the
+    // compensated sum; the cross terms, 2^-8 smaller, over 1,024 rows.
+    const int flush = g.mode == OEM_GRAM_SPLIT_BF16 ? 128 : 256;
     LAUNCH(OEM_PROF_GRAM_TC, launch_zpack(a, g.K, b.t, s));
     LAUNCH(OEM_PROF_GRAM_TC, launch_gram_tma(a, b.t, flush, s));
     GramArgs r = a;

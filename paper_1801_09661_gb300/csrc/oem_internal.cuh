@@ -11,6 +11,8 @@
 namespace oem {
 
 constexpr int kNumSMsHint = 152;
+// Packed copies of Z pad every fold's rows to a multiple of this.
+constexpr int kGramPackRows = 64;
 
 // Device-side status word bits (ctx->dstatus[0]); oem_sync() maps them to codes.
 enum : unsigned {
@@ -61,7 +63,7 @@ struct TmaBufs {
   void* zhi;            // [rows_cap][qp] bfloat16
   void* zlo;            // [rows_cap][qp] bfloat16 (split mode) or NULL
   int32_t qp;
-  int64_t rows_cap;     // n + 32 K
+  int64_t rows_cap;     // n + kGramPackRows K
   ChunkTable pc;        // chunks of packed rows; pc.fold_off = packed fold offsets
   int32_t max_chunks;
   int64_t chunk_rows;
