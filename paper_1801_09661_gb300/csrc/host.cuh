@@ -137,12 +137,12 @@ struct Arena {
 template <typename A>
 inline void lanczos_request(A& ar, LanczosWork& w, int64_t p, int batch, int steps) {
   ar.add(&w.V, (size_t)batch * (lanczos_steps_eff(steps, p) + 3) * p);
-  ar.add(&w.alpha, (size_t)batch * 128);
-  ar.add(&w.beta, (size_t)batch * 128);
+  ar.add(&w.alpha, (size_t)batch * kLzMax);
+  ar.add(&w.beta, (size_t)batch * kLzMax);
   ar.add(&w.fro, (size_t)batch);
+  ar.add(&w.gmax, (size_t)batch);
   ar.add(&w.mlen, (size_t)batch);
-  ar.add(&w.bar, (size_t)batch * 2);
-  ar.add(&w.part, (size_t)batch * kLzGroupMax * kLzPartStride);
+  ar.add(&w.Gs, (size_t)batch * p * p);
 }
 
 inline int arena_commit(oem_ctx* ctx, Arena& A, cudaStream_t s) {

@@ -1,222 +1,294 @@
 // The OEM constant d (Section 2.1): OEM converges for every d >= lambda_1(G)
 // and fastest at d = lambda_1, which the paper computes by Lanczos. Here:
-// float64 Lanczos (three-term recurrence, v_1 = 1/sqrt(p)) for a batch of
-// Grams, then the largest Ritz value theta of the tridiagonal T_m and its
-// residual norm r = beta_m |s_m|; d = theta + r bounds lambda_1 from above.
+// Lanczos (three-term recurrence, v_1 = 1/sqrt(p), full reorthogonalisation)
+// for a batch of Grams, then the largest Ritz value theta of the tridiagonal
+// T_m and its residual norm r = beta_m |s_m|; d = theta + r bounds lambda_1
+// from above.
 //
-// All steps run in one cooperative launch: each Gram is served by a group of
-// CTAs that own contiguous rows, with three group barriers per step (after the
-// mat-vec and after the first Gram-Schmidt pass, for the projections
-// v_i . w; after the second pass, for beta). The basis is reorthogonalised
-// in full (classical Gram-Schmidt twice per step). The next mat-vec reads
-// the unnormalised w of the last step and scales by 1 / beta; per-CTA
-// partial sums are added in rank order (the same d on every run).
+// One thread-block cluster per Gram runs all its steps in one launch: the
+// CTAs own contiguous rows, reduce through distributed shared memory and
+// meet at three cluster barriers per step (after the partial projections of
+// each Gram-Schmidt pass, and after the exchange of w''). All arithmetic is
+// double-float (pairs of float32, about 48 significant bits) on the float32
+// pipe: float64 runs at 1/64 of float32 on this part, with long latencies.
+// Cluster partial sums are added in rank order (the same d on every run).
 #include "oem_internal.cuh"
+
+#include <cooperative_groups.h>
 
 #include <algorithm>
 
 namespace oem {
 
+namespace cg = cooperative_groups;
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+
+// ------------------------------------------------------------ double-float
+// A value is a float2 (hi, lo) with |lo| <= ulp(hi) / 2: about 48 significant
+// bits from float32 arithmetic (float64 arithmetic runs at 1/64 of float32 on
+// this part, with long latencies). TwoSum and TwoProduct are the error-free
+// transformations of Knuth and of Dekker (with a fused multiply-add).
+__device__ __forceinline__ float2 df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ float2 df_quick(float a, float b) {  // |a| >= |b| or a == 0
+  const float s = a + b;
+  return make_float2(s, b - (s - a));
+}
+__device__ __forceinline__ float2 df_add(float2 x, float2 y) {
+  const float2 s = df_two_sum(x.x, y.x);
+  const float2 t = df_two_sum(x.y, y.y);
+  float2 u = df_quick(s.x, s.y + t.x);
+  return df_quick(u.x, u.y + t.y);
+}
+__device__ __forceinline__ float2 df_neg(float2 x) { return make_float2(-x.x, -x.y); }
+__device__ __forceinline__ float2 df_mul(float2 x, float2 y) {
+  const float p = x.x * y.x;
+  float e = fmaf(x.x, y.x, -p);
+  e = fmaf(x.x, y.y, e);
+  e = fmaf(x.y, y.x, e);
+  return df_quick(p, e);
+}
+__device__ __forceinline__ float2 df_scale(float2 x, float s) { return make_float2(x.x * s, x.y * s); }  // s a power of two
+// running dot product: (h, l) += x * y, renormalised by the caller at the end
+__device__ __forceinline__ void df_dot_acc(float& h, float& l, float2 x, float2 y) {
+  const float p = x.x * y.x;
+  const float pe = fmaf(x.x, y.x, -p);
+  const float cr = fmaf(x.x, y.y, x.y * y.x);
+  const float s = h + p;
+  const float bb = s - h;
+  l += ((h - (s - bb)) + (p - bb)) + (pe + cr);
+  h = s;
+}
+__device__ __forceinline__ float2 df_norm(float h, float l) { return df_two_sum(h, l); }
+// 1 / x and sqrt(x): float32 estimate, one Newton step in double-float
+__device__ __forceinline__ float2 df_rcp(float2 x) {
+  const float r = 1.f / x.x;
+  const float2 e = df_add(make_float2(1.f, 0.f), df_neg(df_mul(x, make_float2(r, 0.f))));
+  return df_quick(r, r * e.x);
+}
+__device__ __forceinline__ float2 df_sqrt(float2 x) {
+  if (!(x.x > 0.f)) return make_float2(0.f, 0.f);
+  const float r = sqrtf(x.x);
+  const float2 e = df_add(x, df_neg(df_mul(make_float2(r, 0.f), make_float2(r, 0.f))));
+  return df_quick(r, e.x * (0.5f / r));
+}
+__device__ __forceinline__ float2 df_shfl_xor(float2 v, int o) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+__device__ __forceinline__ float2 df_from(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
 }
 
-// ||G_b||_F^2 partial sums (float32 arithmetic is plenty: it only scales the
-// breakdown test) and v_1 = 1/sqrt(p).
-__global__ void lz_init_kernel(const double* __restrict__ G, int64_t p, int64_t ldg,
-                               int64_t strideG, LanczosWork w, int steps) {
+// Power of two s with s * max|G_b| in [0.5, 1): every double-float value of
+// the recurrence stays far inside the float32 range.
+__device__ __forceinline__ float lz_scale(float gmax) {
+  if (!(gmax > 0.f) || !isfinite(gmax)) return 1.f;
+  int e;
+  frexpf(gmax, &e);  // gmax = m 2^e, m in [0.5, 1)
+  return ldexpf(1.f, -e);
+}
+
+// (hi, lo) float32 copy of G_b and max |G_b| (atomicMax on the bits of a
+// non-negative float: the same value whatever the order).
+__global__ void lz_split_kernel(const double* __restrict__ G, int64_t p, int64_t ldg, int64_t strideG,
+                                LanczosWork w) {
   const int b = blockIdx.y;
   const double* Gb = G + b * strideG;
-  float s = 0.f;
+  float2* out = w.Gs + (int64_t)b * p * p;
+  float mx = 0.f;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < p * p;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const float v = (float)Gb[(e / p) * ldg + (e % p)];
-    s = fmaf(v, v, s);
+    const float2 v = df_from(Gb[(e / p) * ldg + (e % p)]);
+    out[e] = v;
+    mx = fmaxf(mx, fabsf(v.x));
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(&w.fro[b], (double)s);
-  if (blockIdx.x == 0) {
-    double* V = w.V + (int64_t)b * (steps + 3) * p;
-    const double v0 = 1.0 / sqrt((double)p);
-    for (int64_t i = threadIdx.x; i < p; i += blockDim.x) {
-      V[i] = v0;          // slot 0: v_0 (the start vector)
-    }
-    if (threadIdx.x == 0) w.mlen[b] = 0;
-  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned*>(w.gmax) + b, __float_as_uint(mx));
 }
 
-constexpr int kLzThreads = 256;
-constexpr int kLzGather = 64;  // CTAs per Gram at most
-constexpr int kLzWarps = kLzThreads / 32;
-
-// Sum of one value per thread of the CTA, in a fixed order (thread 0's
-// result is the CTA's partial; every thread returns it).
-__device__ double block_sum_fixed(double v, double* red) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) red[w] = v;
+// Sum of one double-float per thread of the CTA in a fixed order; every
+// thread returns it.
+__device__ float2 block_sum_df(float2 v, float2* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+  const int wp = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[wp] = v;
   __syncthreads();
-  double t = 0.0;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kLzWarps; ++i) t += red[i];
-    red[kLzWarps] = t;
+    float2 t = red[0];
+    for (int i = 1; i < kLzThreads / 32; ++i) t = df_add(t, red[i]);
+    red[kLzThreads / 32] = t;
   }
   __syncthreads();
-  t = red[kLzWarps];
+  const float2 t = red[kLzThreads / 32];
   __syncthreads();
   return t;
 }
 
-// Steps 0 .. steps-1 for Gram b = b0 + blockIdx.x / GC; CTA rank owns rows
-// [r0, r1). V slots (each p doubles): i = 0 .. steps hold v_i on the own
-// rows (slot 0 starts as the full v_0 = 1/sqrt(p)); steps + 1 + (j & 1)
-// holds w_j for all rows. Full reorthogonalisation by classical Gram-Schmidt
-// applied twice: w' = w - sum_{i <= j} (v_i . w) v_i, then
-// w'' = w' - sum_{i <= j} (v_i . w') v_i; alpha_j = v_j . w + v_j . w',
-// beta_j = ||w''||. One group barrier after each of the three reductions.
-__global__ void __launch_bounds__(kLzThreads) lz_steps_kernel(const double* __restrict__ G, int64_t p,
-                                                             int64_t ldg, int64_t strideG, int steps,
-                                                             LanczosWork w, int GC, int b0,
-                                                             unsigned* dstatus) {
-  extern __shared__ double src_s[];  // [p] the vector the mat-vec multiplies, then
-                                     // [GC][j+1] the group's partials (gathered)
-  double* gath = src_s + ((p + 1) & ~1LL);
-  __shared__ double red[kLzWarps + 1];
-  __shared__ double cs[kLzMax];      // projections of the current pass, i <= j
-  const int b = b0 + (int)(blockIdx.x / GC), rank = (int)(blockIdx.x % GC);
+// Steps 0 .. steps-1 of the Lanczos recurrence for Gram b = blockIdx.x / C,
+// run by one thread-block cluster of C CTAs in double-float arithmetic on
+// the scaled matrix s G_b. CTA rank owns rows [rank per, +per); it holds the
+// whole current vector X, its rows of G_b, of the basis V and of w. Per step:
+//   v_j = X / beta_{j-1}; w = s G_b v_j on the own rows;
+//   two classical Gram-Schmidt passes w <- w - sum_{i <= j} (v_i . w) v_i,
+//   each projection summed over the cluster: every CTA stores its partial
+//   into a slot of every peer (DSMEM), a cluster barrier, then each CTA adds
+//   the C slots in rank order;
+//   the CTAs store their rows of w'' into every peer's X together with their
+//   partial ||w''||^2, a cluster barrier, beta_j = ||w''|| (the same on every
+//   CTA).
+// alpha_j = v_j . w + v_j . w'. Three cluster barriers per step.
+__global__ void __launch_bounds__(kLzThreads, 1) lz_cluster_kernel(int64_t p, int steps, LanczosWork w, LzPlan L) {
+  extern __shared__ __align__(16) unsigned char lz_smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = L.C;
+  const int rank = (int)cluster.block_rank();
+  const int b = (int)(blockIdx.x / C);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t per = (p + GC - 1) / GC;
-  const int64_t r0 = min(p, (int64_t)rank * per), r1 = min(p, r0 + per);
+  float2* X = reinterpret_cast<float2*>(lz_smem + L.off_X);
+  float2* P1 = reinterpret_cast<float2*>(lz_smem + L.off_P1);
+  float2* P2 = reinterpret_cast<float2*>(lz_smem + L.off_P2);
+  float2* Bq = reinterpret_cast<float2*>(lz_smem + L.off_B);
+  float2* W = reinterpret_cast<float2*>(lz_smem + L.off_W);
+  __shared__ float2 red[kLzThreads / 32 + 1];
+  __shared__ float2 cs[kLzMax];
+  const int64_t r0 = min(p, (int64_t)rank * L.per), r1 = min(p, r0 + L.per);
   const int R = (int)(r1 - r0);
-  double* V = w.V + (int64_t)b * (steps + 3) * p;
-  const double* Gb = G + b * strideG;
-  unsigned* bar = w.bar + 2 * b;
-  // partials per CTA: pass-1 projections [0, kLzMax), pass-2 projections
-  // [kLzMax, 2 kLzMax), ||w''||^2 at 2 kLzMax
-  double* part = w.part + (int64_t)b * kLzGroupMax * kLzPartStride;
-  double* mine = part + (int64_t)rank * kLzPartStride;
-  const double tol = 1e-13 * sqrt(w.fro[b]);
-  unsigned gen = 0;
-  double inv_prev = 1.0;
-  for (int j = 0; j < steps; ++j) {
-    double* vj = V + (int64_t)j * p;
-    double* wj = V + (int64_t)(steps + 1 + (j & 1)) * p;
-    const double* src = (j == 0) ? V : V + (int64_t)(steps + 1 + ((j + 1) & 1)) * p;
-    const double scale = (j == 0) ? 1.0 : inv_prev;
-    // ---- v_j = w''_{j-1} / beta_{j-1} (all rows into shared memory, own
-    // rows kept), then w = G v_j on the own rows
-    for (int64_t c = threadIdx.x; c < p; c += kLzThreads) src_s[c] = __ldcg(src + c) * scale;
-    __syncthreads();
-    if (j > 0)  // (v_0 is already in slot 0)
-      for (int64_t row = r0 + threadIdx.x; row < r1; row += kLzThreads) vj[row] = src_s[row];
-    for (int64_t row = r0 + warp; row < r1; row += kLzWarps) {
-      const double* g = Gb + row * ldg;
-      double acc = 0.0;
-      for (int64_t c = lane; c < p; c += 32) acc = fma(g[c], src_s[c], acc);
-      acc = warp_sum(acc);
-      if (lane == 0) wj[row] = acc;
+  // basis rows: V(i, t) = vb[i * vs + t]
+  float2* vb = L.vsm ? reinterpret_cast<float2*>(lz_smem + L.off_V)
+                     : reinterpret_cast<float2*>(w.V + (int64_t)b * (steps + 3) * p) + r0;
+  const int64_t vs = L.vsm ? L.vstride : p;
+  const float2* Gr = w.Gs + (int64_t)b * p * p + r0 * p;  // own rows of G_b, row stride p
+  if (L.gsm) {
+    float2* Gsm = reinterpret_cast<float2*>(lz_smem + L.off_G);
+    const float4* src = reinterpret_cast<const float4*>(Gr);
+    float4* dst = reinterpret_cast<float4*>(Gsm);
+    const int64_t n2 = (int64_t)R * p;  // float2 elements
+    if ((((int64_t)b * p * p + r0 * p) & 1) == 0) {  // 16-byte aligned start: copy in float4
+      for (int64_t e = threadIdx.x; e < n2 / 2; e += kLzThreads) dst[e] = __ldg(src + e);
+      if ((n2 & 1) && threadIdx.x == 0) Gsm[n2 - 1] = Gr[n2 - 1];
+    } else {
+      for (int64_t e = threadIdx.x; e < n2; e += kLzThreads) Gsm[e] = Gr[e];
     }
-    double alpha = 0.0;
+    Gr = Gsm;
+  }
+  const float s = lz_scale(w.gmax[b]);
+  // ||s G_b||_F^2 over the own rows, summed over the cluster in rank order
+  {
+    float fh = 0.f, fl = 0.f;
+    for (int64_t e = threadIdx.x; e < (int64_t)R * p; e += kLzThreads) {
+      const float2 g = df_scale(Gr[e], s);
+      df_dot_acc(fh, fl, g, g);
+    }
+    const float2 f = block_sum_df(df_norm(fh, fl), red);
+    if (threadIdx.x < C) cluster.map_shared_rank(Bq, (int)threadIdx.x)[rank] = f;
+  }
+  {
+    const float2 v0 = df_from(1.0 / sqrt((double)p));
+    for (int64_t c = threadIdx.x; c < p; c += kLzThreads) X[c] = v0;
+  }
+  cluster.sync();  // every CTA initialised (and its ||G||_F^2 part delivered)
+  float2 fro2 = Bq[0];
+  for (int k = 1; k < C; ++k) fro2 = df_add(fro2, Bq[k]);
+  if (rank == 0 && threadIdx.x == 0) {
+    w.fro[b] = (double)fro2.x + (double)fro2.y;
+    w.mlen[b] = 0;
+  }
+  const float tol = 1e-13f * sqrtf(fro2.x);
+  float2 scale = make_float2(1.f, 0.f);  // v_j = X * scale
+  for (int j = 0; j < steps; ++j) {
+    // ---- v_j (all rows) and its own rows in V
+    for (int64_t c = threadIdx.x; c < p; c += kLzThreads) X[c] = df_mul(X[c], scale);
+    __syncthreads();
+    for (int t = threadIdx.x; t < R; t += kLzThreads) vb[(int64_t)j * vs + t] = X[r0 + t];
+    // ---- w = s G v_j on the own rows (two interleaved sums per lane)
+    for (int t = warp; t < R; t += kLzThreads / 32) {
+      const float2* g = Gr + (int64_t)t * p;
+      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+      int c = lane;
+      for (; c + 32 < p; c += 64) {
+        df_dot_acc(h0, l0, g[c], X[c]);
+        df_dot_acc(h1, l1, g[c + 32], X[c + 32]);
+      }
+      if (c < p) df_dot_acc(h0, l0, g[c], X[c]);
+      float2 acc = df_add(df_norm(h0, l0), df_norm(h1, l1));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc = df_add(acc, df_shfl_xor(acc, o));
+      if (lane == 0) W[t] = df_scale(acc, s);
+    }
+    float2 alpha = make_float2(0.f, 0.f);
+    const int nv = j + 1;
     for (int pass = 0; pass < 2; ++pass) {
+      float2* Pb = pass ? P2 : P1;
       __syncthreads();
-      // partial projections v_i . w over the own rows, i <= j
-      for (int i = threadIdx.x; i <= j; i += kLzThreads) {
-        const double* vi = V + (int64_t)i * p;
-        double t = 0.0;
-        for (int64_t row = r0; row < r1; ++row) t = fma(vi[row], wj[row], t);
-        mine[pass * kLzMax + i] = t;
-      }
-      if (!group_barrier(bar, (unsigned)GC, gen)) {
-        if (threadIdx.x == 0) atomicOr(dstatus, kStatTimeout);
-        return;
-      }
-      // gather all partials at once (independent loads), then add them per
-      // projection in rank order
-      const int nv = j + 1;
-      for (int e = threadIdx.x; e < GC * nv; e += kLzThreads)
-        gath[e] = __ldcg(part + (int64_t)(e / nv) * kLzPartStride + pass * kLzMax + e % nv);
-      __syncthreads();
+      // partial projections v_i . w over the own rows, into slot `rank` of every CTA
       for (int i = threadIdx.x; i < nv; i += kLzThreads) {
-        double t = 0.0;
-        for (int r = 0; r < GC; ++r) t += gath[r * nv + i];
+        float h = 0.f, l = 0.f;
+        for (int u = 0; u < R; ++u) df_dot_acc(h, l, vb[(int64_t)i * vs + u], W[u]);
+        const float2 t = df_norm(h, l);
+        for (int k = 0; k < C; ++k) cluster.map_shared_rank(Pb, k)[rank * kLzMax + i] = t;
+      }
+      cluster.sync();
+      for (int i = threadIdx.x; i < nv; i += kLzThreads) {
+        float2 t = Pb[i];
+        for (int k = 1; k < C; ++k) t = df_add(t, Pb[k * kLzMax + i]);
         cs[i] = t;
       }
       __syncthreads();
-      alpha += cs[j];
+      alpha = df_add(alpha, cs[j]);
       // w <- w - sum_i (v_i . w) v_i on the own rows: 16 threads per row,
       // thread sub takes i = sub, sub + 16, ...; fixed shuffle tree
       for (int t0 = 0; t0 < R; t0 += kLzThreads / 16) {
         const int t = t0 + (int)(threadIdx.x >> 4), sub = (int)(threadIdx.x & 15);
-        double v = 0.0;
+        float h = 0.f, l = 0.f;
         if (t < R)
-          for (int i = sub; i < nv; i += 16) v = fma(cs[i], V[(int64_t)i * p + r0 + t], v);
+          for (int i = sub; i < nv; i += 16) df_dot_acc(h, l, cs[i], vb[(int64_t)i * vs + t]);
+        float2 v = df_norm(h, l);
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (t < R && sub == 0) wj[r0 + t] -= v;
+        for (int o = 8; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+        if (t < R && sub == 0) W[t] = df_add(W[t], df_neg(v));
       }
     }
-    double pb = 0.0;
-    for (int t = threadIdx.x; t < R; t += kLzThreads) pb = fma(wj[r0 + t], wj[r0 + t], pb);
-    const double pb_cta = block_sum_fixed(pb, red);
-    if (threadIdx.x == 0) mine[2 * kLzMax] = pb_cta;
-    if (!group_barrier(bar, (unsigned)GC, gen)) {
-      if (threadIdx.x == 0) atomicOr(dstatus, kStatTimeout);
-      return;
+    __syncthreads();
+    // ---- ||w''||^2 partial; w'' rows and the partial into every CTA
+    float bh = 0.f, bl = 0.f;
+    for (int t = threadIdx.x; t < R; t += kLzThreads) df_dot_acc(bh, bl, W[t], W[t]);
+    const float2 pb_cta = block_sum_df(df_norm(bh, bl), red);
+    for (int e = threadIdx.x; e < C * R; e += kLzThreads) {
+      const int k = e / R, t = e % R;
+      cluster.map_shared_rank(X, k)[r0 + t] = W[t];
     }
-    double bb = threadIdx.x < GC ? __ldcg(part + (int64_t)threadIdx.x * kLzPartStride + 2 * kLzMax) : 0.0;
-    const double bn = sqrt(block_sum_fixed(bb, red));
+    if (threadIdx.x < C) cluster.map_shared_rank(Bq, (int)threadIdx.x)[rank] = pb_cta;
+    cluster.sync();
+    float2 bq = Bq[0];
+    for (int k = 1; k < C; ++k) bq = df_add(bq, Bq[k]);
+    const float2 bn = df_sqrt(bq);
     if (rank == 0 && threadIdx.x == 0) {
       w.alpha[(int64_t)b * kLzMax + j] = alpha;
       w.beta[(int64_t)b * kLzMax + j] = bn;
     }
-    if (bn <= tol || j + 1 >= steps) {
+    if (bn.x <= tol || j + 1 >= steps) {
       if (rank == 0 && threadIdx.x == 0) w.mlen[b] = j + 1;
-      return;
+      break;
     }
-    inv_prev = 1.0 / bn;
-    // the next step reads w'' (all rows, complete after the barrier) times
-    // 1 / beta_j
+    scale = df_rcp(bn);
   }
+  cluster.sync();  // no CTA leaves while a peer could still address its shared memory
 }
 
 // Number of eigenvalues of the symmetric tridiagonal (a, e) smaller than x:
 // the sign changes along chi_0 = 1, chi_1, ..., chi_m, chi_k(x) = det(T_k - x I)
 // (Sturm sequence), from the three-term recurrence
 //   chi_k = (a_k - x) chi_{k-1} - e_{k-1}^2 chi_{k-2},
-// which needs no division (float64 division is slow on this part). The pair
-// (chi_{k-1}, chi_k) is rescaled by a power of two when it leaves
-// [2^-400, 2^400], which keeps every sign; an exact zero takes the sign of its
-// predecessor (the usual convention: a zero pivot counts as positive).
-__device__ int sturm_below(const double* a, const double* e2, int m, double x) {
-  // e2[i] = e_i^2 (precomputed). Float64 work per step: one add, one
-  // multiply, one fma; the sign test reads the sign bits, and the rescaling
-  // test runs every 8 steps (a pair grows by at most (|a|+|x|+|e|)^8 between
-  // tests, far inside the 2^+-400 window).
-  int cnt = 0;
-  double c0 = 1.0, c1 = a[0] - x;
-  if (c1 == 0.0) c1 = 0x1p-600;
-  cnt += __double2hiint(c1) < 0;
-  for (int i = 1; i < m; ++i) {
-    double c2 = fma(a[i] - x, c1, -e2[i - 1] * c0);
-    if (c2 == 0.0) c2 = copysign(0x1p-600, c1) * fmax(fabs(c1), 0x1p-400);
-    cnt += (__double2hiint(c2) ^ __double2hiint(c1)) < 0;
-    c0 = c1;
-    c1 = c2;
-    if ((i & 7) == 0) {
-      const int ex = max((__double2hiint(c0) >> 20) & 0x7FF, (__double2hiint(c1) >> 20) & 0x7FF);
-      if (ex > 1023 + 400) { c0 *= 0x1p-400; c1 *= 0x1p-400; }
-      else if (ex < 1023 - 400) { c0 *= 0x1p400; c1 *= 0x1p400; }
-    }
-  }
-  return cnt;
-}
-
-// The same count in float32 (coarse phase of the multisection; float64
-// arithmetic is slow on this part). Rescaling by 2^+-60.
+// which needs no division. The pair (chi_{k-1}, chi_k) is rescaled by a power
+// of two when it leaves [2^-60, 2^60], which keeps every sign; an exact zero
+// takes the sign of its predecessor (the usual convention: a zero pivot
+// counts as positive). Float32 (coarse phase) and double-float versions.
 __device__ int sturm_below_f32(const float* a, const float* e2, int m, float x) {
   int cnt = 0;
   float c0 = 1.f, c1 = a[0] - x;
@@ -234,161 +306,181 @@ __device__ int sturm_below_f32(const float* a, const float* e2, int m, float x) 
   }
   return cnt;
 }
-
-__global__ void lz_finish_kernel(LanczosWork w, int steps, double* d) {
-  const int b = blockIdx.x;
-  (void)steps;
-  const double fro = sqrt(w.fro[b]);
-  const int m = w.mlen[b];
-  if (fro == 0.0 || m <= 0) { d[b] = 1.0; return; }
-  const double* a = w.alpha + (int64_t)b * kLzMax;
-  const double* e = w.beta + (int64_t)b * kLzMax;  // e[0..m-2] off-diagonal; e[m-1] = beta_m
-  if (m == 1) { d[b] = a[0] + e[0]; return; }
-  // Gershgorin interval of T_m
-  double lo = 1e300, hi = -1e300;
-  for (int i = 0; i < m; ++i) {
-    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < m - 1 ? fabs(e[i]) : 0.0);
-    lo = fmin(lo, a[i] - r);
-    hi = fmax(hi, a[i] + r);
+__device__ int sturm_below_df(const float2* a, const float2* e2, int m, float2 x) {
+  int cnt = 0;
+  const float2 nx = df_neg(x);
+  float2 c0 = make_float2(1.f, 0.f), c1 = df_add(a[0], nx);
+  if (c1.x == 0.f) c1 = make_float2(0x1p-100f, 0.f);
+  if (c1.x < 0.f) ++cnt;
+  for (int i = 1; i < m; ++i) {
+    float2 c2 = df_add(df_mul(df_add(a[i], nx), c1), df_neg(df_mul(e2[i - 1], c0)));
+    if (c2.x == 0.f) c2 = make_float2(copysignf(0x1p-100f, c1.x) * fmaxf(fabsf(c1.x), 0x1p-60f), 0.f);
+    if ((c2.x < 0.f) != (c1.x < 0.f)) ++cnt;
+    c0 = c1;
+    c1 = c2;
+    const float mag = fmaxf(fabsf(c0.x), fabsf(c1.x));
+    if (mag > 0x1p60f) { c0 = df_scale(c0, 0x1p-60f); c1 = df_scale(c1, 0x1p-60f); }
+    else if (mag < 0x1p-60f) { c0 = df_scale(c0, 0x1p60f); c1 = df_scale(c1, 0x1p60f); }
   }
-  // Multisection for the largest eigenvalue theta: count(x) >= m <=> x > theta.
-  // Each round the 32 lanes test 32 interior points and keep the sub-interval
-  // where the count crosses m (the interval shrinks 33-fold per round).
-  // Coarse rounds in float32 down to a relative width of 1e-5, widened by a
-  // margin and checked in float64; then float64 rounds.
+  return cnt;
+}
+
+// theta = the largest eigenvalue of T_m (scaled), its unit eigenvector s and
+// d = (theta + beta_m |s_m|) (1 + 1e-12) / scale. One warp per Gram.
+__global__ void lz_finish_kernel(LanczosWork w, double* d) {
+  const int b = blockIdx.x;
   const int lane = threadIdx.x;
-  __shared__ double ad[kLzMax], e2d[kLzMax];
+  const float sc = lz_scale(w.gmax[b]);
+  const float fro = sqrtf((float)w.fro[b]);
+  const int m = w.mlen[b];
+  if (fro == 0.f || m <= 0) { if (lane == 0) d[b] = 1.0; return; }
+  const float2* a = w.alpha + (int64_t)b * kLzMax;
+  const float2* e = w.beta + (int64_t)b * kLzMax;  // e[0..m-2] off-diagonal; e[m-1] = beta_m
+  if (m == 1) {
+    if (lane == 0) d[b] = (((double)a[0].x + (double)a[0].y) + ((double)e[0].x + (double)e[0].y)) / (double)sc;
+    return;
+  }
+  __shared__ float2 ad[kLzMax], e2d[kLzMax];
+  __shared__ float af[kLzMax], e2f[kLzMax];
   for (int i = lane; i < m; i += 32) {
     ad[i] = a[i];
-    e2d[i] = e[i] * e[i];
+    e2d[i] = df_mul(e[i], e[i]);
+    af[i] = a[i].x;
+    e2f[i] = e[i].x * e[i].x;
   }
   __syncwarp();
-  {
-    __shared__ float af[kLzMax], e2f[kLzMax];
-    for (int i = lane; i < m; i += 32) {
-      af[i] = (float)a[i];
-      e2f[i] = (float)(e[i] * e[i]);
-    }
-    __syncwarp();
-    const float scale = (float)fmax(fabs(lo), fabs(hi));
-    float flo = (float)lo, fhi = (float)hi;
-    for (int it = 0; it < 8 && (fhi - flo) > 1e-5f * scale; ++it) {
-      const float wd = (fhi - flo) / 33.f;
-      const float x = flo + wd * (lane + 1);
-      const bool above = (x < fhi) && (x > flo) ? sturm_below_f32(af, e2f, m, x) >= m : (x >= fhi);
-      const unsigned mask = __ballot_sync(0xffffffffu, above);
-      const int first = mask ? __ffs(mask) - 1 : 32;
-      const float nlo = first == 0 ? flo : flo + wd * first;
-      const float nhi = first == 32 ? fhi : flo + wd * (first + 1);
-      if (!(nhi - nlo < fhi - flo)) break;
-      flo = nlo;
-      fhi = nhi;
-    }
-    // widen by 1e-4 of the scale and keep it only if float64 counts confirm it
-    const double mg = 1e-4 * (double)scale + 1e-300;
-    const double tlo = fmax(lo, (double)flo - mg), thi = fmin(hi, (double)fhi + mg);
-    const bool ok_lo = lane == 0 ? sturm_below(ad, e2d, m, tlo) < m : true;
-    const bool ok_hi = lane == 1 ? sturm_below(ad, e2d, m, thi) >= m : true;
-    if (__all_sync(0xffffffffu, ok_lo && ok_hi)) { lo = tlo; hi = thi; }
+  // Gershgorin interval of T_m, widened by a relative 1e-6
+  float lo = 3.4e38f, hi = -3.4e38f;
+  for (int i = lane; i < m; i += 32) {
+    const float r = (i > 0 ? fabsf(e[i - 1].x) : 0.f) + (i < m - 1 ? fabsf(e[i].x) : 0.f);
+    lo = fminf(lo, a[i].x - r);
+    hi = fmaxf(hi, a[i].x + r);
   }
-  for (int it = 0; it < 40; ++it) {
-    const double wd = (hi - lo) / 33.0;
-    const double x = lo + wd * (lane + 1);
-    const bool above = (x < hi) && (x > lo) ? sturm_below(ad, e2d, m, x) >= m : (x >= hi);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  const float scale = fmaxf(fabsf(lo), fabsf(hi));
+  lo -= 1e-6f * scale;
+  hi += 1e-6f * scale;
+  // Multisection for the largest eigenvalue theta: count(x) >= m <=> x > theta.
+  // Each round the 32 lanes test 32 interior points and keep the sub-interval
+  // where the count crosses m (the interval shrinks 33-fold per round):
+  // float32 rounds down to a relative width of 1e-5, the bracket widened and
+  // checked in double-float, then double-float rounds.
+  float flo = lo, fhi = hi;
+  for (int it = 0; it < 12 && (fhi - flo) > 1e-5f * scale; ++it) {
+    const float wd = (fhi - flo) / 33.f;
+    const float x = flo + wd * (lane + 1);
+    const bool above = (x < fhi) && (x > flo) ? sturm_below_f32(af, e2f, m, x) >= m : (x >= fhi);
     const unsigned mask = __ballot_sync(0xffffffffu, above);
-    const int first = mask ? __ffs(mask) - 1 : 32;  // first tested point above theta
-    const double nlo = first == 0 ? lo : lo + wd * first;
-    const double nhi = first == 32 ? hi : lo + wd * (first + 1);
-    if (!(nhi - nlo < hi - lo)) break;  // no further progress in float64
-    lo = nlo;
-    hi = nhi;
+    const int first = mask ? __ffs(mask) - 1 : 32;
+    const float nlo = first == 0 ? flo : flo + wd * first;
+    const float nhi = first == 32 ? fhi : flo + wd * (first + 1);
+    if (!(nhi - nlo < fhi - flo)) break;
+    flo = nlo;
+    fhi = nhi;
+  }
+  float2 dlo = make_float2(lo, 0.f), dhi = make_float2(hi, 0.f);
+  {
+    const float mg = 1e-4f * scale;
+    const float2 tlo = make_float2(fmaxf(lo, flo - mg), 0.f), thi = make_float2(fminf(hi, fhi + mg), 0.f);
+    const bool ok_lo = lane == 0 ? sturm_below_df(ad, e2d, m, tlo) < m : true;
+    const bool ok_hi = lane == 1 ? sturm_below_df(ad, e2d, m, thi) >= m : true;
+    if (__all_sync(0xffffffffu, ok_lo && ok_hi)) { dlo = tlo; dhi = thi; }
+  }
+  for (int it = 0; it < 16; ++it) {
+    const float2 wd = df_scale(df_add(dhi, df_neg(dlo)), 1.f / 32.f);  // 32 equal parts; lanes test 31 points
+    const float2 x = df_add(dlo, df_mul(wd, make_float2((float)(lane + 1), 0.f)));
+    const bool above = lane < 31 ? sturm_below_df(ad, e2d, m, x) >= m : true;
+    const unsigned mask = __ballot_sync(0xffffffffu, above);
+    const int first = __ffs(mask) - 1;  // first tested point above theta (lane 31 stands for dhi)
+    const float2 nlo = first == 0 ? dlo : df_add(dlo, df_mul(wd, make_float2((float)first, 0.f)));
+    const float2 nhi = first == 31 ? dhi : df_add(dlo, df_mul(wd, make_float2((float)(first + 1), 0.f)));
+    const float2 wnew = df_add(nhi, df_neg(nlo)), wold = df_add(dhi, df_neg(dlo));
+    if (!(wnew.x < wold.x) || wnew.x <= 1e-14f * scale) { dlo = nlo; dhi = nhi; break; }
+    dlo = nlo;
+    dhi = nhi;
   }
   if (lane != 0) return;
-  // full float64 resolution: the inverse iteration's shift below needs theta
-  // to ~1e-15 to separate it from near-copies
-  const double theta = hi;  // count(hi) >= m: hi >= theta
+  const float2 theta = dhi;  // count(dhi) >= m: dhi >= theta
   // eigenvector of T_m for theta by inverse iteration with shift slightly
-  // above theta (T - sigma I is then negative definite: no pivoting needed);
-  // one reciprocal per row of the Thomas sweep. The shift must separate theta
-  // from near-copies of it (the recurrence is not reorthogonalised), hence
-  // float64 and a relative gap of 1e-12.
-  const double sigma = theta + 1e-12 * fmax(fabs(theta), fro) + 1e-300;
-  double x[kLzMax], cp[kLzMax], rp[kLzMax];
+  // above theta (T - sigma I is then negative definite: no pivoting needed)
+  const float2 sigma = df_add(theta, make_float2(1e-12f * fmaxf(fabsf(theta.x), fro), 0.f));
+  float2 x[kLzMax], cp[kLzMax], rp[kLzMax];
   {
-    double den = a[0] - sigma;
-    rp[0] = 1.0 / den;
-    cp[0] = e[0] * rp[0];
+    float2 den = df_add(ad[0], df_neg(sigma));
+    rp[0] = df_rcp(den);
+    cp[0] = df_mul(e[0], rp[0]);
     for (int i = 1; i < m; ++i) {
-      den = (a[i] - sigma) - e[i - 1] * cp[i - 1];
-      rp[i] = 1.0 / den;
-      cp[i] = (i < m - 1) ? e[i] * rp[i] : 0.0;
+      den = df_add(df_add(ad[i], df_neg(sigma)), df_neg(df_mul(e[i - 1], cp[i - 1])));
+      rp[i] = df_rcp(den);
+      cp[i] = (i < m - 1) ? df_mul(e[i], rp[i]) : make_float2(0.f, 0.f);
     }
   }
-  for (int i = 0; i < m; ++i) x[i] = 1.0;
+  for (int i = 0; i < m; ++i) x[i] = make_float2(1.f, 0.f);
   for (int rep = 0; rep < 2; ++rep) {
-    // forward: dp_i = (x_i - e_{i-1} dp_{i-1}) / den_i, kept in x
-    x[0] = x[0] * rp[0];
-    for (int i = 1; i < m; ++i) x[i] = (x[i] - e[i - 1] * x[i - 1]) * rp[i];
-    for (int i = m - 2; i >= 0; --i) x[i] = x[i] - cp[i] * x[i + 1];
-    double nrm = 0.0;
-    for (int i = 0; i < m; ++i) nrm = fma(x[i], x[i], nrm);
-    const double inv = 1.0 / sqrt(nrm);
-    for (int i = 0; i < m; ++i) x[i] *= inv;
+    x[0] = df_mul(x[0], rp[0]);
+    for (int i = 1; i < m; ++i) x[i] = df_mul(df_add(x[i], df_neg(df_mul(e[i - 1], x[i - 1]))), rp[i]);
+    for (int i = m - 2; i >= 0; --i) x[i] = df_add(x[i], df_neg(df_mul(cp[i], x[i + 1])));
+    float h = 0.f, l = 0.f;
+    for (int i = 0; i < m; ++i) df_dot_acc(h, l, x[i], x[i]);
+    const float2 inv = df_rcp(df_sqrt(df_norm(h, l)));
+    for (int i = 0; i < m; ++i) x[i] = df_mul(x[i], inv);
   }
-  const double r = fabs(e[m - 1] * x[m - 1]);
-  // theta is resolved to the last bits of float64; the relative 1e-12 keeps
-  // d above lambda_1 whatever the rounding in T_m
-  d[b] = (theta + r) * (1.0 + 1e-12);
+  const float2 r = df_mul(e[m - 1], x[m - 1]);
+  const double th = (double)theta.x + (double)theta.y;
+  const double rr = fabs((double)r.x + (double)r.y);
+  // theta is resolved to about 2^-46 of the spectrum; the relative 1e-12
+  // keeps d above lambda_1 whatever the rounding
+  d[b] = (th + rr) * (1.0 + 1e-12) / (double)sc;
 }
 
 cudaError_t launch_lanczos(const double* G, int64_t p, int64_t ldg, int batch, int64_t strideG,
                            int steps, LanczosWork w, double* d, unsigned* dstatus, cudaStream_t s,
                            int64_t* launches) {
+  (void)dstatus;
   steps = lanczos_steps_eff(steps, p);
-  cudaError_t e = cudaMemsetAsync(w.fro, 0, sizeof(double) * batch, s);
+  cudaError_t e = cudaMemsetAsync(w.gmax, 0, sizeof(float) * batch, s);
   if (e != cudaSuccess) return e;
   {
-    unsigned gx = (unsigned)((p * p + 255) / 256);
-    if (gx > 64) gx = 64;
-    lz_init_kernel<<<dim3(gx, batch), 256, 0, s>>>(G, p, ldg, strideG, w, steps);
+    const unsigned gx = (unsigned)std::min<int64_t>(1024, (p * p + 255) / 256);
+    lz_split_kernel<<<dim3(gx, batch), 256, 0, s>>>(G, p, ldg, strideG, w);
     ++*launches;
   }
-  // one cooperative launch per batch slice whose CTA groups fit on the device
-  int dev = 0, sms = kNumSMsHint, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // shared memory: the vector (p, rounded to even) + the gathered partials
-  const size_t smem = ((size_t)((p + 1) & ~1LL) + (size_t)kLzGather * kLzMax) * sizeof(double);
-  e = cudaFuncSetAttribute(lz_steps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // one cluster per Gram; 16 CTAs when the device can hold such a cluster
+  e = cudaFuncSetAttribute(lz_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lz_steps_kernel, kLzThreads, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int cap = per_sm * sms;
-  e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned) * 2 * batch, s);
-  if (e != cudaSuccess) return e;
-  // about 16 rows per CTA (two per warp), at most kLzGather CTAs per Gram:
-  // fewer CTAs make the group barriers and sums cheaper
-  const int want = (int)std::min<int64_t>(kLzGather, std::max<int64_t>(1, (p + 15) / 16));
-  for (int b0 = 0; b0 < batch;) {
-    const int nb = std::min(batch - b0, cap);
-    const int GC = std::max(1, std::min(want, std::min(sms, cap) / nb));
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(nb * GC));
-    cfg.blockDim = dim3(kLzThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident, or no launch
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, lz_steps_kernel, G, p, ldg, strideG, steps, w, GC, b0, dstatus);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kLzThreads);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int C = lanczos_cluster(p);
+  LzPlan L{};
+  for (;;) {
+    L = lanczos_plan(p, steps, C);
+    attr[0].val.clusterDim.x = (unsigned)C;
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.dynamicSmemBytes = L.smem;
+    e = cudaFuncSetAttribute(lz_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     if (e != cudaSuccess) return e;
-    ++*launches;
-    b0 += nb;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, lz_cluster_kernel, &cfg) == cudaSuccess && nclusters > 0) break;
+    cudaGetLastError();
+    if (C == 1) return cudaErrorInvalidConfiguration;
+    C /= 2;
   }
-  lz_finish_kernel<<<batch, 32, 0, s>>>(w, steps, d);
+  cfg.gridDim = dim3((unsigned)(batch * C));
+  e = cudaLaunchKernelEx(&cfg, lz_cluster_kernel, p, steps, w, L);
+  if (e != cudaSuccess) return e;
+  ++*launches;
+  lz_finish_kernel<<<batch, 32, 0, s>>>(w, d);
   ++*launches;
   return cudaGetLastError();
 }

@@ -155,17 +155,55 @@ __device__ __forceinline__ bool group_barrier(unsigned* bar, unsigned nctas, uns
 #endif
 
 struct LanczosWork {
-  double* V;       // [batch][steps + 3][p]: basis v_0 .. v_steps, w by step parity
-  double* alpha;   // [batch][steps]
-  double* beta;    // [batch][steps]
-  double* fro;     // [batch]
+  double* V;       // [batch][steps + 3][p]: basis rows (double-float pairs) when they stay out of shared memory
+  float2* alpha;   // [batch][kLzMax] double-float, of s_b G_b
+  float2* beta;    // [batch][kLzMax]
+  double* fro;     // [batch] ||s_b G_b||_F^2
+  float* gmax;     // [batch] max |G_b| (sets the power-of-two scaling s_b)
   int32_t* mlen;   // [batch] steps taken
-  unsigned* bar;   // [batch][2] barrier words of each Gram's CTA group
-  double* part;    // [batch][kLzGroupMax][kLzPartStride] per-CTA partial sums
+  float2* Gs;      // [batch][p][p] (hi, lo) float32 copy of G_b
 };
-constexpr int kLzGroupMax = 256;  // CTAs serving one Gram at most
 constexpr int kLzMax = 128;       // longest recurrence kept per Gram
-constexpr int kLzPartStride = 2 * kLzMax + 1;
+constexpr int kLzThreads = 256;
+constexpr size_t kLzSmemMax = 230400;  // dynamic shared memory per CTA (227 KB less room for static arrays)
+
+// Cluster layout of the Lanczos kernel for a Gram of order p: C CTAs own
+// `per` rows each; byte offsets of its shared-memory arrays; whether the
+// basis rows (vsm) and the (hi, lo) rows of G (gsm) fit in shared memory.
+struct LzPlan {
+  int C;
+  int64_t per, vstride;
+  bool vsm, gsm;
+  size_t off_X, off_P1, off_P2, off_B, off_W, off_V, off_G, smem;
+};
+inline LzPlan lanczos_plan(int64_t p, int steps, int C) {
+  LzPlan L{};
+  L.C = C;
+  L.per = (p + C - 1) / C;
+  L.vstride = L.per | 1;  // odd stride: projections of different i hit different banks
+  size_t o = 0;
+  auto take = [&](size_t bytes) { const size_t at = o; o += (bytes + 15) & ~(size_t)15; return at; };
+  // every array holds double-float pairs (8 bytes)
+  L.off_X = take(8 * (size_t)p);
+  L.off_P1 = take(8 * (size_t)C * kLzMax);
+  L.off_P2 = take(8 * (size_t)C * kLzMax);
+  L.off_B = take(8 * 16);
+  L.off_W = take(8 * (size_t)L.per);
+  const size_t vbytes = 8 * (size_t)(steps + 1) * (size_t)L.vstride;
+  L.vsm = o + vbytes <= kLzSmemMax;
+  L.off_V = L.vsm ? take(vbytes) : 0;
+  const size_t gbytes = 8 * (size_t)L.per * (size_t)p;
+  L.gsm = o + gbytes <= kLzSmemMax;
+  L.off_G = L.gsm ? take(gbytes) : 0;
+  L.smem = o;
+  return L;
+}
+// CTAs per Gram: 16 rows per CTA at least, a power of two up to 16.
+inline int lanczos_cluster(int64_t p) {
+  int C = 1;
+  while (C < 16 && (int64_t)(2 * C) * 16 <= p) C *= 2;
+  return C;
+}
 // Lanczos steps actually taken for a request of `steps` (0 = 64) at order p.
 inline int lanczos_steps_eff(int steps, int64_t p) {
   if (steps <= 0) steps = 64;

@@ -95,6 +95,8 @@ struct SrvJob {
   // prep-only device buffers
   int32_t *blk_counts = nullptr, *blk_offsets = nullptr, *perm = nullptr;
   double* partial = nullptr;
+  uint16_t *zhi = nullptr, *zlo = nullptr;  // packed bfloat16 copy of Z (TMA-fed Gram)
+  ChunkTable tpc{};                         // its chunk table
   double* G64 = nullptr;
   double *N = nullptr, *cnt = nullptr;
   LanczosWork lw{};
@@ -154,10 +156,10 @@ void plan_job(oem_server* S, SrvJob* J) {
   const oem_job& j = J->spec;
   const int64_t n = j.n, p = j.p;
   const int L = j.nlambda, B = J->B;
+  // the Gram pass takes the TMA-fed kernel (and its packed copy of Z, in the
+  // job's preparation scratch) on the same terms as a direct call, so a
+  // served result equals the direct one
   J->gp = plan_gram(S->ctx, n, p, J->K > 0 ? J->K : 1, J->gram_mode, J->K > 0);
-  // the converting Gram kernel reads X in place: no packed copy of X counts
-  // against the serving budget while jobs prepare
-  J->gp.tma = false;
   const GramPlan& g = J->gp;
   J->q = g.q;
   J->ycols = g.ycols;
@@ -169,7 +171,17 @@ void plan_job(oem_server* S, SrvJob* J) {
     A.add(&J->blk_offsets, (size_t)g.nblk * g.K);
     A.add(&J->perm, (size_t)n);
   }
-  A.add(&J->partial, (size_t)g.max_chunks * g.ntiles * g.T * g.T);
+  A.add(&J->partial, (size_t)(g.tma ? g.pmax_chunks : g.max_chunks) * g.ntiles * g.T * g.T);
+  if (g.tma) {
+    A.add(&J->zhi, (size_t)g.rows_cap * g.qp);
+    if (g.mode == OEM_GRAM_SPLIT_BF16) A.add(&J->zlo, (size_t)g.rows_cap * g.qp);
+    A.add(&J->tpc.row0, (size_t)g.pmax_chunks);
+    A.add(&J->tpc.row1, (size_t)g.pmax_chunks);
+    A.add(&J->tpc.fold, (size_t)g.pmax_chunks);
+    A.add(&J->tpc.count, 1);
+    A.add(&J->tpc.fold_c0, (size_t)g.K + 1);
+    A.add(&J->tpc.fold_off, (size_t)g.K + 1);
+  }
   A.add(&J->G64, (size_t)B * p * p);
   A.add(&J->N, (size_t)B);
   A.add(&J->cnt, (size_t)B);
@@ -248,6 +260,9 @@ int prep_job(oem_server* S, SrvJob* J) {
   b.ct = J->ct;
   b.partial = J->partial;
   b.Zg = J->Zg;
+  b.zhi = J->zhi;
+  b.zlo = J->zlo;
+  b.t.pc = J->tpc;
   if (!r) r = run_gram(ctx, J->gp, b, j.X, j.xtype, j.n, p, j.ldx, j.y, j.fold, J->K > 0, s);
   if (!r) {
     const int Kf = J->K > 0 ? J->K : 1;
