@@ -63,6 +63,21 @@ __device__ __forceinline__ void df_dot_acc(float& h, float& l, float2 x, float2 
   h = s;
 }
 __device__ __forceinline__ float2 df_norm(float h, float l) { return df_two_sum(h, l); }
+// (h, l) += (h2, l2) without renormalising (for reduction trees)
+__device__ __forceinline__ void df_acc_add(float& h, float& l, float h2, float l2) {
+  const float2 s = df_two_sum(h, h2);
+  h = s.x;
+  l += l2 + s.y;
+}
+// (h, l) summed over the lanes of an aligned group of W lanes (xor tree)
+template <int W>
+__device__ __forceinline__ void df_group_sum(float& h, float& l) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+    df_acc_add(h, l, h2, l2);
+  }
+}
 // 1 / x and sqrt(x): float32 estimate, one Newton step in double-float
 __device__ __forceinline__ float2 df_rcp(float2 x) {
   const float r = 1.f / x.x;
@@ -74,9 +89,6 @@ __device__ __forceinline__ float2 df_sqrt(float2 x) {
   const float r = sqrtf(x.x);
   const float2 e = df_add(x, df_neg(df_mul(make_float2(r, 0.f), make_float2(r, 0.f))));
   return df_quick(r, e.x * (0.5f / r));
-}
-__device__ __forceinline__ float2 df_shfl_xor(float2 v, int o) {
-  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
 }
 __device__ __forceinline__ float2 df_from(double x) {
   const float h = __double2float_rn(x);
@@ -113,11 +125,10 @@ __global__ void lz_split_kernel(const double* __restrict__ G, int64_t p, int64_t
 
 // Sum of one double-float per thread of the CTA in a fixed order; every
 // thread returns it.
-__device__ float2 block_sum_df(float2 v, float2* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+__device__ float2 block_sum_df(float vh, float vl, float2* red) {
+  df_group_sum<32>(vh, vl);
   const int wp = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) red[wp] = v;
+  if (l == 0) red[wp] = df_norm(vh, vl);
   __syncthreads();
   if (threadIdx.x == 0) {
     float2 t = red[0];
@@ -185,7 +196,7 @@ __global__ void __launch_bounds__(kLzThreads, 1) lz_cluster_kernel(int64_t p, in
       const float2 g = df_scale(Gr[e], s);
       df_dot_acc(fh, fl, g, g);
     }
-    const float2 f = block_sum_df(df_norm(fh, fl), red);
+    const float2 f = block_sum_df(fh, fl, red);
     if (threadIdx.x < C) cluster.map_shared_rank(Bq, (int)threadIdx.x)[rank] = f;
   }
   {
@@ -206,7 +217,7 @@ __global__ void __launch_bounds__(kLzThreads, 1) lz_cluster_kernel(int64_t p, in
     for (int64_t c = threadIdx.x; c < p; c += kLzThreads) X[c] = df_mul(X[c], scale);
     __syncthreads();
     for (int t = threadIdx.x; t < R; t += kLzThreads) vb[(int64_t)j * vs + t] = X[r0 + t];
-    // ---- w = s G v_j on the own rows (two interleaved sums per lane)
+    // ---- w = s G v_j on the own rows (a warp per row, two interleaved sums per lane)
     for (int t = warp; t < R; t += kLzThreads / 32) {
       const float2* g = Gr + (int64_t)t * p;
       float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
@@ -216,22 +227,25 @@ __global__ void __launch_bounds__(kLzThreads, 1) lz_cluster_kernel(int64_t p, in
         df_dot_acc(h1, l1, g[c + 32], X[c + 32]);
       }
       if (c < p) df_dot_acc(h0, l0, g[c], X[c]);
-      float2 acc = df_add(df_norm(h0, l0), df_norm(h1, l1));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc = df_add(acc, df_shfl_xor(acc, o));
-      if (lane == 0) W[t] = df_scale(acc, s);
+      df_acc_add(h0, l0, h1, l1);
+      df_group_sum<32>(h0, l0);
+      if (lane == 0) W[t] = df_scale(df_norm(h0, l0), s);
     }
     float2 alpha = make_float2(0.f, 0.f);
     const int nv = j + 1;
     for (int pass = 0; pass < 2; ++pass) {
       float2* Pb = pass ? P2 : P1;
       __syncthreads();
-      // partial projections v_i . w over the own rows, into slot `rank` of every CTA
-      for (int i = threadIdx.x; i < nv; i += kLzThreads) {
+      // partial projections v_i . w over the own rows (8 threads per i), into
+      // slot `rank` of every CTA
+      for (int i0 = 0; i0 < nv; i0 += kLzThreads / 8) {
+        const int i = i0 + (int)(threadIdx.x >> 3), sub = (int)(threadIdx.x & 7);
         float h = 0.f, l = 0.f;
-        for (int u = 0; u < R; ++u) df_dot_acc(h, l, vb[(int64_t)i * vs + u], W[u]);
-        const float2 t = df_norm(h, l);
-        for (int k = 0; k < C; ++k) cluster.map_shared_rank(Pb, k)[rank * kLzMax + i] = t;
+        if (i < nv)
+          for (int u = sub; u < R; u += 8) df_dot_acc(h, l, vb[(int64_t)i * vs + u], W[u]);
+        df_group_sum<8>(h, l);
+        if (i < nv && sub < C) cluster.map_shared_rank(Pb, sub)[rank * kLzMax + i] = df_norm(h, l);
+        if (i < nv && C > 8 && sub + 8 < C) cluster.map_shared_rank(Pb, sub + 8)[rank * kLzMax + i] = df_norm(h, l);
       }
       cluster.sync();
       for (int i = threadIdx.x; i < nv; i += kLzThreads) {
@@ -248,17 +262,15 @@ __global__ void __launch_bounds__(kLzThreads, 1) lz_cluster_kernel(int64_t p, in
         float h = 0.f, l = 0.f;
         if (t < R)
           for (int i = sub; i < nv; i += 16) df_dot_acc(h, l, cs[i], vb[(int64_t)i * vs + t]);
-        float2 v = df_norm(h, l);
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
-        if (t < R && sub == 0) W[t] = df_add(W[t], df_neg(v));
+        df_group_sum<16>(h, l);
+        if (t < R && sub == 0) W[t] = df_add(W[t], df_neg(df_norm(h, l)));
       }
     }
     __syncthreads();
     // ---- ||w''||^2 partial; w'' rows and the partial into every CTA
     float bh = 0.f, bl = 0.f;
     for (int t = threadIdx.x; t < R; t += kLzThreads) df_dot_acc(bh, bl, W[t], W[t]);
-    const float2 pb_cta = block_sum_df(df_norm(bh, bl), red);
+    const float2 pb_cta = block_sum_df(bh, bl, red);
     for (int e = threadIdx.x; e < C * R; e += kLzThreads) {
       const int k = e / R, t = e % R;
       cluster.map_shared_rank(X, k)[r0 + t] = W[t];

@@ -164,7 +164,7 @@ struct LanczosWork {
   float2* Gs;      // [batch][p][p] (hi, lo) float32 copy of G_b
 };
 constexpr int kLzMax = 128;       // longest recurrence kept per Gram
-constexpr int kLzThreads = 256;
+constexpr int kLzThreads = 512;
 constexpr size_t kLzSmemMax = 230400;  // dynamic shared memory per CTA (227 KB less room for static arrays)
 
 // Cluster layout of the Lanczos kernel for a Gram of order p: C CTAs own
