@@ -40,7 +40,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # moves bytes in proportion to n (scaled to the full n below). Set to None
 # whenever the kernel changes, until it is captured again.
 NCU_DRAM_BYTES = {"oem_iter_kernel": 1.074688e6,
-                  "gram_tma_kernel_per_row": None}
+                  "gram_tma_kernel_per_row": (419.762432e6 + 71.911936e6) / 200_000}
 
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 WORKLOAD = "four_penalties_f32_n1e6_p500"
