@@ -34,6 +34,8 @@ __all__ = [
     "threshold_group_scad", "threshold_sparse_group_lasso",
     "oem_path", "penalty_value", "objective", "kkt_violation",
     "cv_mse", "cv_select", "xval", "group_weights_default",
+    "FitResult", "augmented_sums", "centered_stats", "back_transform", "cv_mse_intercept",
+    "fit", "xval_intercept",
 ]
 
 KINDS = ("lasso", "enet", "mcp", "scad", "grp.lasso", "grp.mcp", "grp.scad", "sgl")
@@ -639,3 +641,138 @@ def xval(X, y, fold, K, pens: Sequence[Penalty], nlambda=100, lambda_min_ratio=1
     i1se = np.array([s[3] for s in sel])
     best = int(np.argmin([cvm[i, imin[i]] for i in range(len(pens))]))
     return CVResult(full, folds, lams, mse, cvm, cvsd, imin, i1se, best, d, G, c)
+
+
+# ---------------------------------------------------------------------------
+# Centring, standardisation and the intercept
+# ---------------------------------------------------------------------------
+# Section 2.1 assumes standardized columns (sum_i x_ij^2 = 1; with the 1/n
+# scaling above: unit second moment), and the package's API follows glmnet's
+# (Section 5, API comparison with glmnet), where an unpenalised intercept and
+# standardisation are options. Reading: with an intercept, X and y are
+# centred by their means over the rows of the fit; with standardisation,
+# column j is divided by sd_j = sqrt(G_c[j, j]) (the population sd of the
+# centred column, or the root second moment without an intercept); penalties
+# apply to the standardized coefficients; a column whose variance is zero
+# (or below 1e-14 of its second moment) keeps scale 1 and drops out (zero
+# coefficient). Coefficients are reported on the original scale:
+# beta_j = beta_std_j / sd_j and beta_0 = ybar - mu^T beta.
+
+def augmented_sums(X: np.ndarray, y: np.ndarray):
+    """Raw sums of Z = [X | y | 1]: X^T X, X^T y, y^T y, X^T 1, y^T 1, n."""
+    Xd = np.asarray(X, dtype=np.float64)
+    yd = np.asarray(y, dtype=np.float64)
+    return Xd.T @ Xd, Xd.T @ yd, float(yd @ yd), Xd.sum(0), float(yd.sum()), Xd.shape[0]
+
+
+def centered_stats(Gr, cr, Nr, s, t, n, intercept: bool = True, standardize: bool = True):
+    """Statistics (G, c, N) of the centred / scaled problem from the raw sums
+    of one row set, and the maps back: (G, c, N, mu, sd, ybar, const).
+
+    G = D (X^T X / n - mu mu^T) D, c = D (X^T y / n - mu ybar),
+    N = y^T y / n - ybar^2, D = diag(1 / sd); mu, ybar = 0 without an intercept.
+    """
+    Gr = np.asarray(Gr, dtype=np.float64)
+    cr = np.asarray(cr, dtype=np.float64)
+    p = cr.size
+    mu = np.asarray(s, dtype=np.float64) / n if intercept else np.zeros(p)
+    ybar = float(t) / n if intercept else 0.0
+    Gc = Gr / n - np.outer(mu, mu)
+    cc = cr / n - mu * ybar
+    Nc = float(Nr) / n - ybar * ybar
+    raw2 = np.diag(Gr) / n
+    var = np.diag(Gc).copy()
+    const = ~(var > 1e-14 * raw2)
+    if standardize:
+        sd = np.where(const, 1.0, np.sqrt(np.where(const, 1.0, var)))
+    else:
+        sd = np.ones(p)
+    keep = (~const).astype(np.float64)
+    G = Gc / np.outer(sd, sd) * np.outer(keep, keep)
+    c = cc / sd * keep
+    return G, c, Nc, mu, sd, ybar, const
+
+
+def back_transform(beta_std, mu, sd, ybar, intercept: bool = True):
+    """Original-scale coefficients (beta, beta_0) of standardized beta_std
+    (any leading shape (..., p))."""
+    b = np.asarray(beta_std, dtype=np.float64) / sd
+    b0 = (ybar - b @ mu) if intercept else np.zeros(b.shape[:-1])
+    return b, b0
+
+
+def cv_mse_intercept(Gk_raw, ck_raw, Nk_raw, sk, tk, nk, beta, beta0):
+    """Held-out MSE of fold k for the model beta_0 + x^T beta from the raw
+    sums of [X_k | y_k | 1]: ||y_k - beta_0 - X_k beta||^2 / n_k
+    = (N_k - 2 beta_0 t_k - 2 beta^T c_k + n_k beta_0^2 + 2 beta_0 beta^T s_k
+       + beta^T G_k beta) / n_k."""
+    b = np.asarray(beta, dtype=np.float64)
+    b0 = np.asarray(beta0, dtype=np.float64)
+    quad = np.einsum("...i,ij,...j->...", b, Gk_raw, b)
+    return (Nk_raw - 2.0 * b0 * tk - 2.0 * b @ ck_raw + nk * b0 * b0
+            + 2.0 * b0 * (b @ sk) + quad) / nk
+
+
+@dataclass
+class FitResult:
+    beta: np.ndarray        # (npen, L, p) original scale
+    beta0: np.ndarray       # (npen, L)
+    lambdas: np.ndarray     # (npen, L)
+    paths: list             # PathResult per penalty (standardized problem)
+    d: float
+    G: np.ndarray           # the standardized G the paths ran on
+    c: np.ndarray
+
+
+def fit(X, y, pens: Sequence[Penalty], intercept: bool = True, standardize: bool = True,
+        nlambda=100, lambda_min_ratio=1e-3, tol=1e-7, max_iter=10_000,
+        lanczos_steps=64) -> FitResult:
+    """oem() with the intercept / standardisation options: raw sums of
+    [X | y | 1], the centred and scaled statistics, d, one lambda grid per
+    penalty from the scaled c, warm-started paths, back to the original
+    scale."""
+    Gr, cr, Nr, s, t, n = augmented_sums(X, y)
+    G, c, N, mu, sd, ybar, const = centered_stats(Gr, cr, Nr, s, t, n, intercept, standardize)
+    d = lanczos_d(G, lanczos_steps)[0]
+    lams = np.array([lambda_grid(lambda_max(c, pen), nlambda, lambda_min_ratio) for pen in pens])
+    paths = [oem_path(G, c, d, pen, lams[i], tol, max_iter) for i, pen in enumerate(pens)]
+    bs = np.stack([pr.beta for pr in paths])
+    beta, beta0 = back_transform(bs, mu, sd, ybar, intercept)
+    return FitResult(beta, beta0, lams, paths, d, G, c)
+
+
+def xval_intercept(X, y, fold, K, pens: Sequence[Penalty], intercept: bool = True,
+                   standardize: bool = True, nlambda=100, lambda_min_ratio=1e-3, tol=1e-7,
+                   max_iter=10_000, lanczos_steps=64):
+    """xval.oem with the intercept / standardisation options: every fit
+    (full data and each leave-fold-out set) centres and scales by its own
+    rows' statistics; held-out MSE by cv_mse_intercept on the raw fold sums.
+    Returns (FitResult of the full data, mse (npen, K, L), cvm, cvsd,
+    idx_min, idx_1se, best_penalty)."""
+    X = np.asarray(X)
+    y = np.asarray(y)
+    sums = [augmented_sums(X[fold == k], y[fold == k]) for k in range(K)]
+    tot = [sum(v[i] for v in sums) for i in range(6)]
+    sets = [tot] + [[tot[i] - sums[k][i] for i in range(6)] for k in range(K)]
+    stats = [centered_stats(*st, intercept, standardize) for st in sets]
+    d = [lanczos_d(sb[0], lanczos_steps)[0] for sb in stats]
+    lams = np.array([lambda_grid(lambda_max(stats[0][1], pen), nlambda, lambda_min_ratio)
+                     for pen in pens])
+    res = []
+    for b in range(K + 1):
+        G, c, N, mu, sd, ybar, const = stats[b]
+        paths = [oem_path(G, c, d[b], pen, lams[i], tol, max_iter) for i, pen in enumerate(pens)]
+        beta, beta0 = back_transform(np.stack([pr.beta for pr in paths]), mu, sd, ybar, intercept)
+        res.append(FitResult(beta, beta0, lams, paths, d[b], G, c))
+    mse = np.zeros((len(pens), K, nlambda))
+    for i in range(len(pens)):
+        for k in range(K):
+            Gk, ck, Nk, sk, tk, nk = sums[k]
+            mse[i, k] = cv_mse_intercept(Gk, ck, Nk, sk, tk, nk, res[k + 1].beta[i], res[k + 1].beta0[i])
+    sel = [cv_select(mse[i]) for i in range(len(pens))]
+    cvm = np.array([s_[0] for s_ in sel])
+    cvsd = np.array([s_[1] for s_ in sel])
+    imin = np.array([s_[2] for s_ in sel])
+    i1se = np.array([s_[3] for s_ in sel])
+    best = int(np.argmin([cvm[i, imin[i]] for i in range(len(pens))]))
+    return res[0], mse, cvm, cvsd, imin, i1se, best
