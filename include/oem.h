@@ -134,6 +134,19 @@ typedef struct oem_options {
                                stream once) and the context keeps the fastest;
                                skipped while the stream is being captured.
                                0: the library's fixed rule */
+  int32_t intercept;        /* oem_fit / oem_cv: 1 = fit an unpenalised
+                               intercept by centring X and y by their means
+                               over the rows of each fit; default 0 */
+  int32_t standardize;      /* oem_fit / oem_cv: 1 = divide column j by its
+                               standard deviation sd_j (population, of the
+                               centred column with an intercept, else the
+                               root second moment) before fitting; penalties
+                               apply to the standardized coefficients, results
+                               are reported on the original scale; a column
+                               with zero variance (or below 1e-14 of its
+                               second moment) gets a zero coefficient.
+                               Section 2.1 assumes standardized columns; the
+                               API follows glmnet's (Section 5). Default 0 */
 } oem_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -236,11 +249,19 @@ int oem_fit_path(oem_ctx* ctx, const double* G, const double* c, int64_t p, doub
 
 /* oem(): Gram pass over X (opt->gram_mode), d, lambda grid and paths, in one
  * call (Section 5.1-5.2: several penalties from one Gram). Outputs as for
- * oem_fit_path, plus d_out (1 float64, device, may be NULL). */
+ * oem_fit_path, plus d_out (1 float64, device, may be NULL; d of the
+ * standardized problem when opt->standardize) and beta0 (npen x nlambda
+ * float64, device, may be NULL: the intercepts, 0 without opt->intercept).
+ * With opt->intercept or opt->standardize the Gram pass also forms the column
+ * sums (a column of ones appended to [X | y], on X and y shifted by the
+ * column means of a sample of rows so that centring loses no precision), and
+ * the paths run on the centred / scaled statistics: beta is then on the
+ * original scale and beta0 = mean(y) - mean(X) beta. A bfloat16 Gram request
+ * with an intercept runs in split mode (the shifted X is not bfloat16). */
 int oem_fit(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p,
             int64_t ldx, const void* y, const oem_penalty* pens, int32_t npen,
             const oem_options* opt, double* beta, double* lambdas_out,
-            int32_t* iters, uint8_t* converged, double* d_out, void* stream);
+            int32_t* iters, uint8_t* converged, double* d_out, double* beta0, void* stream);
 
 /* xval.oem(): K-fold cross validation by per-fold statistics (Section 3).
  * One pass forms every fold's sums; leave-fold-out statistics by
@@ -253,12 +274,17 @@ int oem_fit(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p,
  * ties to the larger lambda; lambda.1se: largest lambda with
  * cvm <= cvm_min + cvsd_min); best_penalty 1 int32 (lowest cvm at its
  * lambda.min). 2 <= K <= 64; every fold must have >= 1 row (OEM_EINVAL after
- * the fold count pass otherwise, reported by oem_sync). */
+ * the fold count pass otherwise, reported by oem_sync). With opt->intercept
+ * / opt->standardize every fit (full data and each leave-fold-out set)
+ * centres and scales by its own rows' statistics, the held-out error is that
+ * of beta_0 + x^T beta, and beta0_full (npen x nlambda float64, device, may
+ * be NULL) receives the full-data intercepts. */
 int oem_cv(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p,
            int64_t ldx, const void* y, const uint8_t* fold, int32_t K,
            const oem_penalty* pens, int32_t npen, const oem_options* opt,
            double* beta_full, double* lambdas_out, double* cvm, double* cvsd,
-           int32_t* idx_min, int32_t* idx_1se, int32_t* best_penalty, void* stream);
+           int32_t* idx_min, int32_t* idx_1se, int32_t* best_penalty, double* beta0_full,
+           void* stream);
 
 /* ------------------------------------------------------------------------
  * Serving: a request loop that admits fit and cross-validation jobs of mixed

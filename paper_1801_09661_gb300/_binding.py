@@ -61,7 +61,7 @@ class oem_options(C.Structure):
                 ("max_iter", C.c_int64), ("lanczos_steps", C.c_int32),
                 ("gram_mode", C.c_int32), ("iter_precision", C.c_int32),
                 ("cluster_ctas", C.c_int32), ("instances_per_task", C.c_int32),
-                ("autotune", C.c_int32)]
+                ("autotune", C.c_int32), ("intercept", C.c_int32), ("standardize", C.c_int32)]
 
 
 class oem_job(C.Structure):
@@ -93,10 +93,10 @@ _sigs = {
     "oem_fit_path": (C.c_int, [_vp, _vp, _vp, _i64, _d, C.POINTER(oem_penalty), _i32,
                                C.POINTER(oem_options), _vp, _vp, _vp, _vp, _vp]),
     "oem_fit": (C.c_int, [_vp, _vp, _i32, _i64, _i64, _i64, _vp, C.POINTER(oem_penalty), _i32,
-                          C.POINTER(oem_options), _vp, _vp, _vp, _vp, _vp, _vp]),
+                          C.POINTER(oem_options), _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "oem_cv": (C.c_int, [_vp, _vp, _i32, _i64, _i64, _i64, _vp, _vp, _i32,
                          C.POINTER(oem_penalty), _i32, C.POINTER(oem_options), _vp, _vp, _vp,
-                         _vp, _vp, _vp, _vp, _vp]),
+                         _vp, _vp, _vp, _vp, _vp, _vp]),
     "oem_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_size_t, _i32, _i64]),
     "oem_server_submit": (C.c_int, [_vp, C.POINTER(oem_job), C.POINTER(C.c_int64)]),
     "oem_server_poll": (C.c_int, [_vp, _i64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
@@ -171,7 +171,7 @@ class _PenArray:
 
 def make_options(nlambda=100, lambda_min_ratio=1e-3, lambdas=None, tol=1e-7, max_iter=10000,
                  lanczos_steps=64, gram_mode="auto", iter_precision="f32", cluster_ctas=0,
-                 instances_per_task=0, autotune=True):
+                 instances_per_task=0, autotune=True, intercept=False, standardize=False):
     o = oem_options()
     lib.oem_options_default(C.byref(o))
     o.nlambda = int(nlambda)
@@ -188,6 +188,8 @@ def make_options(nlambda=100, lambda_min_ratio=1e-3, lambdas=None, tol=1e-7, max
     o.cluster_ctas = int(cluster_ctas)
     o.instances_per_task = int(instances_per_task)
     o.autotune = 1 if autotune else 0
+    o.intercept = 1 if intercept else 0
+    o.standardize = 1 if standardize else 0
     o._keep = keep
     return o
 
@@ -340,6 +342,8 @@ def oem_fit_path(ctx: Context, G, c, pens: Sequence[Penalty], d: float = 0.0, st
 
 
 def oem_fit(ctx: Context, X, y, pens: Sequence[Penalty], stream=None, out=None, **opts):
+    """oem_fit; returns (beta, lambdas, iters, converged, d), and the
+    intercepts beta0 as a sixth element when intercept or standardize is set."""
     import torch
     n, p = X.shape
     o = make_options(**opts)
@@ -349,9 +353,13 @@ def oem_fit(ctx: Context, X, y, pens: Sequence[Penalty], stream=None, out=None, 
         d = torch.empty(1, dtype=torch.float64, device=X.device)
     else:
         beta, lam, its, conv, d = out
+    centred = bool(o.intercept or o.standardize)
+    beta0 = torch.empty((P.n, o.nlambda), dtype=torch.float64, device=X.device) if centred else None
     ctx.check(lib.oem_fit(ctx.h, _ptr(X), _xtype(X), n, p, X.stride(0), _ptr(y), P.arr, P.n,
                           C.byref(o), _ptr(beta), _ptr(lam), _ptr(its), _ptr(conv), _ptr(d),
-                          _stream(stream)))
+                          _ptr(beta0), _stream(stream)))
+    if centred:
+        return beta, lam, its, conv, d, beta0
     return beta, lam, its, conv, d
 
 
@@ -369,11 +377,12 @@ def oem_cv(ctx: Context, X, y, fold, K, pens: Sequence[Penalty], stream=None, **
     imin = torch.empty(P.n, dtype=torch.int32, device=dev)
     i1se = torch.empty(P.n, dtype=torch.int32, device=dev)
     best = torch.empty(1, dtype=torch.int32, device=dev)
+    beta0 = torch.empty((P.n, L), dtype=torch.float64, device=dev)
     ctx.check(lib.oem_cv(ctx.h, _ptr(X), _xtype(X), n, p, X.stride(0), _ptr(y), _ptr(fold), int(K),
                          P.arr, P.n, C.byref(o), _ptr(beta), _ptr(lam), _ptr(cvm), _ptr(cvsd),
-                         _ptr(imin), _ptr(i1se), _ptr(best), _stream(stream)))
-    return {"beta": beta, "lambdas": lam, "cvm": cvm, "cvsd": cvsd, "idx_min": imin,
-            "idx_1se": i1se, "best_penalty": best}
+                         _ptr(imin), _ptr(i1se), _ptr(best), _ptr(beta0), _stream(stream)))
+    return {"beta": beta, "beta0": beta0, "lambdas": lam, "cvm": cvm, "cvsd": cvsd,
+            "idx_min": imin, "idx_1se": i1se, "best_penalty": best}
 
 
 class Server:

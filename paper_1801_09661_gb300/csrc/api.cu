@@ -247,7 +247,7 @@ int oem_fit_path(oem_ctx* ctx, const double* G, const double* c, int64_t p, doub
 int oem_fit(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, int64_t ldx,
             const void* y, const oem_penalty* pens, int32_t npen, const oem_options* opt,
             double* beta, double* lambdas_out, int32_t* iters, uint8_t* converged, double* d_out,
-            void* stream) {
+            double* beta0, void* stream) {
   if (!ctx) return OEM_EINVAL;
   int r = check_x(ctx, X, xtype, n, p, ldx, y);
   if (r) return r;
@@ -263,13 +263,15 @@ int oem_fit(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, in
   const int ldg32 = (int)((p + 3) & ~3LL);
   IterPlan I;
   if ((r = plan_iter(ctx, p, 1, P, opt, I))) return r;
-  GramPlan g = plan_gram(ctx, n, p, 1, m, false);
+  const bool centre = opt->intercept || opt->standardize;
+  GramPlan g = plan_gram(ctx, n, p, 1, m, false, opt->intercept != 0);
   GramBufs b;
-  double *G64 = nullptr, *c = nullptr, *N = nullptr, *cnt = nullptr, *dd = nullptr;
+  double *G64 = nullptr, *c = nullptr, *N = nullptr, *cnt = nullptr, *dd = nullptr, *cen = nullptr;
   float* G32 = nullptr;
   LanczosWork w{};
   Arena A;
   gram_request(A, g, n, b);
+  if (centre) A.add(&cen, (size_t)(2 * p + 1));
   A.add(&G64, (size_t)p * p);
   if (opt->iter_precision == OEM_ITER_F32) A.add(&G32, (size_t)p * ldg32);
   A.add(&c, (size_t)p);
@@ -281,18 +283,34 @@ int oem_fit(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, in
   iter_request(A, p, 1, I);
   if ((r = arena_commit(ctx, A, s))) return r;
   if ((r = run_gram(ctx, g, b, X, xtype, n, p, ldx, y, nullptr, false, s))) return r;
+  CentreArgs ce;
+  if (centre) {
+    ce.ocol = opt->intercept ? (int32_t)p + g.ycols : -1;
+    ce.intercept = opt->intercept;
+    ce.standardize = opt->standardize;
+    ce.cen = cen;
+  }
   LAUNCH(OEM_PROF_ASSEMBLE, launch_assemble(b.Zg, 1, g.q, (int)p, g.ycols, b.ct.fold_off, 0, G64, G32, ldg32, c, N,
-                         cnt, s));
+                         cnt, s, ce));
   cudaError_t e = lanczos_prof(ctx, s, G64, p, p, 1, p * p, opt->lanczos_steps, w, dd, s, &ctx->launches);
   if (e != cudaSuccess) return fail(ctx, OEM_ECUDA, "Lanczos launch failed: %s", cudaGetErrorString(e));
   if (d_out) CU(cudaMemcpyAsync(d_out, dd, sizeof(double), cudaMemcpyDeviceToDevice, s));
-  return fit_tail(ctx, p, 1, G64, G32, ldg32, c, dd, P, I, opt, lambdas_out, beta, iters, converged, s);
+  if ((r = fit_tail(ctx, p, 1, G64, G32, ldg32, c, dd, P, I, opt, lambdas_out, beta, iters, converged, s)))
+    return r;
+  if (centre) {
+    LAUNCH(OEM_PROF_COPY, launch_unstandardize(beta, 1, P.npen, opt->nlambda, (int)p, cen, b.shift,
+                                               opt->intercept, nullptr, beta0, s));
+  } else if (beta0) {
+    CU(cudaMemsetAsync(beta0, 0, sizeof(double) * P.npen * opt->nlambda, s));
+  }
+  return OEM_OK;
 }
 
 int oem_cv(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, int64_t ldx,
            const void* y, const uint8_t* fold, int32_t K, const oem_penalty* pens, int32_t npen,
            const oem_options* opt, double* beta_full, double* lambdas_out, double* cvm,
-           double* cvsd, int32_t* idx_min, int32_t* idx_1se, int32_t* best_penalty, void* stream) {
+           double* cvsd, int32_t* idx_min, int32_t* idx_1se, int32_t* best_penalty, double* beta0_full,
+           void* stream) {
   if (!ctx) return OEM_EINVAL;
   int r = check_x(ctx, X, xtype, n, p, ldx, y);
   if (r) return r;
@@ -312,10 +330,11 @@ int oem_cv(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, int
   const int L = opt->nlambda;
   IterPlan I;
   if ((r = plan_iter(ctx, p, B, P, opt, I))) return r;
-  GramPlan g = plan_gram(ctx, n, p, K, m, true);
+  const bool centre = opt->intercept || opt->standardize;
+  GramPlan g = plan_gram(ctx, n, p, K, m, true, opt->intercept != 0);
   GramBufs b;
   double *G64 = nullptr, *c = nullptr, *N = nullptr, *cnt = nullptr, *dd = nullptr;
-  double *beta_all = nullptr, *mse = nullptr;
+  double *beta_all = nullptr, *mse = nullptr, *cen = nullptr, *bprime = nullptr;
   int32_t* it_all = nullptr;
   uint8_t* cv_all = nullptr;
   float* G32 = nullptr;
@@ -333,19 +352,35 @@ int oem_cv(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, int
   A.add(&it_all, (size_t)B * npen * L);
   A.add(&cv_all, (size_t)B * npen * L);
   A.add(&mse, (size_t)npen * K * L);
+  if (centre) {
+    A.add(&cen, (size_t)B * (2 * p + 1));
+    A.add(&bprime, (size_t)B * npen * L);
+  }
   pens_request(A, P);
   iter_request(A, p, B, I);
   if ((r = arena_commit(ctx, A, s))) return r;
   if ((r = run_gram(ctx, g, b, X, xtype, n, p, ldx, y, fold, true, s))) return r;
+  CentreArgs ce;
+  if (centre) {
+    ce.ocol = opt->intercept ? (int32_t)p + g.ycols : -1;
+    ce.intercept = opt->intercept;
+    ce.standardize = opt->standardize;
+    ce.cen = cen;
+  }
   LAUNCH(OEM_PROF_ASSEMBLE, launch_assemble(b.Zg, K, g.q, (int)p, g.ycols, b.ct.fold_off, 1, G64, G32, ldg32, c, N,
-                         cnt, s));
+                         cnt, s, ce));
   cudaError_t e = lanczos_prof(ctx, s, G64, p, p, B, p * p, opt->lanczos_steps, w, dd, s, &ctx->launches);
   if (e != cudaSuccess) return fail(ctx, OEM_ECUDA, "Lanczos launch failed: %s", cudaGetErrorString(e));
   if ((r = fit_tail(ctx, p, B, G64, G32, ldg32, c, dd, P, I, opt, lambdas_out, beta_all, it_all,
                     cv_all, s)))
     return r;
+  if (centre)
+    LAUNCH(OEM_PROF_COPY, launch_unstandardize(beta_all, B, npen, L, (int)p, cen, b.shift, opt->intercept,
+                                               bprime, beta0_full, s));
+  else if (beta0_full)
+    CU(cudaMemsetAsync(beta0_full, 0, sizeof(double) * npen * L, s));
   LAUNCH(OEM_PROF_CV, launch_cv_score(b.Zg, K, g.q, (int)p, g.ycols, b.ct.fold_off, beta_all, npen, L, mse, cvm,
-                         cvsd, idx_min, idx_1se, best_penalty, s));
+                         cvsd, idx_min, idx_1se, best_penalty, s, ce.ocol, bprime));
   LAUNCH(OEM_PROF_COPY, launch_copy_paths(beta_all, it_all, cv_all, npen, L, (int)p, beta_full, nullptr, nullptr,
                            ctx->dstatus, s));
   return OEM_OK;

@@ -4,6 +4,8 @@
 // paper's identity X_{-k}^T X_{-k} = sum_{c != k} X_c^T X_c.
 #include "oem_internal.cuh"
 
+#include <cuda_bf16.h>
+
 namespace oem {
 
 __global__ void gram_reduce_kernel(GramArgs a, int K, double* __restrict__ Zg) {
@@ -75,23 +77,82 @@ cudaError_t launch_extract_folds(const double* Zg, int K, int q, int p, int ycol
   return cudaGetLastError();
 }
 
-// b = 0: full data / n; b = k+1: (sum - fold k) / (n - n_k).
+// Sum over the folds of one entry of the fold Grams of Z, less fold b-1
+// (b > 0: the leave-fold-out set).
+__device__ __forceinline__ double fold_sum(const double* Zg, int K, int64_t qq, int b, int64_t o) {
+  double s = 0.0;
+  for (int k = 0; k < K; ++k) s += Zg[k * qq + o];
+  if (b > 0) s -= Zg[(b - 1) * qq + o];
+  return s;
+}
+__device__ __forceinline__ double fold_sum_c(const double* Zg, int K, int64_t qq, int b, int q, int p,
+                                             int ycols, int i) {
+  double s = 0.0;
+  for (int k = 0; k < K; ++k) s += zc(Zg + k * qq, q, p, ycols, i);
+  if (b > 0) s -= zc(Zg + (b - 1) * qq, q, p, ycols, i);
+  return s;
+}
+__device__ __forceinline__ double fold_sum_n(const double* Zg, int K, int64_t qq, int b, int q, int p,
+                                             int ycols) {
+  double s = 0.0;
+  for (int k = 0; k < K; ++k) s += zn(Zg + k * qq, q, p, ycols);
+  if (b > 0) s -= zn(Zg + (b - 1) * qq, q, p, ycols);
+  return s;
+}
+
+// Centring and scale of column i of fit b (from the raw sums of the shifted
+// Z): mean mu_i (0 without an intercept), variance var_i, sd_i and whether
+// the column is constant (variance zero or below 1e-14 of its second moment;
+// it then keeps scale 1 and drops out).
+struct ColStat {
+  double mu, sd;
+  bool konst;
+};
+__device__ __forceinline__ ColStat col_stat(const double* Zg, int K, int64_t qq, int b, int q, int i,
+                                            double inv, const CentreArgs& ce) {
+  ColStat r;
+  const double sxx = fold_sum(Zg, K, qq, b, (int64_t)i * q + i) * inv;
+  r.mu = ce.intercept ? fold_sum(Zg, K, qq, b, (int64_t)i * q + ce.ocol) * inv : 0.0;
+  const double var = sxx - r.mu * r.mu;
+  r.konst = !(var > 1e-14 * sxx);
+  r.sd = (ce.standardize && !r.konst) ? sqrt(var) : 1.0;
+  return r;
+}
+
+// b = 0: full data / n; b = k+1: (sum - fold k) / (n - n_k). With centring
+// (Section 2.1's standardized design; the intercept / standardize options):
+// G = D (S_xx / n_b - mu mu^T) D, c = D (S_xy / n_b - mu ybar),
+// N = S_yy / n_b - ybar^2, D = diag(1 / sd), constant columns zeroed; the
+// means, scales and ybar go to ce.cen.
 __global__ void assemble_kernel(const double* __restrict__ Zg, int K, int q, int p, int ycols,
                                 const int64_t* __restrict__ fold_off, int B, double* G64,
-                                float* G32, int ldg32, double* c, double* N, double* cnt) {
+                                float* G32, int ldg32, double* c, double* N, double* cnt,
+                                CentreArgs ce) {
   const int b = blockIdx.y;
   const int64_t n = fold_off[K] - fold_off[0];
   const int64_t nb = (b == 0) ? n : n - (fold_off[b] - fold_off[b - 1]);
   const double inv = nb > 0 ? 1.0 / (double)nb : 0.0;
   const int64_t pp = (int64_t)p * p, qq = (int64_t)q * q;
+  const bool centre = ce.intercept || ce.standardize;
+  double ybar = 0.0;
+  if (ce.intercept) {
+    double t = 0.0;
+    for (int s2 = 0; s2 < ycols; ++s2) t += fold_sum(Zg, K, qq, b, (int64_t)(p + s2) * q + ce.ocol);
+    ybar = t * inv;
+  }
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < pp;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / p), j = (int)(e % p);
     const int64_t o = (int64_t)i * q + j;
-    double s = 0.0;
-    for (int k = 0; k < K; ++k) s += Zg[k * qq + o];
-    if (b > 0) s -= Zg[(b - 1) * qq + o];
-    const double v = s * inv;
+    double v;
+    if (!centre) {
+      v = fold_sum(Zg, K, qq, b, o) * inv;
+    } else {
+      const ColStat si = col_stat(Zg, K, qq, b, q, i, inv, ce);
+      const ColStat sj = (i == j) ? si : col_stat(Zg, K, qq, b, q, j, inv, ce);
+      v = (si.konst || sj.konst) ? 0.0
+                                 : (fold_sum(Zg, K, qq, b, o) * inv - si.mu * sj.mu) / (si.sd * sj.sd);
+    }
     if (G64) G64[b * pp + e] = v;
     if (G32) {
       float* row = G32 + (int64_t)b * p * ldg32 + (int64_t)i * ldg32;
@@ -100,30 +161,128 @@ __global__ void assemble_kernel(const double* __restrict__ Zg, int K, int q, int
         for (int jj = p; jj < ldg32; ++jj) row[jj] = 0.f;
     }
     if (j == 0) {
-      double sc = 0.0;
-      for (int k = 0; k < K; ++k) sc += zc(Zg + k * qq, q, p, ycols, i);
-      if (b > 0) sc -= zc(Zg + (b - 1) * qq, q, p, ycols, i);
-      c[(int64_t)b * p + i] = sc * inv;
+      const double sc = fold_sum_c(Zg, K, qq, b, q, p, ycols, i) * inv;
+      if (!centre) {
+        c[(int64_t)b * p + i] = sc;
+      } else {
+        const ColStat si = col_stat(Zg, K, qq, b, q, i, inv, ce);
+        c[(int64_t)b * p + i] = si.konst ? 0.0 : (sc - si.mu * ybar) / si.sd;
+        double* cb = ce.cen + (int64_t)b * (2 * p + 1);
+        cb[i] = si.mu;
+        cb[p + i] = si.sd;
+      }
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    double sn = 0.0;
-    for (int k = 0; k < K; ++k) sn += zn(Zg + k * qq, q, p, ycols);
-    if (b > 0) sn -= zn(Zg + (b - 1) * qq, q, p, ycols);
-    N[b] = sn * inv;
+    N[b] = fold_sum_n(Zg, K, qq, b, q, p, ycols) * inv - ybar * ybar;
     cnt[b] = (double)nb;
+    if (centre) ce.cen[(int64_t)b * (2 * p + 1) + 2 * p] = ybar;
   }
 }
 
 cudaError_t launch_assemble(const double* Zg, int K, int q, int p, int ycols,
                             const int64_t* fold_off, int with_leave_out, double* G64, float* G32,
-                            int ldg32, double* c, double* N, double* cnt, cudaStream_t s) {
+                            int ldg32, double* c, double* N, double* cnt, cudaStream_t s,
+                            const CentreArgs& ce) {
   const int B = with_leave_out ? K + 1 : 1;
   int64_t pp = (int64_t)p * p;
   unsigned gx = (unsigned)((pp + 255) / 256);
   if (gx > 2048) gx = 2048;
   assemble_kernel<<<dim3(gx, B), 256, 0, s>>>(Zg, K, q, p, ycols, fold_off, B, G64, G32, ldg32,
-                                              c, N, cnt);
+                                              c, N, cnt, ce);
+  return cudaGetLastError();
+}
+
+// Column shifts: lane = column within a group of 32, warp = a stride of the
+// sampled rows; float32 sums, min and max per column. A column whose sampled
+// values are all equal gets that value exactly (its shifted copy is zero).
+__global__ void col_shift_kernel(const void* __restrict__ X, int32_t xtype, int64_t n, int64_t p,
+                                 int64_t ldx, const void* __restrict__ y, float* shift) {
+  __shared__ float ssum[8][33], smin[8][33], smax[8][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t col = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t S = n < 8192 ? n : 8192;
+  float sum = 0.f, mn = 3.4e38f, mx = -3.4e38f;
+  if (col <= p) {
+    for (int64_t i = warp; i < S; i += 8) {
+      const int64_t row = (S == n) ? i : (i * n) / S;
+      float v;
+      if (col < p) {
+        const int64_t o = row * ldx + col;
+        v = xtype == OEM_F64 ? (float)((const double*)X)[o]
+            : xtype == OEM_F32 ? ((const float*)X)[o]
+                               : __bfloat162float(((const __nv_bfloat16*)X)[o]);
+      } else {
+        v = xtype == OEM_F64 ? (float)((const double*)y)[row] : ((const float*)y)[row];
+      }
+      sum += v;
+      mn = fminf(mn, v);
+      mx = fmaxf(mx, v);
+    }
+  }
+  ssum[warp][lane] = sum;
+  smin[warp][lane] = mn;
+  smax[warp][lane] = mx;
+  __syncthreads();
+  if (warp == 0 && col <= p) {
+    float t = 0.f, a = 3.4e38f, z = -3.4e38f;
+    for (int w = 0; w < 8; ++w) {
+      t += ssum[w][lane];
+      a = fminf(a, smin[w][lane]);
+      z = fmaxf(z, smax[w][lane]);
+    }
+    shift[col] = (a == z) ? a : t / (float)S;
+  }
+}
+
+cudaError_t launch_col_shift(const void* X, int32_t xtype, int64_t n, int64_t p, int64_t ldx,
+                             const void* y, float* shift, cudaStream_t s) {
+  const unsigned gx = (unsigned)((p + 1 + 31) / 32);
+  col_shift_kernel<<<gx, 256, 0, s>>>(X, xtype, n, p, ldx, y, shift);
+  return cudaGetLastError();
+}
+
+// One block per (fit b, penalty, lambda): beta_j /= sd_j; the intercept in
+// the shifted coordinates bprime = ybar - mu^T beta; on the original scale
+// beta0 = bprime + shift_y - shift_x^T beta.
+__global__ void unstandardize_kernel(double* beta_all, int npen, int nlambda, int p,
+                                     const double* __restrict__ cen, const float* __restrict__ shift,
+                                     int intercept, double* bprime, double* beta0) {
+  __shared__ double red[2][8];
+  const int l = blockIdx.x, pen = blockIdx.y, b = blockIdx.z;
+  const double* cb = cen + (int64_t)b * (2 * p + 1);
+  double* beta = beta_all + (((int64_t)b * npen + pen) * nlambda + l) * p;
+  double s1 = 0.0, s2 = 0.0;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    const double v = beta[j] / cb[p + j];
+    beta[j] = v;
+    s1 = fma(cb[j], v, s1);
+    if (shift) s2 = fma((double)shift[j], v, s2);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  if (ln == 0) { red[0][w] = s1; red[1][w] = s2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t1 = 0.0, t2 = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { t1 += red[0][i]; t2 += red[1][i]; }
+    const double bp = intercept ? cb[2 * p] - t1 : 0.0;
+    const int64_t o = ((int64_t)b * npen + pen) * nlambda + l;
+    if (bprime) bprime[o] = bp;
+    if (beta0 && b == 0)
+      beta0[(int64_t)pen * nlambda + l] = intercept ? bp + (shift ? (double)shift[p] : 0.0) - t2 : 0.0;
+  }
+}
+
+cudaError_t launch_unstandardize(double* beta_all, int B, int npen, int nlambda, int p,
+                                 const double* cen, const float* shift, int intercept,
+                                 double* bprime, double* beta0, cudaStream_t s) {
+  unstandardize_kernel<<<dim3(nlambda, npen, B), 256, 0, s>>>(beta_all, npen, nlambda, p, cen, shift,
+                                                              intercept, bprime, beta0);
   return cudaGetLastError();
 }
 

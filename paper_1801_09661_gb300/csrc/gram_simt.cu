@@ -12,18 +12,28 @@ constexpr int kT = 64;      // tile edge
 constexpr int kRS = 16;     // rows staged per step
 constexpr int kF32Block = 256;  // rows summed in float32 before adding to float64
 
+// One element of Z = [X | y | 1]. With a column shift (centring) the
+// difference is taken in float64 and rounded once to A.
 template <typename A>
 __device__ __forceinline__ A zval(const GramArgs& a, int64_t row, int col) {
   if (col < a.p) {
     int64_t o = row * a.ldx + col;
+    if (a.shift) {
+      const double x = a.xtype == OEM_F64   ? ((const double*)a.X)[o]
+                       : a.xtype == OEM_F32 ? (double)((const float*)a.X)[o]
+                                            : (double)__bfloat162float(((const __nv_bfloat16*)a.X)[o]);
+      return (A)(x - (double)a.shift[col]);
+    }
     if (a.xtype == OEM_F64) return (A)((const double*)a.X)[o];
     if (a.xtype == OEM_F32) return (A)((const float*)a.X)[o];
     return (A)__bfloat162float(((const __nv_bfloat16*)a.X)[o]);
   }
   if (col == a.p) {
-    if (a.xtype == OEM_F64) return (A)((const double*)a.y)[row];
-    return (A)((const float*)a.y)[row];
+    const double yv = a.xtype == OEM_F64 ? ((const double*)a.y)[row] : (double)((const float*)a.y)[row];
+    if (a.shift) return (A)(yv - (double)a.shift[a.p]);
+    return (A)yv;
   }
+  if (col == a.p + 1 && a.ocols) return (A)1;
   return (A)0;
 }
 

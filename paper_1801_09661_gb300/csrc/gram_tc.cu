@@ -56,10 +56,17 @@ __device__ __forceinline__ uint32_t off_kmaj_f32(int mn, int kq) {
   return (uint32_t)((mn >> 3) * 1024 + (mn & 7) * 128 + ((kq ^ (mn & 7)) << 4));
 }
 
-// One element of Z = [X | y] (tf32 mode: one y column).
+// Column shift of Z (centring; 0 without a shift vector or past y).
+__device__ __forceinline__ float zshift(const GramArgs& a, int col) {
+  if (!a.shift) return 0.f;
+  return col < a.p ? a.shift[col] : (col == a.p ? a.shift[a.p] : 0.f);
+}
+
+// One element of Z = [X | y | 1] (tf32 mode: one y column), shifted.
 __device__ __forceinline__ float zval_f32(const GramArgs& a, int64_t row, int col) {
-  if (col < a.p) return ((const float*)a.X)[row * a.ldx + col];
-  if (col == a.p) return ((const float*)a.y)[row];
+  if (col < a.p) return ((const float*)a.X)[row * a.ldx + col] - zshift(a, col);
+  if (col == a.p) return ((const float*)a.y)[row] - zshift(a, col);
+  if (col == a.p + a.ycols && a.ocols) return 1.f;
   return 0.f;
 }
 
@@ -91,6 +98,8 @@ __device__ __forceinline__ void load8(const GramArgs& a, int64_t row, int c0, fl
                                : __bfloat162float(((const __nv_bfloat16*)a.X)[row * a.ldx + c]);
     } else if (c - p < a.ycols) {
       x = yp[c - p];
+    } else if (c - p == a.ycols && a.ocols) {
+      x = 1.f;
     }
     v[u] = x;
   }
@@ -407,7 +416,14 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a, int fl
           unsigned char* ph = base + pan * 16384;
           const uint32_t o = off_bf16(g * 8, r);
           uint4 hi, lo;
-          split8(v, hi, lo);
+          if (a.shift) {
+            float m[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) m[i] = row >= 0 ? zshift(a, col + i) : 0.f;
+            split8_shift(v, m, hi, lo);
+          } else {
+            split8(v, hi, lo);
+          }
           *reinterpret_cast<uint4*>(ph + o) = hi;
           if (split) *reinterpret_cast<uint4*>(ph + 8192 + o) = lo;
         }

@@ -370,6 +370,8 @@ struct ZPackArgs {
   int64_t ldx, p;
   const float* y;
   int32_t ycols;        // 1 (split) or 3 (bfloat16 pieces of y)
+  int32_t ocols;        // 1: a column of ones after y (split mode)
+  const float* shift;   // [p + 1] or NULL (split mode): subtracted exactly
   int32_t qp;           // packed columns (multiple of 64)
   const int32_t* perm;  // sorted -> original row, or NULL
   const int64_t* fold_off;  // [K+1] sorted offsets
@@ -396,6 +398,7 @@ __global__ void __launch_bounds__(256) zpack_kernel(ZPackArgs a) {
       row = a.perm ? (int64_t)a.perm[sr] : sr;
     }
     float yp[3] = {0.f, 0.f, 0.f};
+    const float yshift = a.shift ? a.shift[a.p] : 0.f;
     if (row >= 0) {
       const float yv = a.y[row];
       yp[0] = yv;
@@ -434,13 +437,25 @@ __global__ void __launch_bounds__(256) zpack_kernel(ZPackArgs a) {
                                        : __bfloat162float(((const __nv_bfloat16*)a.X)[row * a.ldx + c]);
             } else if (c - a.p < a.ycols) {
               x = yp[c - a.p];
+            } else if (c - a.p == a.ycols && a.ocols) {
+              x = 1.f;
             }
           }
           v[u] = x;
         }
       }
       uint4 hi, lo;
-      tc::split8(v, hi, lo);
+      if (a.shift) {
+        float m[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int c = c0 + u;
+          m[u] = (row < 0) ? 0.f : (c < a.p ? a.shift[c] : (c == a.p ? yshift : 0.f));
+        }
+        tc::split8_shift(v, m, hi, lo);
+      } else {
+        tc::split8(v, hi, lo);
+      }
       *reinterpret_cast<uint4*>(a.zhi + pr * a.qp + c0) = hi;
       if (a.zlo) *reinterpret_cast<uint4*>(a.zlo + pr * a.qp + c0) = lo;
     }
@@ -475,7 +490,7 @@ cudaError_t launch_zpack(const GramArgs& a, int K, const TmaBufs& t, cudaStream_
   if (e != cudaSuccess) return e;
   ZPackArgs z{};
   z.X = a.X; z.xtype = a.xtype; z.ldx = a.ldx; z.p = a.p; z.y = (const float*)a.y;
-  z.ycols = a.ycols; z.qp = t.qp; z.perm = a.perm; z.fold_off = a.ct.fold_off; z.poff = t.pc.fold_off;
+  z.ycols = a.ycols; z.ocols = a.ocols; z.shift = a.shift; z.qp = t.qp; z.perm = a.perm; z.fold_off = a.ct.fold_off; z.poff = t.pc.fold_off;
   z.K = K; z.rows_cap = t.rows_cap;
   z.zhi = (__nv_bfloat16*)t.zhi;
   z.zlo = (__nv_bfloat16*)t.zlo;

@@ -217,6 +217,8 @@ inline bool tc_mode(int32_t mode) {
 // Everything the Gram pass needs in the workspace.
 struct GramPlan {
   int32_t mode, q, ycols, T, nt, ntiles;
+  int32_t ocols = 0;     // column of ones (centring)
+  bool centre = false;
   int64_t chunk_rows, nblk;
   int max_chunks;
   int K;
@@ -228,12 +230,19 @@ struct GramPlan {
   int pmax_chunks = 0;
 };
 
-inline GramPlan plan_gram(oem_ctx* ctx, int64_t n, int64_t p, int K, int32_t mode, bool sorted) {
+// centre: Z = [X | y | 1] on X and y shifted by sampled column means (the
+// intercept option); a bfloat16 request then runs in split mode, since the
+// shifted X is not bfloat16.
+inline GramPlan plan_gram(oem_ctx* ctx, int64_t n, int64_t p, int K, int32_t mode, bool sorted,
+                          bool centre = false) {
   GramPlan g;
+  if (centre && mode == OEM_GRAM_BF16) mode = OEM_GRAM_SPLIT_BF16;
   g.mode = mode;
+  g.centre = centre;
   // bfloat16 mode carries the float32 y as three bfloat16 pieces (exact)
   g.ycols = (mode == OEM_GRAM_BF16) ? 3 : 1;
-  g.q = (int32_t)p + g.ycols;
+  g.ocols = centre ? 1 : 0;
+  g.q = (int32_t)p + g.ycols + g.ocols;
   g.T = tc_mode(mode) ? 128 : 64;
   g.nt = (g.q + g.T - 1) / g.T;
   g.ntiles = g.nt * (g.nt + 1) / 2;
@@ -280,6 +289,7 @@ struct GramBufs {
   double* Zg = nullptr;
   TmaBufs t{};
   uint16_t *zhi = nullptr, *zlo = nullptr;
+  float* shift = nullptr;  // [p + 1] column shifts (centring)
 };
 
 inline void gram_request(Arena& A, const GramPlan& g, int64_t n, GramBufs& b) {
@@ -296,6 +306,7 @@ inline void gram_request(Arena& A, const GramPlan& g, int64_t n, GramBufs& b) {
   A.add(&b.ct.fold_off, (size_t)g.K + 1);
   A.add(&b.partial, (size_t)(g.tma ? g.pmax_chunks : g.max_chunks) * g.ntiles * g.T * g.T);
   A.add(&b.Zg, (size_t)g.K * g.q * g.q);
+  if (g.centre) A.add(&b.shift, (size_t)(g.q - g.ycols - g.ocols) + 1);
   if (g.tma) {
     A.add(&b.zhi, (size_t)g.rows_cap * g.qp);
     if (g.mode == OEM_GRAM_SPLIT_BF16) A.add(&b.zlo, (size_t)g.rows_cap * g.qp);
@@ -324,6 +335,11 @@ inline int run_gram(oem_ctx* ctx, const GramPlan& g, GramBufs& b, const void* X,
   a.X = X; a.xtype = xtype; a.n = n; a.p = p; a.ldx = ldx; a.y = y;
   a.perm = g.sorted ? b.perm : nullptr;
   a.mode = g.mode; a.q = g.q; a.ycols = g.ycols; a.T = g.T; a.ntile1 = g.nt; a.ntiles = g.ntiles;
+  a.ocols = g.ocols;
+  if (g.centre) {
+    LAUNCH(OEM_PROF_CHUNKS, launch_col_shift(X, xtype, n, p, ldx, y, b.shift, s));
+    a.shift = b.shift;
+  }
   a.ct = b.ct; a.max_chunks = g.max_chunks; a.partial = b.partial; a.dstatus = ctx->dstatus;
   if (g.tma) {
     b.t.zhi = b.zhi;
@@ -494,6 +510,10 @@ inline int check_opts(oem_ctx* ctx, const oem_options* o) {
     return fail(ctx, OEM_EINVAL, "instances_per_task=%d not in {0,1,2,4,8}", g);
   if (o->autotune != 0 && o->autotune != 1)
     return fail(ctx, OEM_EINVAL, "autotune=%d not in {0,1}", o->autotune);
+  if (o->intercept != 0 && o->intercept != 1)
+    return fail(ctx, OEM_EINVAL, "intercept=%d not in {0,1}", o->intercept);
+  if (o->standardize != 0 && o->standardize != 1)
+    return fail(ctx, OEM_EINVAL, "standardize=%d not in {0,1}", o->standardize);
   return OEM_OK;
 }
 

@@ -100,37 +100,45 @@ cudaError_t launch_lambda_grid(const double* c, int p, const DevPenalty* pens, i
 
 // mse[pen][k][l] = (N_k - 2 beta^T c_k + beta^T G_k beta) / n_k with the raw
 // fold sums of fold k and beta = the path leaving fold k out (Gram b = k+1).
+// With an intercept (ocol >= 0) the coefficient vector is extended by the
+// intercept bprime on the column of ones of Z (index ocol): the same quadratic
+// form then gives ||y_k - bprime - X_k beta||^2 in the shifted coordinates.
 __global__ void cv_mse_kernel(const double* __restrict__ Zg, int K, int q, int p, int ycols,
                               const int64_t* __restrict__ fold_off,
                               const double* __restrict__ beta_all, int npen, int nlambda,
-                              double* __restrict__ mse) {
+                              double* __restrict__ mse, int ocol, const double* __restrict__ bprime) {
   __shared__ double red[32];
-  __shared__ double bsh[2048];
+  __shared__ double bsh[2049];
   const int l = blockIdx.x, k = blockIdx.y, pen = blockIdx.z;
   const double* Z = Zg + (int64_t)k * q * q;
-  const double* beta =
-      beta_all + ((((int64_t)(k + 1) * npen + pen) * nlambda) + l) * p;
-  const bool cached = p <= 2048;
-  if (cached)
+  const int64_t o = ((int64_t)(k + 1) * npen + pen) * nlambda + l;
+  const double* beta = beta_all + o * p;
+  const int pe = ocol >= 0 ? p + 1 : p;  // coefficients incl. the intercept
+  const bool cached = pe <= 2049;
+  if (cached) {
     for (int i = threadIdx.x; i < p; i += blockDim.x) bsh[i] = beta[i];
+    if (ocol >= 0 && threadIdx.x == 0) bsh[p] = bprime[o];
+  }
   __syncthreads();
-  const double* bv = cached ? bsh : beta;
+  auto coef = [&](int i) { return cached ? bsh[i] : (i < p ? beta[i] : bprime[o]); };
+  auto col = [&](int i) { return i < p ? i : ocol; };
   double s = 0.0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = warp; i < p; i += nw) {
-    const double bi = bv[i];
+  for (int i = warp; i < pe; i += nw) {
+    const double bi = coef(i);
     if (bi == 0.0) continue;  // sparse paths: skip zero rows
+    const int64_t ri = (int64_t)col(i) * q;
     double r = 0.0;
-    for (int j = lane; j < p; j += 32) r = fma(Z[(int64_t)i * q + j], bv[j], r);
+    for (int j = lane; j < pe; j += 32) r = fma(Z[ri + col(j)], coef(j), r);
     s = fma(bi, r, s);
     if (lane == 0) {
       double ci = 0.0;
-      for (int t = 0; t < ycols; ++t) ci += Z[(int64_t)i * q + p + t];
+      for (int t = 0; t < ycols; ++t) ci += Z[ri + p + t];
       s -= 2.0 * bi * ci;  // the linear term, added once per row
     }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  for (int o2 = 16; o2 > 0; o2 >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o2);
   if (lane == 0) red[warp] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -138,7 +146,7 @@ __global__ void cv_mse_kernel(const double* __restrict__ Zg, int K, int q, int p
     for (int w = 0; w < nw; ++w) t += red[w];
     double Nk = 0.0;
     for (int s2 = 0; s2 < ycols; ++s2)
-      for (int t = 0; t < ycols; ++t) Nk += Z[(int64_t)(p + s2) * q + p + t];
+      for (int t2 = 0; t2 < ycols; ++t2) Nk += Z[(int64_t)(p + s2) * q + p + t2];
     const double nk = (double)(fold_off[k + 1] - fold_off[k]);
     mse[((int64_t)pen * K + k) * nlambda + l] = nk > 0 ? (Nk + t) / nk : 0.0;
   }
@@ -190,9 +198,10 @@ __global__ void cv_select_kernel(const double* __restrict__ mse, int K, int npen
 cudaError_t launch_cv_score(const double* Zg, int K, int q, int p, int ycols,
                             const int64_t* fold_off, const double* beta_all, int npen,
                             int nlambda, double* mse, double* cvm, double* cvsd,
-                            int32_t* idx_min, int32_t* idx_1se, int32_t* best, cudaStream_t s) {
+                            int32_t* idx_min, int32_t* idx_1se, int32_t* best, cudaStream_t s,
+                            int ocol, const double* bprime) {
   cv_mse_kernel<<<dim3(nlambda, K, npen), 256, 0, s>>>(Zg, K, q, p, ycols, fold_off, beta_all,
-                                                       npen, nlambda, mse);
+                                                       npen, nlambda, mse, ocol, bprime);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   cv_select_kernel<<<1, 32, 0, s>>>(mse, K, npen, nlambda, cvm, cvsd, idx_min, idx_1se, best);

@@ -45,8 +45,10 @@ struct GramArgs {
   const void* y;
   const int32_t* perm;  // sorted row -> original row (NULL = identity)
   int32_t mode;         // OEM_GRAM_*
-  int32_t q;            // augmented columns
-  int32_t ycols;        // y columns appended (1 or 2)
+  int32_t q;            // augmented columns: p + ycols + ocols
+  int32_t ycols;        // y columns appended (1, or 3 bfloat16 pieces)
+  int32_t ocols;        // 1: a column of ones after the y columns (column sums, n)
+  const float* shift;   // [p + 1] or NULL: subtracted from X's columns and y
   int32_t T;            // tile size
   int32_t ntile1;       // tiles per side
   int32_t ntiles;       // upper-triangular tile count
@@ -106,11 +108,34 @@ cudaError_t launch_extract_folds(const double* Zg, int K, int q, int p, int ycol
                                  double* ck, double* ytyk, int64_t* nk, const int64_t* fold_off,
                                  cudaStream_t s);
 
+// Centring and scaling of the assembled statistics (intercept / standardize
+// options): ocol = column of ones in Z (or -1); cen [B][2p+1] receives the
+// means of the (shifted) X columns, the scales sd and the mean of the
+// (shifted) y of each fit.
+struct CentreArgs {
+  int32_t ocol = -1;
+  int32_t intercept = 0, standardize = 0;
+  double* cen = nullptr;
+};
+
 // Assemble scaled statistics: b = 0 full data, b = k+1 leave fold k out.
 // G64 [B][p][p], G32 [B][p][ldg32] (may be NULL), c [B][p], N [B], cnt [B].
 cudaError_t launch_assemble(const double* Zg, int K, int q, int p, int ycols,
                             const int64_t* fold_off, int with_leave_out, double* G64, float* G32,
-                            int ldg32, double* c, double* N, double* cnt, cudaStream_t s);
+                            int ldg32, double* c, double* N, double* cnt, cudaStream_t s,
+                            const CentreArgs& ce = CentreArgs());
+// Column shifts for centring: shift[j] = the mean of column j over a sample
+// of at most 8,192 rows (exactly the common value when the sample is
+// constant), shift[p] the same for y.
+cudaError_t launch_col_shift(const void* X, int32_t xtype, int64_t n, int64_t p, int64_t ldx,
+                             const void* y, float* shift, cudaStream_t s);
+// Standardized paths back to the original scale: beta_all [B][npen][L][p]
+// divided by sd in place; bprime [B][npen][L] (may be NULL) = the intercept
+// in the shifted coordinates of the Gram pass; beta0 [npen][L] (may be
+// NULL) = the intercept of fit b = 0 on the original scale.
+cudaError_t launch_unstandardize(double* beta_all, int B, int npen, int nlambda, int p,
+                                 const double* cen, const float* shift, int intercept,
+                                 double* bprime, double* beta0, cudaStream_t s);
 
 // Lanczos d for a batch of float64 Grams.
 #ifdef __CUDACC__
@@ -317,10 +342,13 @@ int oem_iter_max_cluster(const IterLaunch& P);
 cudaError_t launch_oem_iter(const IterLaunch& P, cudaStream_t s);
 
 // CV scoring from raw fold Grams of Z and the fold paths.
+// With ocol >= 0 the model has the intercept bprime [B][npen][L] on the
+// column of ones (shifted coordinates).
 cudaError_t launch_cv_score(const double* Zg, int K, int q, int p, int ycols,
                             const int64_t* fold_off, const double* beta_all, int npen,
                             int nlambda, double* mse, double* cvm, double* cvsd,
-                            int32_t* idx_min, int32_t* idx_1se, int32_t* best, cudaStream_t s);
+                            int32_t* idx_min, int32_t* idx_1se, int32_t* best, cudaStream_t s,
+                            int ocol = -1, const double* bprime = nullptr);
 
 // Copy the full-data (b = 0) paths out of the batched buffers.
 cudaError_t launch_copy_paths(const double* beta_all, const int32_t* it_all, const uint8_t* cv_all,

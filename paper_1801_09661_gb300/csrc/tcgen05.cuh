@@ -186,5 +186,28 @@ __device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo
   hi = make_uint4(h[0], h[1], h[2], h[3]);
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
+// The same split of v - m, with the difference taken exactly: TwoSum gives
+// s + e = v - m, hi = bf16(s), lo = bf16((s - hi) + e).
+__device__ __forceinline__ void split8_shift(const float (&v)[8], const float (&m)[8], uint4& hi,
+                                             uint4& lo) {
+  float sv[8], ev[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float a = v[i], b = -m[i];
+    const float s = a + b;
+    const float bb = s - a;
+    sv[i] = s;
+    ev[i] = (a - (s - bb)) + (b - bb);
+  }
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    h[i] = cvt_bf16x2(sv[2 * i], sv[2 * i + 1]);
+    const float h0 = __uint_as_float(h[i] << 16), h1 = __uint_as_float(h[i] & 0xFFFF0000u);
+    l[i] = cvt_bf16x2((sv[2 * i] - h0) + ev[2 * i], (sv[2 * i + 1] - h1) + ev[2 * i + 1]);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
 }  // namespace tc
 }  // namespace oem
