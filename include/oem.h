@@ -180,7 +180,7 @@ int64_t oem_kernel_launches(const oem_ctx* ctx);
 enum {
   OEM_PROF_FOLD_SORT = 0, OEM_PROF_CHUNKS = 1, OEM_PROF_GRAM_SIMT = 2, OEM_PROF_GRAM_TC = 3,
   OEM_PROF_GRAM_REDUCE = 4, OEM_PROF_ASSEMBLE = 5, OEM_PROF_LANCZOS = 6, OEM_PROF_LAMBDA = 7,
-  OEM_PROF_ITER = 8, OEM_PROF_CV = 9, OEM_PROF_COPY = 10, OEM_PROF_NKERNELS = 11
+  OEM_PROF_ITER = 8, OEM_PROF_CV = 9, OEM_PROF_COPY = 10, OEM_PROF_LOGIT = 11, OEM_PROF_NKERNELS = 12
 };
 int oem_profile_enable(oem_ctx* ctx, int enable);
 int oem_profile_get(oem_ctx* ctx, int kernel, double* ms, int64_t* launches);
@@ -285,6 +285,31 @@ int oem_cv(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p,
            double* beta_full, double* lambdas_out, double* cvm, double* cvsd,
            int32_t* idx_min, int32_t* idx_1se, int32_t* best_penalty, double* beta0_full,
            void* stream);
+
+/* Penalised logistic regression (Section 4): minimise
+ *   -(1/n) sum_i { y_i eta_i - log(1 + exp(eta_i)) } + P_lambda(beta),
+ *   eta_i = x_i^T beta (+ beta_0 with opt->intercept, unpenalised),
+ * by the proximal Newton algorithm with the Hessian weights replaced by their
+ * upper bound 1/4: G = Z^T Z / (4n) (Z = [X | 1] with an intercept) comes
+ * from one Gram pass and stays fixed; each outer step makes one pass over X
+ * for the score g = Z^T (y - mu) / n of every penalty's current beta and
+ * solves the surrogate 1/2 b^T G b - (G beta + g)^T b + P_lambda(b) by OEM
+ * iterations warm-started at beta (d >= lambda_1(G) by Lanczos). The outer
+ * loop stops by the inner stopping rule applied to successive outer iterates
+ * (at most 100 steps per lambda). lambda_max and the first warm start are
+ * the null model's (beta = 0, beta_0 = logit(mean y)).
+ * X n x p (float32, bfloat16 or float64; p <= 1023), y n values in {0, 1}
+ * (float32; float64 for float64 X). pens: lasso, elastic net, MCP, SCAD
+ * (npen 1..8). opt->standardize is not supported (OEM_EUNSUPPORTED).
+ * Outputs (device): beta npen x nlambda x p; beta0 npen x nlambda (may be
+ * NULL; 0 without an intercept); lambdas_out npen x nlambda; iters npen x
+ * nlambda (inner OEM iterations summed over the outer steps); converged
+ * npen x nlambda (the outer loop met its stopping rule); d_out (may be NULL).
+ * The host waits for the stream once per outer step. */
+int oem_fit_logistic(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p,
+                     int64_t ldx, const void* y, const oem_penalty* pens, int32_t npen,
+                     const oem_options* opt, double* beta, double* beta0, double* lambdas_out,
+                     int32_t* iters, uint8_t* converged, double* d_out, void* stream);
 
 /* ------------------------------------------------------------------------
  * Serving: a request loop that admits fit and cross-validation jobs of mixed

@@ -44,9 +44,9 @@ MODE = {"fp64": OEM_GRAM_FP64, "fp32": OEM_GRAM_FP32, "tf32": OEM_GRAM_TF32,
 EXPORTED = ["oem_options_default", "oem_create", "oem_destroy", "oem_last_error", "oem_sync",
             "oem_kernel_launches", "oem_profile_enable", "oem_profile_get", "oem_profile_name",
             "oem_gram", "oem_gram_noalloc", "oem_fold_grams", "oem_spectral_d", "oem_fit_path",
-            "oem_fit", "oem_cv", "oem_server_create", "oem_server_submit", "oem_server_poll",
+            "oem_fit", "oem_cv", "oem_fit_logistic", "oem_server_create", "oem_server_submit", "oem_server_poll",
             "oem_server_result", "oem_server_stats", "oem_server_destroy"]
-OEM_PROF_NKERNELS = 11
+OEM_PROF_NKERNELS = 12
 
 
 class oem_penalty(C.Structure):
@@ -97,6 +97,8 @@ _sigs = {
     "oem_cv": (C.c_int, [_vp, _vp, _i32, _i64, _i64, _i64, _vp, _vp, _i32,
                          C.POINTER(oem_penalty), _i32, C.POINTER(oem_options), _vp, _vp, _vp,
                          _vp, _vp, _vp, _vp, _vp, _vp]),
+    "oem_fit_logistic": (C.c_int, [_vp, _vp, _i32, _i64, _i64, _i64, _vp, C.POINTER(oem_penalty), _i32,
+                                   C.POINTER(oem_options), _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "oem_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_size_t, _i32, _i64]),
     "oem_server_submit": (C.c_int, [_vp, C.POINTER(oem_job), C.POINTER(C.c_int64)]),
     "oem_server_poll": (C.c_int, [_vp, _i64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
@@ -383,6 +385,22 @@ def oem_cv(ctx: Context, X, y, fold, K, pens: Sequence[Penalty], stream=None, **
                          _ptr(imin), _ptr(i1se), _ptr(best), _ptr(beta0), _stream(stream)))
     return {"beta": beta, "beta0": beta0, "lambdas": lam, "cvm": cvm, "cvsd": cvsd,
             "idx_min": imin, "idx_1se": i1se, "best_penalty": best}
+
+
+def oem_fit_logistic(ctx: Context, X, y, pens: Sequence[Penalty], stream=None, **opts):
+    """Penalised logistic regression path; returns (beta, beta0, lambdas,
+    iters, converged, d)."""
+    import torch
+    n, p = X.shape
+    o = make_options(**opts)
+    P = _PenArray(pens)
+    beta, lam, its, conv = _path_outputs(P.n, o.nlambda, p, X.device)
+    beta0 = torch.empty((P.n, o.nlambda), dtype=torch.float64, device=X.device)
+    d = torch.empty(1, dtype=torch.float64, device=X.device)
+    ctx.check(lib.oem_fit_logistic(ctx.h, _ptr(X), _xtype(X), n, p, X.stride(0), _ptr(y), P.arr, P.n,
+                                   C.byref(o), _ptr(beta), _ptr(beta0), _ptr(lam), _ptr(its), _ptr(conv),
+                                   _ptr(d), _stream(stream)))
+    return beta, beta0, lam, its, conv, d
 
 
 class Server:

@@ -98,7 +98,8 @@ int oem_profile_get(oem_ctx* ctx, int kernel, double* ms, int64_t* launches) {
 const char* oem_profile_name(int kernel) {
   static const char* names[OEM_PROF_NKERNELS] = {
       "fold_sort", "chunk_table", "gram_simt_kernel", "gram_tc_pass", "gram_reduce_kernel",
-      "assemble", "lanczos", "lambda_grid_kernel", "oem_iter_kernel", "cv_score", "copy_paths"};
+      "assemble", "lanczos", "lambda_grid_kernel", "oem_iter_kernel", "cv_score", "copy_paths",
+      "logistic_outer_step"};
   return (kernel >= 0 && kernel < OEM_PROF_NKERNELS) ? names[kernel] : "unknown";
 }
 
@@ -264,7 +265,7 @@ int oem_fit(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, in
   IterPlan I;
   if ((r = plan_iter(ctx, p, 1, P, opt, I))) return r;
   const bool centre = opt->intercept || opt->standardize;
-  GramPlan g = plan_gram(ctx, n, p, 1, m, false, opt->intercept != 0);
+  GramPlan g = plan_gram(ctx, n, p, 1, m, false, opt->intercept ? kOnesShifted : 0);
   GramBufs b;
   double *G64 = nullptr, *c = nullptr, *N = nullptr, *cnt = nullptr, *dd = nullptr, *cen = nullptr;
   float* G32 = nullptr;
@@ -331,7 +332,7 @@ int oem_cv(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, int
   IterPlan I;
   if ((r = plan_iter(ctx, p, B, P, opt, I))) return r;
   const bool centre = opt->intercept || opt->standardize;
-  GramPlan g = plan_gram(ctx, n, p, K, m, true, opt->intercept != 0);
+  GramPlan g = plan_gram(ctx, n, p, K, m, true, opt->intercept ? kOnesShifted : 0);
   GramBufs b;
   double *G64 = nullptr, *c = nullptr, *N = nullptr, *cnt = nullptr, *dd = nullptr;
   double *beta_all = nullptr, *mse = nullptr, *cen = nullptr, *bprime = nullptr;
@@ -384,6 +385,152 @@ int oem_cv(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, int
   LAUNCH(OEM_PROF_COPY, launch_copy_paths(beta_all, it_all, cv_all, npen, L, (int)p, beta_full, nullptr, nullptr,
                            ctx->dstatus, s));
   return OEM_OK;
+}
+
+int oem_fit_logistic(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, int64_t ldx,
+                     const void* y, const oem_penalty* pens, int32_t npen, const oem_options* opt,
+                     double* beta, double* beta0, double* lambdas_out, int32_t* iters,
+                     uint8_t* converged, double* d_out, void* stream) {
+  if (!ctx) return OEM_EINVAL;
+  int r = check_x(ctx, X, xtype, n, p, ldx, y);
+  if (r) return r;
+  if ((r = check_opts(ctx, opt))) return r;
+  if (!beta || !lambdas_out || !iters || !converged) return fail(ctx, OEM_EINVAL, "NULL pointer argument");
+  if (p > 1023) return fail(ctx, OEM_EINVAL, "logistic regression: p=%lld exceeds 1023", (long long)p);
+  if (opt->standardize) return fail(ctx, OEM_EUNSUPPORTED, "logistic regression: standardize is not supported");
+  if (!pens || npen < 1 || npen > 8) return fail(ctx, OEM_EINVAL, "npen=%d must be in [1,8]", npen);
+  for (int i = 0; i < npen; ++i)
+    if (pens[i].kind > OEM_SCAD)
+      return fail(ctx, OEM_EUNSUPPORTED, "logistic regression: penalty %d is a group penalty", i);
+  int32_t m;
+  if ((r = resolve_mode(ctx, opt->gram_mode, xtype, &m))) return r;
+  if ((r = check_user_lambdas(ctx, opt, npen))) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  CU(cudaSetDevice(ctx->device));
+  const int icpt = opt->intercept ? 1 : 0;
+  const int64_t pq = p + icpt;  // coefficients incl. the unpenalised intercept (last)
+  const int L = opt->nlambda;
+  // penalties on [X | 1]: the user's weights (or 1), weight 0 on the intercept
+  std::vector<std::vector<double>> wext(npen);
+  std::vector<oem_penalty> ext(pens, pens + npen);
+  for (int i = 0; i < npen; ++i) {
+    wext[i].assign((size_t)pq, 1.0);
+    if (pens[i].w) std::copy(pens[i].w, pens[i].w + p, wext[i].begin());
+    if (icpt) wext[i][p] = 0.0;
+    ext[i].w = wext[i].data();
+  }
+  PenPlan P;
+  if ((r = prepare_pens(ctx, ext.data(), npen, pq, P))) return r;
+  oem_options inner = *opt;  // one lambda per inner launch, fixed layout
+  inner.nlambda = 1;
+  inner.lambdas = nullptr;
+  inner.autotune = 0;
+  const int ldg32 = (int)((pq + 3) & ~3LL);
+  IterPlan I;
+  if ((r = plan_iter(ctx, pq, 1, P, &inner, I))) return r;
+  GramPlan g = plan_gram(ctx, n, p, 1, m, false, kOnes);
+  GramBufs b;
+  int sms = ctx->num_sms;
+  // score pass: one CTA per SM, two row chunks of ~80 KB each in shared memory
+  const int grid = sms;
+  const int64_t lds = (p + 3) & ~3LL;
+  int rc = (int)std::min<int64_t>(64, std::max<int64_t>(8, (81920 / (4 * lds)) / 8 * 8));
+  double *G64 = nullptr, *dd = nullptr, *lam = nullptr, *lam_l = nullptr, *bcur = nullptr, *gv = nullptr;
+  double *bnew = nullptr, *st_u = nullptr, *st_beta = nullptr;
+  int32_t *it_new = nullptr, *its_l = nullptr, *flags = nullptr, *st_ctl = nullptr;
+  uint8_t *conv_l = nullptr, *conv_in = nullptr;
+  float* G32 = nullptr;
+  float2* part = nullptr;
+  LanczosWork w{};
+  Arena A;
+  gram_request(A, g, n, b);
+  A.add(&G64, (size_t)pq * pq);
+  if (opt->iter_precision == OEM_ITER_F32) A.add(&G32, (size_t)pq * ldg32);
+  A.add(&dd, 1);
+  lanczos_request(A, w, pq, 1, opt->lanczos_steps);
+  A.add(&lam, (size_t)npen * L);
+  A.add(&lam_l, (size_t)npen);
+  A.add(&bcur, (size_t)npen * pq);
+  A.add(&gv, (size_t)npen * pq);
+  A.add(&bnew, (size_t)npen * pq);
+  A.add(&st_u, (size_t)npen * pq * 2);
+  A.add(&st_beta, (size_t)npen * pq);
+  A.add(&st_ctl, (size_t)40 * npen);
+  A.add(&it_new, (size_t)npen);
+  A.add(&its_l, (size_t)npen);
+  A.add(&flags, (size_t)npen);
+  A.add(&conv_l, (size_t)npen);
+  A.add(&conv_in, (size_t)npen);
+  A.add(&part, (size_t)grid * npen * pq);
+  pens_request(A, P);
+  iter_request(A, pq, 1, I);
+  if ((r = arena_commit(ctx, A, s))) return r;
+  if ((r = pens_upload(ctx, P, s))) return r;
+  // ---- the Gram pass (one pass over [X | y | 1]) and G = Z^T Z / (4n)
+  if ((r = run_gram(ctx, g, b, X, xtype, n, p, ldx, y, nullptr, false, s))) return r;
+  const int ocol = (int)p + g.ycols;
+  LAUNCH(OEM_PROF_ASSEMBLE, launch_logit_gram(b.Zg, g.q, (int)p, ocol, icpt, n, G64, G32, ldg32, s));
+  cudaError_t e = lanczos_prof(ctx, s, G64, pq, pq, 1, pq * pq, opt->lanczos_steps, w, dd, s, &ctx->launches);
+  if (e != cudaSuccess) return fail(ctx, OEM_ECUDA, "Lanczos launch failed: %s", cudaGetErrorString(e));
+  if (d_out) CU(cudaMemcpyAsync(d_out, dd, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  // ---- null model and its score: lambda_max
+  LogitArgs la{};
+  la.X = X; la.xtype = xtype; la.n = n; la.p = p; la.ldx = ldx; la.y = y;
+  la.ytype = xtype == OEM_F64 ? OEM_F64 : OEM_F32;
+  la.beta = bcur; la.ldb = (int32_t)pq; la.intercept = icpt; la.rc = rc; la.part = part; la.g = gv;
+  LAUNCH(OEM_PROF_CHUNKS, launch_logit_null(bcur, npen, (int)pq, (int)pq, icpt, b.Zg, g.q, (int)p, g.ycols, ocol, n, s));
+  LAUNCH(OEM_PROF_LOGIT, launch_logit_grad(la, npen, grid, s));
+  if (opt->lambdas) {
+    CU(cudaMemcpyAsync(lam, opt->lambdas, sizeof(double) * npen * L, cudaMemcpyHostToDevice, s));
+  } else {
+    LAUNCH(OEM_PROF_LAMBDA, launch_lambda_grid(gv, (int)p, P.dpens, npen, L, opt->lambda_min_ratio, lam, s));
+  }
+  // ---- the path: for each lambda, outer (proximal Newton) steps, each an
+  // X pass, the surrogate's resume state, one inner OEM launch and the step
+  constexpr int kMaxOuter = 100;
+  std::vector<IterTask> tasks;
+  int32_t* hflags = nullptr;
+  CU(cudaMallocHost(&hflags, sizeof(int32_t) * npen));
+  int rr = OEM_OK;
+  for (int l = 0; l < L && !rr; ++l) {
+    CU(cudaMemcpy2DAsync(lam_l, sizeof(double), lam + l, sizeof(double) * L, sizeof(double), npen,
+                         cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemsetAsync(flags, 0, sizeof(int32_t) * npen, s));
+    CU(cudaMemsetAsync(its_l, 0, sizeof(int32_t) * npen, s));
+    CU(cudaMemsetAsync(conv_l, 0, npen, s));
+    for (int t = 1; t <= kMaxOuter; ++t) {
+      if (l > 0 || t > 1) LAUNCH(OEM_PROF_LOGIT, launch_logit_grad(la, npen, grid, s));
+      LAUNCH(OEM_PROF_LOGIT, launch_logit_state(gv, bcur, npen, (int)pq, (int)pq, dd, P.dpens, opt->iter_precision,
+                                               st_u, st_beta, st_ctl, 40 * npen, s));
+      if ((rr = launch_iter_layout(ctx, pq, 1, G32, ldg32, G64, gv, dd, lam_l, P, &inner, I, bnew, it_new,
+                                   conv_in, 0, tasks, s, st_u, st_beta, st_ctl)))
+        break;
+      LAUNCH(OEM_PROF_LOGIT, launch_logit_step(bcur, bnew, npen, (int)pq, (int)pq, it_new, its_l, opt->tol, flags,
+                                              t == kMaxOuter ? 1 : 0, conv_l, s));
+      CU(cudaMemcpyAsync(hflags, flags, sizeof(int32_t) * npen, cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      bool all = true;
+      for (int k = 0; k < npen; ++k) all &= hflags[k] != 0;
+      if (all) break;
+    }
+    if (rr) break;
+    // beta[k][l][:p], beta0[k][l], iters, converged
+    CU(cudaMemcpy2DAsync(beta + (size_t)l * p, sizeof(double) * L * p, bcur, sizeof(double) * pq,
+                         sizeof(double) * p, npen, cudaMemcpyDeviceToDevice, s));
+    if (beta0) {
+      if (icpt)
+        CU(cudaMemcpy2DAsync(beta0 + l, sizeof(double) * L, bcur + p, sizeof(double) * pq, sizeof(double), npen,
+                             cudaMemcpyDeviceToDevice, s));
+      else
+        CU(cudaMemset2DAsync(beta0 + l, sizeof(double) * L, 0, sizeof(double), npen, s));
+    }
+    CU(cudaMemcpy2DAsync(iters + l, sizeof(int32_t) * L, its_l, sizeof(int32_t), sizeof(int32_t), npen,
+                         cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpy2DAsync(converged + l, L, conv_l, 1, 1, npen, cudaMemcpyDeviceToDevice, s));
+  }
+  CU(cudaMemcpyAsync(lambdas_out, lam, sizeof(double) * npen * L, cudaMemcpyDeviceToDevice, s));
+  cudaFreeHost(hflags);
+  return rr;
 }
 
 }  // extern "C"

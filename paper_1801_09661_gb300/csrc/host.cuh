@@ -230,18 +230,21 @@ struct GramPlan {
   int pmax_chunks = 0;
 };
 
-// centre: Z = [X | y | 1] on X and y shifted by sampled column means (the
-// intercept option); a bfloat16 request then runs in split mode, since the
-// shifted X is not bfloat16.
+// ones: 0 = Z = [X | y]; kOnesShifted = Z = [X | y | 1] on X and y shifted
+// by sampled column means (the intercept option of the linear model; a
+// bfloat16 request then runs in split mode, since the shifted X is not
+// bfloat16); kOnes = Z = [X | y | 1] unshifted (logistic regression).
+constexpr int kOnesShifted = 1, kOnes = 2;
 inline GramPlan plan_gram(oem_ctx* ctx, int64_t n, int64_t p, int K, int32_t mode, bool sorted,
-                          bool centre = false) {
+                          int ones = 0) {
   GramPlan g;
+  const bool centre = ones == kOnesShifted;
   if (centre && mode == OEM_GRAM_BF16) mode = OEM_GRAM_SPLIT_BF16;
   g.mode = mode;
   g.centre = centre;
   // bfloat16 mode carries the float32 y as three bfloat16 pieces (exact)
   g.ycols = (mode == OEM_GRAM_BF16) ? 3 : 1;
-  g.ocols = centre ? 1 : 0;
+  g.ocols = ones ? 1 : 0;
   g.q = (int32_t)p + g.ycols + g.ocols;
   g.T = tc_mode(mode) ? 128 : 64;
   g.nt = (g.q + g.T - 1) / g.T;
@@ -677,7 +680,9 @@ inline int launch_iter_layout(oem_ctx* ctx, int64_t p, int B, const float* G32, 
                               const double* G64, const double* c, const double* d,
                               const double* lam, PenPlan& P, const oem_options* o, IterPlan& I,
                               double* beta, int32_t* iters, uint8_t* conv, int64_t max_loops,
-                              std::vector<IterTask>& tasks, cudaStream_t s) {
+                              std::vector<IterTask>& tasks, cudaStream_t s,
+                              double* st_u = nullptr, double* st_beta = nullptr,
+                              int32_t* st_ctl = nullptr) {
   const int L = o->nlambda, npen = P.npen, Mg = I.Mg;
   const int S = (npen + Mg - 1) / Mg;
   tasks.assign((size_t)B * S, IterTask{});
@@ -698,6 +703,12 @@ inline int launch_iter_layout(oem_ctx* ctx, int64_t p, int B, const float* G32, 
       t.beta = beta + ((size_t)b * npen + k0) * L * p;
       t.iters = iters + ((size_t)b * npen + k0) * L;
       t.conv = conv + ((size_t)b * npen + k0) * L;
+      if (st_u) {  // resume every instance from the given (u, beta) state
+        t.resume = 1;
+        t.st_u = st_u + ((size_t)b * npen + k0) * p * 2;
+        t.st_beta = st_beta + ((size_t)b * npen + k0) * p;
+        t.st_ctl = st_ctl + (size_t)(b * S + q) * 40;
+      }
       if (I.grid) {
         const size_t ldgs = (size_t)((p + 3) & ~3LL);
         unsigned char* x = I.d_xbuf + (size_t)(b * S + q) * I.xbuf_task;

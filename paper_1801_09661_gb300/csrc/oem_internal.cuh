@@ -350,6 +350,35 @@ cudaError_t launch_cv_score(const double* Zg, int K, int q, int p, int ycols,
                             int32_t* idx_min, int32_t* idx_1se, int32_t* best, cudaStream_t s,
                             int ocol = -1, const double* bprime = nullptr);
 
+// Logistic regression (Section 4, Hessian bound 1/4): one pass over X per
+// outer step for every penalty's beta ([npen][ldb] float64, the intercept
+// last), partial sums per CTA, g = Z^T (y - mu) / n into g [npen][ldb].
+struct LogitArgs {
+  const void* X;
+  int32_t xtype;
+  int64_t n, p, ldx;
+  const void* y;
+  int32_t ytype;        // OEM_F32 or OEM_F64
+  const double* beta;
+  int32_t ldb;
+  int32_t intercept;
+  int32_t rc;           // rows per shared-memory chunk
+  float2* part;         // [grid][npen][pq] (hi, lo)
+  double* g;            // [npen][ldb]
+};
+size_t logit_grad_smem(int64_t p, int rc, int npen, int intercept);
+cudaError_t launch_logit_grad(const LogitArgs& a, int npen, int grid, cudaStream_t s);
+cudaError_t launch_logit_state(const double* g, const double* beta, int npen, int pq, int ldb,
+                               const double* d, const DevPenalty* pens, int precision, double* st_u,
+                               double* st_beta, int32_t* st_ctl, int nctl, cudaStream_t s);
+cudaError_t launch_logit_step(double* beta, const double* bnew, int npen, int pq, int ldb,
+                              const int32_t* it_new, int32_t* its, double tol, int32_t* flags,
+                              int last_outer, uint8_t* conv, cudaStream_t s);
+cudaError_t launch_logit_null(double* beta, int npen, int pq, int ldb, int intercept, const double* Zg,
+                              int q, int p, int ycols, int ocol, int64_t n, cudaStream_t s);
+cudaError_t launch_logit_gram(const double* Zg, int q, int p, int ocol, int intercept, int64_t n,
+                              double* G64, float* G32, int ldg, cudaStream_t s);
+
 // Copy the full-data (b = 0) paths out of the batched buffers.
 cudaError_t launch_copy_paths(const double* beta_all, const int32_t* it_all, const uint8_t* cv_all,
                               int npen, int nlambda, int p, double* beta, int32_t* iters,
