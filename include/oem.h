@@ -15,6 +15,18 @@
  * Conventions (all entry points):
  *   - Array arguments are DEVICE pointers owned by the caller, unless a
  *     parameter says "host". The library never frees caller memory.
+ *   - Exception, X in host memory: oem_gram, oem_fold_grams, oem_fit and
+ *     oem_cv also accept X (and then y, fold, on either side) in host memory,
+ *     pinned or pageable (the paper's out-of-memory big.oem, Section 5.7, done
+ *     as a stream): row blocks of about 256 MB are copied into two device
+ *     staging buffers on a copy stream while the previous block's Gram pass
+ *     runs, and the blocks' fold sums are added up; pinned memory overlaps
+ *     the copies with the passes. The work is ordered after `stream`'s
+ *     earlier work and before its later work; the call returns without
+ *     waiting for the device, so the host buffers must stay valid until
+ *     `stream` has reached that point. With X in device memory, y and fold
+ *     must be in device memory too (OEM_EINVAL otherwise). oem_fit_logistic
+ *     takes device memory only.
  *   - Matrices are row-major (C order). X is n x p with leading dimension
  *     ldx >= p (elements); ldx * sizeof(element) must be a multiple of 16 and
  *     X, y must be 16-byte aligned, else OEM_EINVAL.

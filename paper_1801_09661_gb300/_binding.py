@@ -124,6 +124,12 @@ def _ptr(t) -> Optional[int]:
     return int(t.data_ptr())
 
 
+def _out_device(ctx, X):
+    """Outputs live on the context's device, also when X is in host memory."""
+    import torch
+    return X.device if X.is_cuda else torch.device("cuda", ctx.device)
+
+
 def _stream(stream) -> Optional[int]:
     if stream is None:
         import torch
@@ -205,6 +211,7 @@ class Context:
         if rc != OEM_OK:
             raise OemError(rc, "oem_create failed")
         self.h = h
+        self.device = int(device)
 
     def close(self):
         if self.h:
@@ -274,7 +281,7 @@ def _xtype(X) -> int:
 def oem_gram(ctx: Context, X, y, mode="auto", G=None, c=None, yty=None, stream=None):
     import torch
     n, p = X.shape
-    dev = X.device
+    dev = _out_device(ctx, X)
     G = torch.empty((p, p), dtype=torch.float64, device=dev) if G is None else G
     c = torch.empty(p, dtype=torch.float64, device=dev) if c is None else c
     yty = torch.empty(1, dtype=torch.float64, device=dev) if yty is None else yty
@@ -303,7 +310,7 @@ def oem_gram_noalloc(X, y, mode="auto", G=None, c=None, yty=None, stream=None):
 def oem_fold_grams(ctx: Context, X, y, fold, K, mode="auto", stream=None):
     import torch
     n, p = X.shape
-    dev = X.device
+    dev = _out_device(ctx, X)
     Gk = torch.empty((K, p, p), dtype=torch.float64, device=dev)
     ck = torch.empty((K, p), dtype=torch.float64, device=dev)
     ytyk = torch.empty(K, dtype=torch.float64, device=dev)
@@ -350,13 +357,14 @@ def oem_fit(ctx: Context, X, y, pens: Sequence[Penalty], stream=None, out=None, 
     n, p = X.shape
     o = make_options(**opts)
     P = _PenArray(pens)
+    dev = _out_device(ctx, X)
     if out is None:
-        beta, lam, its, conv = _path_outputs(P.n, o.nlambda, p, X.device)
-        d = torch.empty(1, dtype=torch.float64, device=X.device)
+        beta, lam, its, conv = _path_outputs(P.n, o.nlambda, p, dev)
+        d = torch.empty(1, dtype=torch.float64, device=dev)
     else:
         beta, lam, its, conv, d = out
     centred = bool(o.intercept or o.standardize)
-    beta0 = torch.empty((P.n, o.nlambda), dtype=torch.float64, device=X.device) if centred else None
+    beta0 = torch.empty((P.n, o.nlambda), dtype=torch.float64, device=dev) if centred else None
     ctx.check(lib.oem_fit(ctx.h, _ptr(X), _xtype(X), n, p, X.stride(0), _ptr(y), P.arr, P.n,
                           C.byref(o), _ptr(beta), _ptr(lam), _ptr(its), _ptr(conv), _ptr(d),
                           _ptr(beta0), _stream(stream)))
@@ -371,7 +379,7 @@ def oem_cv(ctx: Context, X, y, fold, K, pens: Sequence[Penalty], stream=None, **
     o = make_options(**opts)
     P = _PenArray(pens)
     L = o.nlambda
-    dev = X.device
+    dev = _out_device(ctx, X)
     beta = torch.empty((P.n, L, p), dtype=torch.float64, device=dev)
     lam = torch.empty((P.n, L), dtype=torch.float64, device=dev)
     cvm = torch.empty((P.n, L), dtype=torch.float64, device=dev)

@@ -117,6 +117,25 @@ int oem_sync(oem_ctx* ctx, void* stream) {
   return OEM_OK;
 }
 
+// Where X, y and fold live: X in host memory streams through the Gram pass
+// (y and fold may then live on either side); with X on the device, y and fold
+// must be on the device too.
+static int plan_residence(oem_ctx* ctx, const void* X, const void* y, const uint8_t* fold, int64_t n,
+                          int64_t ldx, int32_t xtype, StreamBufs& sb, int64_t* rows) {
+  sb.on = host_resident(X);
+  if (!sb.on) {
+    if (host_resident(y) || (fold && host_resident(fold)))
+      return fail(ctx, OEM_EINVAL, "y and fold must be in device memory when X is");
+    *rows = n;
+    return OEM_OK;
+  }
+  sb.y_host = host_resident(y);
+  sb.fold_host = fold && host_resident(fold);
+  sb.rows = stream_block_rows(n, ldx, xtype);
+  *rows = sb.rows;
+  return OEM_OK;
+}
+
 int oem_gram(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, int64_t ldx,
              const void* y, int32_t mode, double* G, double* c, double* yty, void* stream) {
   if (!ctx) return OEM_EINVAL;
@@ -127,15 +146,21 @@ int oem_gram(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, i
   if ((r = resolve_mode(ctx, mode, xtype, &m))) return r;
   cudaStream_t s = (cudaStream_t)stream;
   CU(cudaSetDevice(ctx->device));
-  GramPlan g = plan_gram(ctx, n, p, 1, m, false);
+  StreamBufs sb;
+  int64_t rows;
+  if ((r = plan_residence(ctx, X, y, nullptr, n, ldx, xtype, sb, &rows))) return r;
+  GramPlan g = plan_gram(ctx, rows, p, 1, m, false);
   GramBufs b;
   Arena A;
-  gram_request(A, g, n, b);
+  gram_request(A, g, rows, b);
+  if (sb.on) stream_request(A, sb, rows, ldx, xtype, 1, g.q, false);
   int64_t* nk = nullptr;
   A.add(&nk, 1);
   if ((r = arena_commit(ctx, A, s))) return r;
-  if ((r = run_gram(ctx, g, b, X, xtype, n, p, ldx, y, nullptr, false, s))) return r;
-  LAUNCH(OEM_PROF_ASSEMBLE, launch_extract_folds(b.Zg, 1, g.q, (int)p, g.ycols, G, c, yty, nk, b.ct.fold_off, s));
+  const double* Zg;
+  const int64_t* foff;
+  if ((r = run_gram_any(ctx, g, b, sb, X, xtype, n, p, ldx, y, nullptr, false, s, &Zg, &foff))) return r;
+  LAUNCH(OEM_PROF_ASSEMBLE, launch_extract_folds(Zg, 1, g.q, (int)p, g.ycols, G, c, yty, nk, foff, s));
   return OEM_OK;
 }
 
@@ -151,13 +176,19 @@ int oem_fold_grams(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_
   if ((r = resolve_mode(ctx, mode, xtype, &m))) return r;
   cudaStream_t s = (cudaStream_t)stream;
   CU(cudaSetDevice(ctx->device));
-  GramPlan g = plan_gram(ctx, n, p, K, m, true);
+  StreamBufs sb;
+  int64_t rows;
+  if ((r = plan_residence(ctx, X, y, fold, n, ldx, xtype, sb, &rows))) return r;
+  GramPlan g = plan_gram(ctx, rows, p, K, m, true);
   GramBufs b;
   Arena A;
-  gram_request(A, g, n, b);
+  gram_request(A, g, rows, b);
+  if (sb.on) stream_request(A, sb, rows, ldx, xtype, K, g.q, true);
   if ((r = arena_commit(ctx, A, s))) return r;
-  if ((r = run_gram(ctx, g, b, X, xtype, n, p, ldx, y, fold, false, s))) return r;
-  LAUNCH(OEM_PROF_ASSEMBLE, launch_extract_folds(b.Zg, K, g.q, (int)p, g.ycols, Gk, ck, ytyk, nk, b.ct.fold_off, s));
+  const double* Zg;
+  const int64_t* foff;
+  if ((r = run_gram_any(ctx, g, b, sb, X, xtype, n, p, ldx, y, fold, false, s, &Zg, &foff))) return r;
+  LAUNCH(OEM_PROF_ASSEMBLE, launch_extract_folds(Zg, K, g.q, (int)p, g.ycols, Gk, ck, ytyk, nk, foff, s));
   return OEM_OK;
 }
 
@@ -265,13 +296,17 @@ int oem_fit(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, in
   IterPlan I;
   if ((r = plan_iter(ctx, p, 1, P, opt, I))) return r;
   const bool centre = opt->intercept || opt->standardize;
-  GramPlan g = plan_gram(ctx, n, p, 1, m, false, opt->intercept ? kOnesShifted : 0);
+  StreamBufs sb;
+  int64_t rows;
+  if ((r = plan_residence(ctx, X, y, nullptr, n, ldx, xtype, sb, &rows))) return r;
+  GramPlan g = plan_gram(ctx, rows, p, 1, m, false, opt->intercept ? kOnesShifted : 0);
   GramBufs b;
   double *G64 = nullptr, *c = nullptr, *N = nullptr, *cnt = nullptr, *dd = nullptr, *cen = nullptr;
   float* G32 = nullptr;
   LanczosWork w{};
   Arena A;
-  gram_request(A, g, n, b);
+  gram_request(A, g, rows, b);
+  if (sb.on) stream_request(A, sb, rows, ldx, xtype, 1, g.q, false);
   if (centre) A.add(&cen, (size_t)(2 * p + 1));
   A.add(&G64, (size_t)p * p);
   if (opt->iter_precision == OEM_ITER_F32) A.add(&G32, (size_t)p * ldg32);
@@ -283,7 +318,9 @@ int oem_fit(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, in
   pens_request(A, P);
   iter_request(A, p, 1, I);
   if ((r = arena_commit(ctx, A, s))) return r;
-  if ((r = run_gram(ctx, g, b, X, xtype, n, p, ldx, y, nullptr, false, s))) return r;
+  const double* Zg;
+  const int64_t* foff;
+  if ((r = run_gram_any(ctx, g, b, sb, X, xtype, n, p, ldx, y, nullptr, false, s, &Zg, &foff))) return r;
   CentreArgs ce;
   if (centre) {
     ce.ocol = opt->intercept ? (int32_t)p + g.ycols : -1;
@@ -291,7 +328,7 @@ int oem_fit(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, in
     ce.standardize = opt->standardize;
     ce.cen = cen;
   }
-  LAUNCH(OEM_PROF_ASSEMBLE, launch_assemble(b.Zg, 1, g.q, (int)p, g.ycols, b.ct.fold_off, 0, G64, G32, ldg32, c, N,
+  LAUNCH(OEM_PROF_ASSEMBLE, launch_assemble(Zg, 1, g.q, (int)p, g.ycols, foff, 0, G64, G32, ldg32, c, N,
                          cnt, s, ce));
   cudaError_t e = lanczos_prof(ctx, s, G64, p, p, 1, p * p, opt->lanczos_steps, w, dd, s, &ctx->launches);
   if (e != cudaSuccess) return fail(ctx, OEM_ECUDA, "Lanczos launch failed: %s", cudaGetErrorString(e));
@@ -332,7 +369,10 @@ int oem_cv(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, int
   IterPlan I;
   if ((r = plan_iter(ctx, p, B, P, opt, I))) return r;
   const bool centre = opt->intercept || opt->standardize;
-  GramPlan g = plan_gram(ctx, n, p, K, m, true, opt->intercept ? kOnesShifted : 0);
+  StreamBufs sb;
+  int64_t rows;
+  if ((r = plan_residence(ctx, X, y, fold, n, ldx, xtype, sb, &rows))) return r;
+  GramPlan g = plan_gram(ctx, rows, p, K, m, true, opt->intercept ? kOnesShifted : 0);
   GramBufs b;
   double *G64 = nullptr, *c = nullptr, *N = nullptr, *cnt = nullptr, *dd = nullptr;
   double *beta_all = nullptr, *mse = nullptr, *cen = nullptr, *bprime = nullptr;
@@ -341,7 +381,8 @@ int oem_cv(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, int
   float* G32 = nullptr;
   LanczosWork w{};
   Arena A;
-  gram_request(A, g, n, b);
+  gram_request(A, g, rows, b);
+  if (sb.on) stream_request(A, sb, rows, ldx, xtype, K, g.q, true);
   A.add(&G64, (size_t)B * p * p);
   if (opt->iter_precision == OEM_ITER_F32) A.add(&G32, (size_t)B * p * ldg32);
   A.add(&c, (size_t)B * p);
@@ -360,7 +401,9 @@ int oem_cv(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, int
   pens_request(A, P);
   iter_request(A, p, B, I);
   if ((r = arena_commit(ctx, A, s))) return r;
-  if ((r = run_gram(ctx, g, b, X, xtype, n, p, ldx, y, fold, true, s))) return r;
+  const double* Zg;
+  const int64_t* foff;
+  if ((r = run_gram_any(ctx, g, b, sb, X, xtype, n, p, ldx, y, fold, true, s, &Zg, &foff))) return r;
   CentreArgs ce;
   if (centre) {
     ce.ocol = opt->intercept ? (int32_t)p + g.ycols : -1;
@@ -368,7 +411,7 @@ int oem_cv(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, int
     ce.standardize = opt->standardize;
     ce.cen = cen;
   }
-  LAUNCH(OEM_PROF_ASSEMBLE, launch_assemble(b.Zg, K, g.q, (int)p, g.ycols, b.ct.fold_off, 1, G64, G32, ldg32, c, N,
+  LAUNCH(OEM_PROF_ASSEMBLE, launch_assemble(Zg, K, g.q, (int)p, g.ycols, foff, 1, G64, G32, ldg32, c, N,
                          cnt, s, ce));
   cudaError_t e = lanczos_prof(ctx, s, G64, p, p, B, p * p, opt->lanczos_steps, w, dd, s, &ctx->launches);
   if (e != cudaSuccess) return fail(ctx, OEM_ECUDA, "Lanczos launch failed: %s", cudaGetErrorString(e));
@@ -380,7 +423,7 @@ int oem_cv(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, int
                                                bprime, beta0_full, s));
   else if (beta0_full)
     CU(cudaMemsetAsync(beta0_full, 0, sizeof(double) * npen * L, s));
-  LAUNCH(OEM_PROF_CV, launch_cv_score(b.Zg, K, g.q, (int)p, g.ycols, b.ct.fold_off, beta_all, npen, L, mse, cvm,
+  LAUNCH(OEM_PROF_CV, launch_cv_score(Zg, K, g.q, (int)p, g.ycols, foff, beta_all, npen, L, mse, cvm,
                          cvsd, idx_min, idx_1se, best_penalty, s, ce.ocol, bprime));
   LAUNCH(OEM_PROF_COPY, launch_copy_paths(beta_all, it_all, cv_all, npen, L, (int)p, beta_full, nullptr, nullptr,
                            ctx->dstatus, s));
@@ -397,6 +440,8 @@ int oem_fit_logistic(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int6
   if ((r = check_opts(ctx, opt))) return r;
   if (!beta || !lambdas_out || !iters || !converged) return fail(ctx, OEM_EINVAL, "NULL pointer argument");
   if (p > 1023) return fail(ctx, OEM_EINVAL, "logistic regression: p=%lld exceeds 1023", (long long)p);
+  if (host_resident(X) || host_resident(y))
+    return fail(ctx, OEM_EUNSUPPORTED, "logistic regression: X and y must be in device memory");
   if (opt->standardize) return fail(ctx, OEM_EUNSUPPORTED, "logistic regression: standardize is not supported");
   if (!pens || npen < 1 || npen > 8) return fail(ctx, OEM_EINVAL, "npen=%d must be in [1,8]", npen);
   for (int i = 0; i < npen; ++i)

@@ -6,6 +6,8 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 namespace oem {
 
 __global__ void gram_reduce_kernel(GramArgs a, int K, double* __restrict__ Zg) {
@@ -190,6 +192,45 @@ cudaError_t launch_assemble(const double* Zg, int K, int q, int p, int ycols,
   if (gx > 2048) gx = 2048;
   assemble_kernel<<<dim3(gx, B), 256, 0, s>>>(Zg, K, q, p, ycols, fold_off, B, G64, G32, ldg32,
                                               c, N, cnt, ce);
+  return cudaGetLastError();
+}
+
+// Streamed Gram pass (X in host memory, row blocks): acc += blk over the
+// fold Grams of Z, and the fold row counts from the block's sorted offsets.
+__global__ void zg_accumulate_kernel(double* __restrict__ acc, const double* __restrict__ blk, int64_t len,
+                                     int first, int64_t* __restrict__ cnt,
+                                     const int64_t* __restrict__ fold_off, int K) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+       e += (int64_t)gridDim.x * blockDim.x)
+    acc[e] = first ? blk[e] : acc[e] + blk[e];
+  if (blockIdx.x == 0 && threadIdx.x < K) {
+    const int64_t c = fold_off[threadIdx.x + 1] - fold_off[threadIdx.x];
+    cnt[threadIdx.x] = first ? c : cnt[threadIdx.x] + c;
+  }
+}
+
+// Offsets of the accumulated folds (the layout the assembly reads:
+// off[k+1] - off[k] = rows of fold k); flags an empty fold when asked.
+__global__ void zg_offsets_kernel(const int64_t* __restrict__ cnt, int64_t* off, int K, int require_nonempty,
+                                  unsigned* dstatus) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  off[0] = 0;
+  for (int k = 0; k < K; ++k) {
+    off[k + 1] = off[k] + cnt[k];
+    if (cnt[k] == 0 && require_nonempty) atomicOr(dstatus, kStatEmptyFold);
+  }
+}
+
+cudaError_t launch_zg_accumulate(double* acc, const double* blk, int64_t len, int first, int64_t* cnt,
+                                 const int64_t* fold_off, int K, cudaStream_t s) {
+  const unsigned gx = (unsigned)std::min<int64_t>(1024, (len + 255) / 256);
+  zg_accumulate_kernel<<<gx, 256, 0, s>>>(acc, blk, len, first, cnt, fold_off, K);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zg_offsets(const int64_t* cnt, int64_t* off, int K, int require_nonempty, unsigned* dstatus,
+                              cudaStream_t s) {
+  zg_offsets_kernel<<<1, 32, 0, s>>>(cnt, off, K, require_nonempty, dstatus);
   return cudaGetLastError();
 }
 

@@ -102,6 +102,19 @@ struct ProfScope {
       return fail(ctx, OEM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
   } while (0)
 
+// LAUNCH that stores the failure in r instead of returning.
+#define LAUNCH_R(cls, call, r)                                                           \
+  do {                                                                                   \
+    cudaError_t e_;                                                                      \
+    {                                                                                    \
+      ProfScope ps_(ctx, s, (cls), 1);                                                   \
+      e_ = (call);                                                                       \
+    }                                                                                    \
+    ++ctx->launches;                                                                     \
+    if (e_ != cudaSuccess)                                                               \
+      r = fail(ctx, OEM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));          \
+  } while (0)
+
 inline cudaError_t lanczos_prof(oem_ctx* ctx, cudaStream_t s, const double* G, int64_t p, int64_t ldg,
                          int batch, int64_t strideG, int steps, LanczosWork w, double* d,
                          cudaStream_t s2, int64_t* launches) {
@@ -325,7 +338,7 @@ inline void gram_request(Arena& A, const GramPlan& g, int64_t n, GramBufs& b) {
 // fold sort (if any) -> chunk table -> Gram partials -> per-fold Z Grams.
 inline int run_gram(oem_ctx* ctx, const GramPlan& g, GramBufs& b, const void* X, int32_t xtype,
              int64_t n, int64_t p, int64_t ldx, const void* y, const uint8_t* fold,
-             bool require_nonempty, cudaStream_t s) {
+             bool require_nonempty, cudaStream_t s, bool shift_ready = false) {
   if (g.sorted) {
     LAUNCH(OEM_PROF_FOLD_SORT, launch_fold_count(fold, n, g.K, b.blk_counts, g.nblk, s));
     LAUNCH(OEM_PROF_FOLD_SORT, launch_fold_scan(b.blk_counts, g.nblk, g.K, g.chunk_rows, b.blk_offsets, b.ct,
@@ -340,7 +353,7 @@ inline int run_gram(oem_ctx* ctx, const GramPlan& g, GramBufs& b, const void* X,
   a.mode = g.mode; a.q = g.q; a.ycols = g.ycols; a.T = g.T; a.ntile1 = g.nt; a.ntiles = g.ntiles;
   a.ocols = g.ocols;
   if (g.centre) {
-    LAUNCH(OEM_PROF_CHUNKS, launch_col_shift(X, xtype, n, p, ldx, y, b.shift, s));
+    if (!shift_ready) LAUNCH(OEM_PROF_CHUNKS, launch_col_shift(X, xtype, n, p, ldx, y, b.shift, s));
     a.shift = b.shift;
   }
   a.ct = b.ct; a.max_chunks = g.max_chunks; a.partial = b.partial; a.dstatus = ctx->dstatus;
@@ -380,6 +393,144 @@ inline int run_gram(oem_ctx* ctx, const GramPlan& g, GramBufs& b, const void* X,
   }
   LAUNCH(OEM_PROF_GRAM_REDUCE, launch_gram_reduce(a, g.K, b.Zg, s));
   return OEM_OK;
+}
+
+// ---------------------------------------------------------------- X in host memory
+// X (and y, fold) may live in host memory (the out-of-memory case of the
+// paper's big.oem, Section 5.7, done as a stream): row blocks are copied into
+// two device staging buffers on a copy stream while the previous block's
+// Gram pass runs, and the blocks' fold Grams of Z and row counts are added up.
+// Pinned host memory overlaps the copies with the passes; pageable memory
+// works without overlap.
+inline bool host_resident(const void* ptr) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+struct StreamBufs {
+  bool on = false;          // X is streamed from host memory
+  bool y_host = false, fold_host = false;
+  int64_t rows = 0;         // rows per block
+  unsigned char* X[2] = {nullptr, nullptr};
+  unsigned char* y[2] = {nullptr, nullptr};
+  uint8_t* fold[2] = {nullptr, nullptr};
+  double* Zg = nullptr;     // [K][q][q] accumulated
+  int64_t* cnt = nullptr;   // [K]
+  int64_t* off = nullptr;   // [K+1]
+};
+
+// Rows per block: about 256 MB of X, a multiple of 64, at most n
+// (OEM_STREAM_ROWS overrides, for experiments).
+inline int64_t stream_block_rows(int64_t n, int64_t ldx, int32_t xtype) {
+  int64_t rb = std::max<int64_t>(65536, ((int64_t)256 << 20) / (ldx * elem_size(xtype))) / 64 * 64;
+  if (const char* ev = getenv("OEM_STREAM_ROWS")) {
+    const long long v = atoll(ev);
+    if (v >= 64) rb = v / 64 * 64;
+  }
+  return std::min<int64_t>(n, rb);
+}
+
+template <typename A>
+inline void stream_request(A& ar, StreamBufs& sb, int64_t rows, int64_t ldx, int32_t xtype, int K, int q,
+                           bool with_fold) {
+  const size_t ye = xtype == OEM_F64 ? 8 : 4;
+  for (int i = 0; i < 2; ++i) {
+    ar.add(&sb.X[i], (size_t)rows * ldx * elem_size(xtype));
+    if (sb.y_host) ar.add(&sb.y[i], (size_t)rows * ye);
+    if (with_fold && sb.fold_host) ar.add(&sb.fold[i], (size_t)rows);
+  }
+  ar.add(&sb.Zg, (size_t)K * q * q);
+  ar.add(&sb.cnt, (size_t)K);
+  ar.add(&sb.off, (size_t)K + 1);
+}
+
+// The Gram pass over X wherever it lives; *Zg and *fold_off receive the fold
+// Grams of Z and the fold offsets the assembly reads.
+inline int run_gram_any(oem_ctx* ctx, const GramPlan& g, GramBufs& b, StreamBufs& sb, const void* X,
+                        int32_t xtype, int64_t n, int64_t p, int64_t ldx, const void* y,
+                        const uint8_t* fold, bool require_nonempty, cudaStream_t s, const double** Zg,
+                        const int64_t** fold_off) {
+  if (!sb.on) {
+    int r = run_gram(ctx, g, b, X, xtype, n, p, ldx, y, fold, require_nonempty, s);
+    *Zg = b.Zg;
+    *fold_off = b.ct.fold_off;
+    return r;
+  }
+  const size_t xrow = (size_t)ldx * elem_size(xtype), ye = xtype == OEM_F64 ? 8 : 4;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t start = nullptr, copied[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
+  int r = OEM_OK;
+  auto cleanup = [&]() {
+    if (cs) cudaStreamDestroy(cs);
+    if (start) cudaEventDestroy(start);
+    for (int i = 0; i < 2; ++i) {
+      if (copied[i]) cudaEventDestroy(copied[i]);
+      if (used[i]) cudaEventDestroy(used[i]);
+    }
+  };
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess) {
+    cleanup();
+    return fail(ctx, OEM_ECUDA, "stream / event creation failed");
+  }
+  for (int i = 0; i < 2; ++i)
+    if (cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&used[i], cudaEventDisableTiming) != cudaSuccess) {
+      cleanup();
+      return fail(ctx, OEM_ECUDA, "event creation failed");
+    }
+  const int64_t nblocks = (n + sb.rows - 1) / sb.rows;
+  const int64_t zlen = (int64_t)g.K * g.q * g.q;
+  cudaError_t e = cudaEventRecord(start, s);  // the copies follow the caller's earlier work
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, start, 0);
+  for (int64_t blk = 0; blk < nblocks && e == cudaSuccess && !r; ++blk) {
+    const int i = (int)(blk & 1);
+    const int64_t r0 = blk * sb.rows, rows = std::min<int64_t>(sb.rows, n - r0);
+    // ---- copy stream: block blk into buffer i once the pass of block blk-2 is done
+    if (blk >= 2) e = cudaStreamWaitEvent(cs, used[i], 0);
+    const void* Xb = X;
+    const void* yb = y;
+    const uint8_t* fb = fold;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(sb.X[i], (const unsigned char*)X + r0 * xrow, (size_t)rows * xrow,
+                          cudaMemcpyHostToDevice, cs);
+    Xb = sb.X[i];
+    if (e == cudaSuccess && sb.y_host) {
+      e = cudaMemcpyAsync(sb.y[i], (const unsigned char*)y + r0 * ye, (size_t)rows * ye, cudaMemcpyHostToDevice, cs);
+      yb = sb.y[i];
+    } else {
+      yb = (const unsigned char*)y + r0 * ye;
+    }
+    if (fold) {
+      if (e == cudaSuccess && sb.fold_host) {
+        e = cudaMemcpyAsync(sb.fold[i], fold + r0, (size_t)rows, cudaMemcpyHostToDevice, cs);
+        fb = sb.fold[i];
+      } else {
+        fb = fold + r0;
+      }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(copied[i], cs);
+    // ---- compute stream: the block's Gram pass and the accumulation
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, copied[i], 0);
+    if (e != cudaSuccess) break;
+    r = run_gram(ctx, g, b, Xb, xtype, rows, p, ldx, yb, fb, false, s, blk > 0);
+    if (r) break;
+    LAUNCH_R(OEM_PROF_GRAM_REDUCE, launch_zg_accumulate(sb.Zg, b.Zg, zlen, blk == 0 ? 1 : 0, sb.cnt, b.ct.fold_off,
+                                                     g.K, s), r);
+    if (r) break;
+    e = cudaEventRecord(used[i], s);
+  }
+  if (!r && e != cudaSuccess) r = fail(ctx, OEM_ECUDA, "streamed Gram pass: %s", cudaGetErrorString(e));
+  if (!r)
+    LAUNCH_R(OEM_PROF_GRAM_REDUCE, launch_zg_offsets(sb.cnt, sb.off, g.K, require_nonempty ? 1 : 0, ctx->dstatus, s), r);
+  cleanup();
+  *Zg = sb.Zg;
+  *fold_off = sb.off;
+  return r;
 }
 
 // Penalties on the device.

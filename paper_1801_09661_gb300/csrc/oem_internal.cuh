@@ -129,6 +129,12 @@ cudaError_t launch_assemble(const double* Zg, int K, int q, int p, int ycols,
 // constant), shift[p] the same for y.
 cudaError_t launch_col_shift(const void* X, int32_t xtype, int64_t n, int64_t p, int64_t ldx,
                              const void* y, float* shift, cudaStream_t s);
+// Streamed Gram pass: acc (+)= blk ([len] float64, K fold Grams of Z) and
+// the fold row counts from the block's sorted offsets; then the offsets.
+cudaError_t launch_zg_accumulate(double* acc, const double* blk, int64_t len, int first, int64_t* cnt,
+                                 const int64_t* fold_off, int K, cudaStream_t s);
+cudaError_t launch_zg_offsets(const int64_t* cnt, int64_t* off, int K, int require_nonempty, unsigned* dstatus,
+                              cudaStream_t s);
 // Standardized paths back to the original scale: beta_all [B][npen][L][p]
 // divided by sd in place; bprime [B][npen][L] (may be NULL) = the intercept
 // in the shifted coordinates of the Gram pass; beta0 [npen][L] (may be
