@@ -1,7 +1,8 @@
 """GPU parity with X in host memory: the Gram pass streams X in row blocks
 (pinned or pageable memory) through two device staging buffers and adds the
 blocks' fold sums up (the paper's out-of-memory big.oem, Section 5.7, done as
-a stream of row blocks rather than a memory map).
+a stream of row blocks; a memory-mapped file is one more kind of pageable
+host memory).
 
 Block sizes are forced small (OEM_STREAM_ROWS) so that every case runs
 several blocks with a ragged last one. Tolerances are those of the
@@ -177,6 +178,29 @@ def test_streamed_cv_matches_oracle(oem, ctx, monkeypatch, mode):
     for i in range(len(op)):
         if imin[i] != ref.idx_min[i]:
             assert abs(ref.cvm[i, imin[i]] - ref.cvm[i, ref.idx_min[i]]) <= 1e-6 * ref.cvm[i].min()
+
+
+def test_streamed_from_a_memory_mapped_file(oem, ctx, monkeypatch, tmp_path):
+    # the paper's big.oem keeps X in a file-backed matrix: a memory-mapped
+    # file is pageable host memory to the library
+    monkeypatch.setenv("OEM_STREAM_ROWS", "2048")
+    n, p, L = 7001, 36, 15
+    X, y = _data(n, p, 17)
+    mm = np.lib.format.open_memmap(str(tmp_path / "X.npy"), mode="w+", dtype=np.float32, shape=(n, p))
+    mm[:] = X
+    mm.flush()
+    Xm = np.load(str(tmp_path / "X.npy"), mmap_mode="r+")
+    Xt = torch.from_numpy(Xm)
+    assert not Xt.is_pinned()
+    pens = [oem.Penalty("lasso"), oem.Penalty("scad", gamma=3.7)]
+    beta, lam, its, conv, d = oem.oem_fit(ctx, Xt, _host(y, False), pens, nlambda=L,
+                                          lambda_min_ratio=1e-2, tol=1e-7)
+    assert ctx.sync() == 0
+    for i, pen in enumerate([oracle.Penalty("lasso"), oracle.Penalty("scad", gamma=3.7)]):
+        ref = oracle.fit(X, y, [pen], False, False, nlambda=L, lambda_min_ratio=1e-2, tol=1e-7)
+        rb = ref.beta[0]
+        assert float(np.abs(beta[i].cpu().numpy() - rb).max()) <= 1e-5 * max(1.0, np.abs(rb).max())
+    del Xt, Xm
 
 
 def test_streamed_matches_device_resident_at_full_size(oem, ctx, monkeypatch):
