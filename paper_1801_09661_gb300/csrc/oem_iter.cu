@@ -20,14 +20,18 @@
 //      pair, which updates u_i and, without groups, applies the threshold;
 //   2. for group penalties, forms the group norms and thresholds afterwards;
 //   3. writes its dbeta rows into the shared memory of every CTA of the
-//      cluster (DSMEM stores) and its max|dbeta|, max|beta| per instance
-//      into the block's table.
-// One block barrier, then one warp folds the CTA's maxima into every CTA's
-// reduction slot (DSMEM atomic max on order-preserving 32-bit images, one
-// per peer and value); one cluster barrier per iteration; then every thread
-// takes the same convergence decisions from the same slot. A launch may stop
-// after a loop budget and save its state (serving), to be resumed by a later
-// launch.
+//      cluster and its max|dbeta|, max|beta| per instance into the block's
+//      table.
+// One block barrier, then one warp sends the CTA's maxima to every CTA.
+// Float32 iteration: the dbeta rows and the maxima go out as st.async
+// stores, each counting its bytes on the receiving CTA's mbarrier for that
+// buffer, so a CTA waits (bounded) for exactly the bytes addressed to it and
+// there is no cluster barrier in the loop; one warp then takes the maximum
+// over the C entries. Float64 iteration: plain DSMEM stores, DSMEM atomic
+// max into every CTA's slot (order-preserving 32-bit images) and one cluster
+// barrier per iteration. Every thread then takes the same convergence
+// decisions from the same values. A launch may stop after a loop budget and
+// save its state (serving), to be resumed by a later launch.
 //
 // Grid mode (large p: the Gram rows of a task do not fit in the shared memory
 // of one cluster, at most 16 SMs, but fit in that of C > 16 CTAs): the C CTAs
@@ -174,11 +178,45 @@ __device__ __forceinline__ float from_red(unsigned int b) { return __uint_as_flo
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Cluster-mode exchange by asynchronous stores: st.async writes into a peer
+// CTA's shared memory and counts its bytes on that CTA's mbarrier, so each
+// CTA waits for exactly the bytes addressed to it (no cluster barrier).
+__device__ __forceinline__ uint32_t xs_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t xs_map(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void xs_st4(uint32_t a, float4 v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+               ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void xs_st1(uint32_t a, uint32_t v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
+               ::"r"(a), "r"(v), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void xs_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void xs_arm(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool xs_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 
 // Shared-memory carve-up (byte offsets, 16-byte aligned). The dbeta buffers
 // have ldgs = round_up(p, 4) rows; rows p.. stay zero.
 struct IterSmem {
-  size_t dbuf, uhi, ulo, beta, w, gn, cgr, glen, st, lred, red, gs, total;
+  size_t dbuf, uhi, ulo, beta, w, gn, cgr, glen, st, lred, red, xbar, xslot, xred, gs, total;
 };
 constexpr int kIterMaxWarps = 16;
 __host__ __device__ inline IterSmem iter_smem_layout(int p, int M, int maxR, int tsz, int smem_rows) {
@@ -196,6 +234,9 @@ __host__ __device__ inline IterSmem iter_smem_layout(int p, int M, int maxR, int
   L.st = o;    o = al16(o + (size_t)maxR * M * tsz);
   L.lred = o;  o = al16(o + (size_t)kIterMaxWarps * M * 2 * 4);
   L.red = o;   o = al16(o + (size_t)3 * M * 2 * 4);
+  L.xbar = o;  o = al16(o + 2 * 8);
+  L.xslot = o; o = al16(o + (size_t)2 * 16 * M * 2 * 4);
+  L.xred = o;  o = al16(o + (size_t)(M * 2 + 1) * 4);
   L.gs = o;    o = al16(o + (size_t)smem_rows * ldgs * tsz);
   L.total = o;
   return L;
@@ -231,6 +272,11 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   float* lred = reinterpret_cast<float*>(smem + Ls.lred);  // [warp][2M] block table
   unsigned int* red = reinterpret_cast<unsigned int*>(smem + Ls.red);  // [3][2M] slots
   T* Gs = reinterpret_cast<T*>(smem + Ls.gs);
+  constexpr bool kAsync = kF32 && !kGrid;
+  const uint32_t xbar0 = xs_u32(smem + Ls.xbar);  // mbarriers of dbeta buffers 0 / 1
+  unsigned int* xslot = reinterpret_cast<unsigned int*>(smem + Ls.xslot);  // [2][C][2M]
+  unsigned int* xred = reinterpret_cast<unsigned int*>(smem + Ls.xred);    // [2M], then the timeout flag
+  volatile unsigned int* xfail = xred + 2 * M;
   const T* Gglob = kF32 ? reinterpret_cast<const T*>(tk.G32) : reinterpret_cast<const T*>(tk.G64);
   const int ldgg = kF32 ? tk.ldg : p;
   const double* cb = tk.c;
@@ -313,6 +359,12 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   }
   for (int e = tid; e < 2 * ldgs * M; e += NT) Dbuf[e] = T(0);
   for (int e = tid; e < 3 * M * 2; e += NT) red[e] = 0u;
+  if (kAsync && tid == 0) {
+    xs_init(xbar0);
+    xs_init(xbar0 + 8);
+    *xfail = 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   for (int e = tid; e < smem_rows * ldgs; e += NT) {
     const int i = e / ldgs, j = e % ldgs;
     Gs[e] = (i < R && j < p) ? Gglob[(size_t)(i0 + i) * ldgg + j] : T(0);
@@ -556,6 +608,33 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
         const int u0 = f0 >> 2, nu = ((f1 + 3) >> 2) - u0;
         T* Dn = (kGrid ? xD : Dbuf) + (size_t)nxt * ldgs * M;
         const int CC = kGrid ? 1 : C;
+        if constexpr (kAsync) {
+          const uint32_t bar = xbar0 + 8 * nxt;
+          for (int e = lane; e < nu * C; e += 32) {
+            const int u = u0 + e / C, r = e % C;
+            float* dl = Dn + ((u ^ ((u >> 3) & (M - 1))) << 2);
+            const float* src = st + (4 * u - i0 * M);
+            const bool whole = 4 * u >= f0 && 4 * u + 4 <= f1;
+            if (r == rank) {
+              if (whole) {
+                *reinterpret_cast<float4*>(dl) = *reinterpret_cast<const float4*>(src);
+              } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                  if (4 * u + q >= f0 && 4 * u + q < f1) dl[q] = src[q];
+              }
+            } else {
+              const uint32_t ra = xs_map(xs_u32(dl), r), rb = xs_map(bar, r);
+              if (whole) {
+                xs_st4(ra, *reinterpret_cast<const float4*>(src), rb);
+              } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                  if (4 * u + q >= f0 && 4 * u + q < f1) xs_st1(ra + 4 * q, __float_as_uint(src[q]), rb);
+              }
+            }
+          }
+        } else {
         for (int e = lane; e < nu * CC; e += 32) {
           const int u = u0 + e / CC, r = e % CC;
           float* dst = (kGrid ? Dn : cluster.map_shared_rank(Dn, r)) + ((u ^ ((u >> 3) & (M - 1))) << 2);
@@ -567,6 +646,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
             for (int q = 0; q < 4; ++q)
               if (4 * u + q >= f0 && 4 * u + q < f1) dst[q] = src[q];
           }
+        }
         }
       } else if constexpr (kGrid) {
         T* Dn = xD + (size_t)nxt * ldgs * M;
@@ -598,7 +678,35 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
       float v = 0.f;
       if (lane < E)
         for (int w = 0; w < NW; ++w) v = fmax(v, lred[w * E + lane]);
-      if constexpr (kGrid) {
+      if constexpr (kAsync) {
+        // this CTA's maxima into entry [nxt][rank] of every CTA; then the
+        // wait for every peer's dbeta rows and maxima (bounded), and the
+        // maxima over the C entries into xred
+        const uint32_t bar = xbar0 + 8 * nxt;
+        unsigned int* sl = xslot + (size_t)nxt * 16 * E;
+        for (int base = 0; base < C * E; base += 32) {
+          const int e = base + lane, q = e % E, r = e / E;
+          const float val = __shfl_sync(0xffffffffu, v, q);
+          if (e < C * E) {
+            if (r == rank) sl[rank * E + q] = __float_as_uint(val);
+            else xs_st1(xs_map(xs_u32(sl + rank * E + q), r), __float_as_uint(val), xs_map(bar, r));
+          }
+        }
+        if (lane == 0) xs_arm(bar, (uint32_t)(((p - R) * M + (C - 1) * E) * 4));
+        const uint32_t par = (uint32_t)((t >> 1) & 1);
+        bool ok = xs_try(bar, par);
+        if (!ok) {
+          const long long t0 = clock64();
+          while (!(ok = xs_try(bar, par)))
+            if (clock64() - t0 > 4000000000LL) break;
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        unsigned int mx = 0u;
+        for (int e = lane; e < C * E; e += 32) mx = max(mx, sl[e]);
+        for (int o = E; o < 32; o <<= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane < E) xred[lane] = mx;
+        if (lane == 0 && !ok) *xfail = 1u;
+      } else if constexpr (kGrid) {
         if (lane < E && v > 0.f) atomicMax(tk.xslot + (size_t)(t % 3) * E + lane, __float_as_uint(v));
       } else {
         unsigned int* slot = red + (size_t)(t % 3) * E;
@@ -618,12 +726,18 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
       // the slot into this CTA's table (read below like the cluster slot)
       if (tid < 2 * M) red[(size_t)(t % 3) * M * 2 + tid] = ld_relaxed_gpu(tk.xslot + (size_t)(t % 3) * M * 2 + tid);
       __syncthreads();
+    } else if constexpr (kAsync) {
+      __syncthreads();
+      if (*xfail) {
+        if (tid == 0) atomicOr(P.dstatus, kStatTimeout);
+        break;
+      }
     } else {
       cluster.sync();
     }
     // ---- 4. decisions (every thread, same data, same result)
     {
-      const unsigned int* slot = red + (size_t)(t % 3) * M * 2;
+      const unsigned int* slot = kAsync ? xred : red + (size_t)(t % 3) * M * 2;
       int anyd = 0;
       all_done = 1;
 #pragma unroll
