@@ -40,7 +40,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # moves bytes in proportion to n (scaled to the full n below). Set to None
 # whenever the kernel changes, until it is captured again.
 NCU_DRAM_BYTES = {"oem_iter_kernel": 1.387776e6,
-                  "gram_tma_kernel_per_row": (420.133376e6 + 71.973632e6) / 200_000}
+                  "gram_tma_kernel_per_row": (419.602176e6 + 71.923456e6) / 200_000}
 
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 WORKLOAD = "four_penalties_f32_n1e6_p500"
@@ -389,9 +389,12 @@ def run_ours(args, w, rank, world, local_rank):
     g_ms_launch = g_ms / max(1, args.steps)
     g_flops = w.n * (p + 1) * (p + 2)
     g_tf = g_flops / (g_ms_launch / 1000.0) / 1e12
-    nprod = 4 if args.gram_mode in ("auto", "split_bf16") else 1
+    # MMA work: split mode takes four products on the nt diagonal tiles and
+    # three on the nt (nt - 1) / 2 others; other modes one product per tile
     nt = math.ceil((p + 1) / 128)
-    mma_flops = 2.0 * (nt * (nt + 1) / 2) * 128 * 128 * w.n * nprod
+    split = args.gram_mode in ("auto", "split_bf16")
+    tile_products = (4 * nt + 3 * nt * (nt - 1) / 2) if split else nt * (nt + 1) / 2
+    mma_flops = 2.0 * tile_products * 128 * 128 * w.n
     bf16 = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
     step_ms = ms / args.steps
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
@@ -595,7 +598,7 @@ def main():
                     help="rows per oracle step of the CPU baseline (time scaled to n)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="CPU baseline: repeat oracle steps until this much CPU work")
-    ap.add_argument("--serving-requests", type=int, default=200,
+    ap.add_argument("--serving-requests", type=int, default=2000,
                     help="requests of the serving measurement added to the default line (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -15,10 +15,11 @@
 //      128-byte swizzle, the layout the tensor core reads as MN-major
 //      bfloat16); one thread issues tcgen05.mma: hi.hi into a double-buffered
 //      float32 accumulator in tensor memory, and in split mode the cross terms
-//      hi.lo + lo.hi + lo.lo, 2^-8 smaller, into a second accumulator that is
-//      emptied every 1,024 rows. Eight epilogue warps add each finished window
-//      into a running TwoSum pair per element — hi in a register, lo in
-//      tensor memory — and write hi + lo as float64 at the end of the item.
+//      hi.lo + lo.hi (+ lo.lo on diagonal tiles), 2^-8 smaller, into a
+//      second accumulator that is emptied every 1,024 rows. Eight epilogue
+//      warps add each finished window into a running TwoSum pair per
+//      element — hi in a register, lo in tensor memory — and write hi + lo as
+//      float64 at the end of the item.
 // Every mbarrier wait is bounded; on expiry the kernel records a timeout in
 // the status word, drains its MMAs, frees tensor memory and returns.
 #include "tcgen05.cuh"
@@ -40,7 +41,7 @@ constexpr int kTEpiCols = 64;           // columns per epilogue thread
 constexpr int kTCrossStages = 32;       // cross-term window (1,024 rows)
 
 // Tensor-memory columns: the hi.hi accumulator (two buffers), in split mode
-// the cross-term accumulator hi.lo + lo.hi + lo.lo (one buffer), and the lo
+// the cross-term accumulator hi.lo + lo.hi (+ lo.lo) (one buffer), and the lo
 // half of each element's running TwoSum pair (its hi half is a register).
 constexpr uint32_t kTD1 = 0, kTD2 = 256, kTLo = 384;
 
@@ -201,6 +202,11 @@ __global__ void __launch_bounds__(kTThreads, 1)
         int ti, tj;
         tile_coords(tile, a.ntile1, &ti, &tj);
         const uint32_t joff = ti == tj ? 0u : 16384u;
+        // lo.lo only on diagonal tiles: there lo_i^2 > 0 would bias G_ii by
+        // ~2^-18 / 3; off the diagonal lo_i lo_j has zero mean and is 2^-16
+        // of the cross terms, so those tiles take the three products
+        // hi.hi, hi.lo, lo.hi
+        const bool lolo = ti == tj;
         const int nst = (int)((a.pc.row1[chunk] - a.pc.row0[chunk]) / kRS);
         bool d2_fresh = true;
         for (int st0 = 0; st0 < nst && ok; st0 += flush_stages, ++v1) {
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
               if (split) {
                 mma_f16(d2, ihi + kof, jlo + kof, idesc, d2_fresh ? 0u : 1u);
                 mma_f16(d2, ilo + kof, jhi + kof, idesc, 1u);
-                mma_f16(d2, ilo + kof, jlo + kof, idesc, 1u);
+                if (lolo) mma_f16(d2, ilo + kof, jlo + kof, idesc, 1u);
                 d2_fresh = false;
               }
             }
