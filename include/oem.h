@@ -27,6 +27,16 @@
  *     `stream` has reached that point. With X in device memory, y and fold
  *     must be in device memory too (OEM_EINVAL otherwise). oem_fit_logistic
  *     takes device memory only.
+ *   - CUDA graphs: oem_gram, oem_fold_grams, oem_spectral_d, oem_fit_path,
+ *     oem_fit and oem_cv (X in device memory) may be captured into a graph
+ *     once the same call has run outside the capture on the same context:
+ *     that call sizes the context's workspace, which cannot grow inside a
+ *     capture (OEM_EINVAL), and fixes the autotuned layout (the autotuner
+ *     does not run inside a capture). Host data a call uploads (penalty and
+ *     task tables, user lambdas, d) travel inside the captured launches, so
+ *     the graph replays the call on whatever the device buffers hold.
+ *     oem_fit_logistic (a host loop over outer steps) and the server are not
+ *     capturable.
  *   - Matrices are row-major (C order). X is n x p with leading dimension
  *     ldx >= p (elements); ldx * sizeof(element) must be a multiple of 16 and
  *     X, y must be 16-byte aligned, else OEM_EINVAL.

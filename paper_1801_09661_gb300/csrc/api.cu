@@ -6,6 +6,25 @@ using namespace oem::host;
 
 
 namespace oem {
+
+constexpr int kUpChunk = 3840;  // bytes per upload kernel (parameters stay under 4 KB)
+struct UpChunk {
+  unsigned char b[kUpChunk];
+};
+__global__ void upload_kernel(unsigned char* dst, UpChunk c, int nbytes) {
+  for (int i = threadIdx.x; i < nbytes; i += blockDim.x) dst[i] = c.b[i];
+}
+cudaError_t launch_upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  for (size_t o = 0; o < bytes; o += kUpChunk) {
+    UpChunk c;
+    const int nb = (int)std::min<size_t>(kUpChunk, bytes - o);
+    memcpy(c.b, (const unsigned char*)src + o, (size_t)nb);
+    upload_kernel<<<1, 256, 0, s>>>((unsigned char*)dst + o, c, nb);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 cudaError_t launch_convert_g(const double* G64, int64_t p, int B, float* G32, int ldg32, cudaStream_t s);
 }
 
@@ -39,6 +58,9 @@ int oem_create(oem_ctx** out, int device, size_t budget) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->dstatus, sizeof(unsigned) * 4);
   if (e == cudaSuccess) e = cudaMemset(ctx->dstatus, 0, sizeof(unsigned) * 4);
+  // load the upload kernel now: its first use may be inside a stream capture
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, oem::upload_kernel);
   if (e != cudaSuccess) {
     cudaGetLastError();
     delete ctx;
@@ -121,8 +143,10 @@ int oem_sync(oem_ctx* ctx, void* stream) {
 // (y and fold may then live on either side); with X on the device, y and fold
 // must be on the device too.
 static int plan_residence(oem_ctx* ctx, const void* X, const void* y, const uint8_t* fold, int64_t n,
-                          int64_t ldx, int32_t xtype, StreamBufs& sb, int64_t* rows) {
+                          int64_t ldx, int32_t xtype, StreamBufs& sb, int64_t* rows, cudaStream_t s) {
   sb.on = host_resident(X);
+  if (sb.on && capturing(s))
+    return fail(ctx, OEM_EINVAL, "X in host memory cannot be streamed inside a stream capture");
   if (!sb.on) {
     if (host_resident(y) || (fold && host_resident(fold)))
       return fail(ctx, OEM_EINVAL, "y and fold must be in device memory when X is");
@@ -148,7 +172,7 @@ int oem_gram(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, i
   CU(cudaSetDevice(ctx->device));
   StreamBufs sb;
   int64_t rows;
-  if ((r = plan_residence(ctx, X, y, nullptr, n, ldx, xtype, sb, &rows))) return r;
+  if ((r = plan_residence(ctx, X, y, nullptr, n, ldx, xtype, sb, &rows, s))) return r;
   GramPlan g = plan_gram(ctx, rows, p, 1, m, false);
   GramBufs b;
   Arena A;
@@ -178,7 +202,7 @@ int oem_fold_grams(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_
   CU(cudaSetDevice(ctx->device));
   StreamBufs sb;
   int64_t rows;
-  if ((r = plan_residence(ctx, X, y, fold, n, ldx, xtype, sb, &rows))) return r;
+  if ((r = plan_residence(ctx, X, y, fold, n, ldx, xtype, sb, &rows, s))) return r;
   GramPlan g = plan_gram(ctx, rows, p, K, m, true);
   GramBufs b;
   Arena A;
@@ -220,7 +244,7 @@ static int fit_tail(oem_ctx* ctx, int64_t p, int B, const double* G64, const flo
   int r;
   if ((r = pens_upload(ctx, P, s))) return r;
   if (o->lambdas) {
-    CU(cudaMemcpyAsync(lam, o->lambdas, sizeof(double) * P.npen * o->nlambda, cudaMemcpyHostToDevice, s));
+    CU(upload(lam, o->lambdas, sizeof(double) * P.npen * o->nlambda, s));
   } else {
     LAUNCH(OEM_PROF_LAMBDA, launch_lambda_grid(c, (int)p, P.dpens, P.npen, o->nlambda, o->lambda_min_ratio, lam, s));
   }
@@ -268,7 +292,7 @@ int oem_fit_path(oem_ctx* ctx, const double* G, const double* c, int64_t p, doub
   if ((r = arena_commit(ctx, A, s))) return r;
   if (G32) LAUNCH(OEM_PROF_ASSEMBLE, launch_convert_g(G, p, 1, G32, ldg32, s));
   if (d > 0.0) {
-    CU(cudaMemcpyAsync(dd, &d, sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(upload(dd, &d, sizeof(double), s));
   } else {
     cudaError_t e = lanczos_prof(ctx, s, G, p, p, 1, p * p, opt->lanczos_steps, w, dd, s, &ctx->launches);
     if (e != cudaSuccess) return fail(ctx, OEM_ECUDA, "Lanczos launch failed: %s", cudaGetErrorString(e));
@@ -298,7 +322,7 @@ int oem_fit(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, in
   const bool centre = opt->intercept || opt->standardize;
   StreamBufs sb;
   int64_t rows;
-  if ((r = plan_residence(ctx, X, y, nullptr, n, ldx, xtype, sb, &rows))) return r;
+  if ((r = plan_residence(ctx, X, y, nullptr, n, ldx, xtype, sb, &rows, s))) return r;
   GramPlan g = plan_gram(ctx, rows, p, 1, m, false, opt->intercept ? kOnesShifted : 0);
   GramBufs b;
   double *G64 = nullptr, *c = nullptr, *N = nullptr, *cnt = nullptr, *dd = nullptr, *cen = nullptr;
@@ -371,7 +395,7 @@ int oem_cv(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, int
   const bool centre = opt->intercept || opt->standardize;
   StreamBufs sb;
   int64_t rows;
-  if ((r = plan_residence(ctx, X, y, fold, n, ldx, xtype, sb, &rows))) return r;
+  if ((r = plan_residence(ctx, X, y, fold, n, ldx, xtype, sb, &rows, s))) return r;
   GramPlan g = plan_gram(ctx, rows, p, K, m, true, opt->intercept ? kOnesShifted : 0);
   GramBufs b;
   double *G64 = nullptr, *c = nullptr, *N = nullptr, *cnt = nullptr, *dd = nullptr;
@@ -526,7 +550,7 @@ int oem_fit_logistic(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int6
   LAUNCH(OEM_PROF_CHUNKS, launch_logit_null(bcur, npen, (int)pq, (int)pq, icpt, b.Zg, g.q, (int)p, g.ycols, ocol, n, s));
   LAUNCH(OEM_PROF_LOGIT, launch_logit_grad(la, npen, grid, s));
   if (opt->lambdas) {
-    CU(cudaMemcpyAsync(lam, opt->lambdas, sizeof(double) * npen * L, cudaMemcpyHostToDevice, s));
+    CU(upload(lam, opt->lambdas, sizeof(double) * npen * L, s));
   } else {
     LAUNCH(OEM_PROF_LAMBDA, launch_lambda_grid(gv, (int)p, P.dpens, npen, L, opt->lambda_min_ratio, lam, s));
   }

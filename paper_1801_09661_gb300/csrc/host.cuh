@@ -60,6 +60,25 @@ inline int fail(oem_ctx* ctx, int code, const char* fmt, ...) {
       return fail(ctx, OEM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
   } while (0)
 
+// Whether `s` is being captured into a CUDA graph.
+inline bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+// Host data to device memory, ordered on `s`: cudaMemcpyAsync, or inside a
+// stream capture kernels that carry the bytes (the host buffer may be gone
+// by the time the graph is replayed).
+inline cudaError_t upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (!bytes) return cudaSuccess;
+  if (capturing(s)) return launch_upload(dst, src, bytes, s);
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+}
+
 inline cudaEvent_t prof_event(oem_ctx* ctx) {
   if (!ctx->ev_pool.empty()) {
     cudaEvent_t e = ctx->ev_pool.back();
@@ -79,7 +98,8 @@ struct ProfScope {
   int64_t n;
   cudaEvent_t e0 = nullptr;
   ProfScope(oem_ctx* c, cudaStream_t st, int k, int64_t cnt) : ctx(c), s(st), cls(k), n(cnt) {
-    if (ctx->prof && (e0 = prof_event(ctx))) cudaEventRecord(e0, s);
+    // no timing inside a stream capture (its events are never recorded)
+    if (ctx->prof && !capturing(s) && (e0 = prof_event(ctx))) cudaEventRecord(e0, s);
   }
   ~ProfScope() {
     if (!e0) return;
@@ -164,6 +184,10 @@ inline int arena_commit(oem_ctx* ctx, Arena& A, cudaStream_t s) {
     return fail(ctx, OEM_EBUDGET, "workspace of %zu bytes exceeds the budget of %zu bytes", need,
                 ctx->budget);
   if (need > ctx->arena_cap) {
+    if (capturing(s))
+      return fail(ctx, OEM_EINVAL,
+                  "inside a stream capture the workspace cannot grow to %zu bytes: make the same call "
+                  "once outside the capture first", need);
     if (ctx->arena) CU(cudaFreeAsync(ctx->arena, ctx->arena_stream ? ctx->arena_stream : s));
     ctx->arena = nullptr;
     ctx->arena_cap = 0;
@@ -631,19 +655,19 @@ inline int pens_upload(oem_ctx* ctx, PenPlan& P, cudaStream_t s) {
   for (int i = 0; i < P.npen; ++i) {
     DevPenalty& d = P.host[i];
     if (!P.w64[i].empty()) {
-      CU(cudaMemcpyAsync(P.d_w64[i], P.w64[i].data(), P.w64[i].size() * 8, cudaMemcpyHostToDevice, s));
-      CU(cudaMemcpyAsync(P.d_w32[i], P.w32[i].data(), P.w32[i].size() * 4, cudaMemcpyHostToDevice, s));
+      CU(upload(P.d_w64[i], P.w64[i].data(), P.w64[i].size() * 8, s));
+      CU(upload(P.d_w32[i], P.w32[i].data(), P.w32[i].size() * 4, s));
       d.w64 = P.d_w64[i];
       d.w32 = P.d_w32[i];
     }
     if (!P.grp[i].empty()) {
-      CU(cudaMemcpyAsync(P.d_grp[i], P.grp[i].data(), P.grp[i].size() * 4, cudaMemcpyHostToDevice, s));
-      CU(cudaMemcpyAsync(P.d_cg[i], P.cg[i].data(), P.cg[i].size() * 8, cudaMemcpyHostToDevice, s));
+      CU(upload(P.d_grp[i], P.grp[i].data(), P.grp[i].size() * 4, s));
+      CU(upload(P.d_cg[i], P.cg[i].data(), P.cg[i].size() * 8, s));
       d.grp = P.d_grp[i];
       d.cg = P.d_cg[i];
     }
   }
-  CU(cudaMemcpyAsync(P.dpens, P.host.data(), sizeof(DevPenalty) * P.npen, cudaMemcpyHostToDevice, s));
+  CU(upload(P.dpens, P.host.data(), sizeof(DevPenalty) * P.npen, s));
   return OEM_OK;
 }
 
@@ -873,10 +897,9 @@ inline int launch_iter_layout(oem_ctx* ctx, int64_t p, int B, const float* G32, 
     if ((int)I.gslice.size() > I.gslice_cap || tasks.size() * I.xbuf_task == 0)
       return fail(ctx, OEM_ECUDA, "grid mode buffers too small");
     CU(cudaMemsetAsync(I.d_xbuf, 0, tasks.size() * I.xbuf_task, s));
-    CU(cudaMemcpyAsync(I.d_gslice, I.gslice.data(), sizeof(int32_t) * I.gslice.size(),
-                       cudaMemcpyHostToDevice, s));
+    CU(upload(I.d_gslice, I.gslice.data(), sizeof(int32_t) * I.gslice.size(), s));
   }
-  CU(cudaMemcpyAsync(I.d_tasks, tasks.data(), sizeof(IterTask) * tasks.size(), cudaMemcpyHostToDevice, s));
+  CU(upload(I.d_tasks, tasks.data(), sizeof(IterTask) * tasks.size(), s));
   IterLaunch Lc{};
   Lc.tasks = I.d_tasks; Lc.ntasks = (int)tasks.size(); Lc.C = I.C; Lc.M = I.M;
   Lc.precision = o->iter_precision;
@@ -953,7 +976,7 @@ inline int run_iter(oem_ctx* ctx, int64_t p, int B, const float* G32, int ldg, c
              cudaStream_t s) {
   if (I.groups) {
     std::vector<uint8_t> al(P.allowed.begin(), P.allowed.end());
-    CU(cudaMemcpyAsync(I.d_allowed, al.data(), al.size(), cudaMemcpyHostToDevice, s));
+    CU(upload(I.d_allowed, al.data(), al.size(), s));
   }
   if (I.tune) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

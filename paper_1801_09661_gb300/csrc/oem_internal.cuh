@@ -131,6 +131,11 @@ cudaError_t launch_col_shift(const void* X, int32_t xtype, int64_t n, int64_t p,
                              const void* y, float* shift, cudaStream_t s);
 // Streamed Gram pass: acc (+)= blk ([len] float64, K fold Grams of Z) and
 // the fold row counts from the block's sorted offsets; then the offsets.
+// Copy `bytes` of host memory to device memory by kernels that carry the
+// bytes in their launch parameters, so that a stream capture records the
+// data itself (a captured cudaMemcpyAsync would read the host buffer again
+// at every replay).
+cudaError_t launch_upload(void* dst, const void* src, size_t bytes, cudaStream_t s);
 cudaError_t launch_zg_accumulate(double* acc, const double* blk, int64_t len, int first, int64_t* cnt,
                                  const int64_t* fold_off, int K, cudaStream_t s);
 cudaError_t launch_zg_offsets(const int64_t* cnt, int64_t* off, int K, int require_nonempty, unsigned* dstatus,
