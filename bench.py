@@ -175,6 +175,19 @@ def cpu_cores():
     return os.cpu_count() or 1
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
+
+
 def run_reference(args, w, rank, world):
     if rank != 0:
         return 0
@@ -197,7 +210,7 @@ def run_reference(args, w, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "n": w.n, "p": w.p, "penalties": list(w.penalties),
                    "nlambda": w.nlambda, "tol": w.tol},
-        "cpu_baseline": {"value": value, "unit": "paths/s", "cores": cpu_cores(),
+        "cpu_baseline": {"value": value, "unit": "paths/s", "cores": cpu_cores(), "cpu_model": cpu_model(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -456,7 +469,7 @@ def run_ours(args, w, rank, world, local_rank):
             tot_raw += raw
             reps += 1
         line["cpu_baseline"] = {
-            "value": npen * reps / tot_scaled, "unit": "paths/s", "cores": cpu_cores(), "kind": "oracle",
+            "value": npen * reps / tot_scaled, "unit": "paths/s", "cores": cpu_cores(), "cpu_model": cpu_model(), "kind": "oracle",
             "sample": (f"{reps} oracle steps, each the Gram of {n_sample} of {w.n} rows"
                        + (f" (time scaled by n/{n_sample})" if n_sample < w.n else "")
                        + f", d and {npen} x {w.nlambda}-lambda paths; {tot_raw:.1f} s of CPU work")}
