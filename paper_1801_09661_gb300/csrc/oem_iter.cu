@@ -635,18 +635,18 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
             }
           }
         } else {
-        for (int e = lane; e < nu * CC; e += 32) {
-          const int u = u0 + e / CC, r = e % CC;
-          float* dst = (kGrid ? Dn : cluster.map_shared_rank(Dn, r)) + ((u ^ ((u >> 3) & (M - 1))) << 2);
-          const float* src = st + (4 * u - i0 * M);
-          if (4 * u >= f0 && 4 * u + 4 <= f1) {
-            *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(src);
-          } else {
+          for (int e = lane; e < nu * CC; e += 32) {
+            const int u = u0 + e / CC, r = e % CC;
+            float* dst = (kGrid ? Dn : cluster.map_shared_rank(Dn, r)) + ((u ^ ((u >> 3) & (M - 1))) << 2);
+            const float* src = st + (4 * u - i0 * M);
+            if (4 * u >= f0 && 4 * u + 4 <= f1) {
+              *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(src);
+            } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-              if (4 * u + q >= f0 && 4 * u + q < f1) dst[q] = src[q];
+              for (int q = 0; q < 4; ++q)
+                if (4 * u + q >= f0 && 4 * u + q < f1) dst[q] = src[q];
+            }
           }
-        }
         }
       } else if constexpr (kGrid) {
         T* Dn = xD + (size_t)nxt * ldgs * M;
