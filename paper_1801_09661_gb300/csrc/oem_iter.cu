@@ -15,9 +15,11 @@
 // iteration a warp, on its own rows and with no block-wide barrier:
 //   1. forms (G dbeta)_i for all instances of the task at once, 16 / M rows
 //      at a time so that one pass over dbeta serves the group (lane l reads
-//      columns l, l + 32, ...; G rows resident in shared memory, the rest read
-//      from L2); a reduce-scatter leaves each (row, instance) sum in one lane
-//      pair, which updates u_i and, without groups, applies the threshold;
+//      columns 4l .. 4l+3, + 128, ...; G rows in registers when a warp has
+//      one row group and p <= 512, else resident in shared memory, the rest
+//      read from L2); a reduce-scatter leaves each (row, instance) sum in one
+//      lane pair, which updates u_i and, without groups, applies the
+//      threshold;
 //   2. for group penalties, forms the group norms and thresholds afterwards;
 //   3. writes its dbeta rows into the shared memory of every CTA of the
 //      cluster and its max|dbeta|, max|beta| per instance into the block's
@@ -398,6 +400,30 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   const bool my_inst = kq < m;
 
   const T tol = (T)P.tol;
+  // Float32 with one row group per warp and p <= 512: the warp's G rows live
+  // in registers (lane l holds columns 4l .. 4l+3 + 128 s of each row), so the
+  // mat-vec reads only dbeta from shared memory. Same products in the same
+  // order as from shared memory.
+  constexpr int kGS = 4;                          // column steps of 128
+  constexpr bool kGregT = kF32 && RG <= 4;        // register budget: RG * kGS float4
+  const bool greg_on = kGregT && (whi - wlo) <= RG && p <= 128 * kGS;
+  float4 greg[kGregT ? RG : 1][kGregT ? kGS : 1];
+  if constexpr (kGregT) {
+#pragma unroll
+    for (int r = 0; r < RG; ++r)
+#pragma unroll
+      for (int sx = 0; sx < kGS; ++sx) {
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int j4 = lane * 4 + 128 * sx;
+        if (greg_on && r < whi - wlo && j4 < p) {
+          const int ib = wlo + r;
+          const float* rowp = reinterpret_cast<const float*>(
+              ib < smem_rows ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg);
+          g = *reinterpret_cast<const float4*>(rowp + j4);
+        }
+        greg[r][sx] = g;
+      }
+  }
   int skip_mv = 1;      // dbeta of the previous iteration is all zero
   int all_done = 1;
   for (int k = 0; k < m; ++k) all_done &= done[k];
@@ -463,8 +489,36 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
               }
             }
           };
-          if (gb + nv <= smem_rows) matvec([&](int r) { return g0 + (size_t)r * ldgs; });
-          else matvec([&](int r) { return gr[r]; });
+          if (kGregT && greg_on) {
+#pragma unroll
+            for (int sx = 0; sx < kGS; ++sx) {
+              const int j4 = lane * 4 + 128 * sx;
+              if (j4 < p) {
+                float dv[4][M];
+#pragma unroll
+                for (int q = 0; q < M; ++q) {
+                  const int u = (j4 * M >> 2) + q;
+                  const float4 t = *reinterpret_cast<const float4*>(Dc + ((u ^ ((u >> 3) & (M - 1))) << 2));
+                  const float tv[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                  for (int e = 0; e < 4; ++e) dv[(q * 4 + e) / M][(q * 4 + e) % M] = tv[e];
+                }
+#pragma unroll
+                for (int r = 0; r < RG; ++r) {
+                  const float4 g4 = greg[kGregT ? r : 0][kGregT ? sx : 0];
+                  const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+                  for (int c = 0; c < 4; ++c)
+#pragma unroll
+                    for (int k = 0; k < M; ++k) acc[r * M + k] = fma(gv[c], dv[c][k], acc[r * M + k]);
+                }
+              }
+            }
+          } else if (gb + nv <= smem_rows) {
+            matvec([&](int r) { return g0 + (size_t)r * ldgs; });
+          } else {
+            matvec([&](int r) { return gr[r]; });
+          }
         } else {
 #pragma unroll 4
           for (int j = lane; j < p; j += 32) {
