@@ -171,6 +171,22 @@ def oracle_step(w, n_sample: int, seed_shift: int = 0):
     return t_gram * (w.n / n_sample) + t_rest, t_gram + t_rest
 
 
+def max_over_ranks(ms: float, world: int, device="cpu") -> float:
+    """The slowest rank's time for the timed region (every rank leaves it at
+    the same barrier; the job is as fast as its last rank)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(paths_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job paths/s: the paths of every rank over the slowest rank's time."""
+    return paths_per_rank * world / (ms / 1000.0)
+
+
 def cpu_cores():
     return os.cpu_count() or 1
 
@@ -278,10 +294,7 @@ def run_ours(args, w, rank, world, local_rank):
     ctx.profile(False)
     clk = clocks.stop()
     status = ctx.sync()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     its_h = its.cpu().numpy().astype(np.int64)
     conv_h = conv.cpu().numpy()
     loops = int(its_h.sum(axis=1).max())
@@ -331,10 +344,7 @@ def run_ours(args, w, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     ms_e2e = f0.elapsed_time(f1)
-    if world > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(ms_e2e, world, dev)
     h2d = Xh.numel() * Xh.element_size() + yh.numel() * yh.element_size()
     d2h = sum(t.numel() * t.element_size() for t in (bh, lh, ih, ch))
 
@@ -385,8 +395,7 @@ def run_ours(args, w, rank, world, local_rank):
         ctx.close()
         return 0
     peaks, peak_src = load_peaks()
-    total_paths = npen * args.steps * world
-    value = total_paths / (ms / 1000.0)
+    value = job_throughput(npen * args.steps, world, ms)
     # roofline: the OEM iteration kernel (dominant) against HBM
     p = w.p
     it_ms, it_n = prof.get("oem_iter_kernel", (float("nan"), 0))
@@ -423,7 +432,7 @@ def run_ours(args, w, rank, world, local_rank):
                    "gram_mode": args.gram_mode, "x_dtype": w.dtype,
                    "l2": "inputs larger than L2 (X is %.2f GB)" % (X.nbytes / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
-        "e2e": {"value": npen * args.steps * world / (ms_e2e / 1000.0), "unit": "paths/s",
+        "e2e": {"value": job_throughput(npen * args.steps, world, ms_e2e), "unit": "paths/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "streamed": streamed,
