@@ -408,6 +408,21 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   constexpr bool kGregT = kF32 && RG <= 4;        // register budget: RG * kGS float4
   const bool greg_on = kGregT && (whi - wlo) <= RG && p <= 128 * kGS;
   float4 greg[kGregT ? RG : 1][kGregT ? kGS : 1];
+  // With one row group per warp and scalar penalties, the lane that owns row
+  // wlo + rsub of instance kq keeps u (hi, lo), beta, w and its last dbeta
+  // in registers for the whole launch (beta is still stored for the outputs,
+  // u written back at the end); the same values as in shared memory.
+  const bool regst = kF32 && greg_on && !has_group;
+  const int i_own = wlo + rsub;
+  const bool own = even && i_own < whi;
+  T r_uhi = T(0), r_ulo = T(0), r_bet = T(0), r_w = T(1), r_dn = T(0);
+  if (regst && own) {
+    const int idx = kq * maxR + i_own;
+    r_uhi = uhi[idx];
+    r_ulo = ulo[idx];
+    r_bet = bet[idx];
+    r_w = wv[idx];
+  }
   if constexpr (kGregT) {
 #pragma unroll
     for (int r = 0; r < RG; ++r)
@@ -535,7 +550,37 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
         y = reduce_scatter<V>(acc, lane);
       }
       const int i = gb + rsub;  // this lane's row (local index)
-      if (even && i < whi) {
+      if (regst) {
+        if (own) {
+          if (my_inst && !skip_mv) {
+            const T incr = fma(my_d, r_dn, -y);
+            if (incr != T(0)) {
+              const T h = r_uhi;
+              const T s1 = h + incr, bb = s1 - h;
+              const T e = (h - (s1 - bb)) + (incr - bb);
+              const T lo = r_ulo + e;
+              const T hi2 = s1 + lo;
+              r_ulo = lo - (hi2 - s1);
+              r_uhi = hi2;
+            }
+          }
+          T dn = T(0);
+          if (my_inst) {
+            if (!my_done) {
+              const T bn = thr_scalar<T>(my_kind, r_uhi, r_w * my_lam, my_alpha, my_gamma, my_d);
+              dn = bn - r_bet;
+              r_bet = bn;
+              bet[kq * maxR + i] = bn;
+              lmd = fmax(lmd, fabs(dn));
+              lmb = fmax(lmb, fabs(bn));
+            } else {
+              lmb = fmax(lmb, fabs(r_bet));
+            }
+          }
+          st[(size_t)i * M + kq] = dn;
+          r_dn = dn;
+        }
+      } else if (even && i < whi) {
         const int idx = kq * maxR + i;
         if (my_inst && !skip_mv) {
           const T incr = fma(my_d, Dc[dpos<T, M>(i0 + i, kq)], -y);
@@ -831,6 +876,11 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
     ++loops;
     if (P.max_loops > 0 && loops >= P.max_loops) break;
   }
+  if (regst && own) {
+    uhi[kq * maxR + i_own] = r_uhi;
+    ulo[kq * maxR + i_own] = r_ulo;
+  }
+  __syncwarp();
   // ---- save the state for a later launch (serving): apply the pending dbeta
   if (tk.st_u) {
     if (!all_done && !skip_mv) {
