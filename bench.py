@@ -256,6 +256,11 @@ def run_ours(args, w, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     opts = dict(nlambda=w.nlambda, lambda_min_ratio=w.lambda_min_ratio, tol=w.tol,
                 gram_mode=args.gram_mode)
+    if args.cluster_ctas or args.instances_per_task:
+        # a fixed iteration layout (no autotuning), e.g. for a profiler run,
+        # where the autotuner's timing trials would be distorted
+        opts.update(cluster_ctas=args.cluster_ctas, instances_per_task=args.instances_per_task,
+                    autotune=False)
     beta, lam, its, conv = (torch.empty((npen, w.nlambda, w.p), dtype=torch.float64, device=dev),
                             torch.empty((npen, w.nlambda), dtype=torch.float64, device=dev),
                             torch.empty((npen, w.nlambda), dtype=torch.int32, device=dev),
@@ -430,6 +435,9 @@ def run_ours(args, w, rank, world, local_rank):
         "config": {"workload": w.name, "n": w.n, "p": p, "penalties": list(w.penalties),
                    "nlambda": w.nlambda, "lambda_min_ratio": w.lambda_min_ratio, "tol": w.tol,
                    "gram_mode": args.gram_mode, "x_dtype": w.dtype,
+                   "iteration_layout": ({"cluster_ctas": args.cluster_ctas,
+                                         "instances_per_task": args.instances_per_task}
+                                        if args.cluster_ctas or args.instances_per_task else "autotuned"),
                    "l2": "inputs larger than L2 (X is %.2f GB)" % (X.nbytes / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": job_throughput(npen * args.steps, world, ms_e2e), "unit": "paths/s",
@@ -614,6 +622,10 @@ def main():
                     help="serving: requests in the batched-vs-plain comparison")
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--iters-per-round", type=int, default=1000)
+    ap.add_argument("--cluster-ctas", type=int, default=0,
+                    help="iteration layout: CTAs per task (0: autotuned)")
+    ap.add_argument("--instances-per-task", type=int, default=0,
+                    help="iteration layout: penalty paths per task (0: autotuned)")
     ap.add_argument("--gram-mode", default="auto",
                     choices=["auto", "split_bf16", "tf32", "fp32", "fp64", "bf16"])
     ap.add_argument("--cpu-sample-rows", type=int, default=1_000_000,
