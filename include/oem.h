@@ -92,7 +92,9 @@ enum { OEM_F64 = 0, OEM_F32 = 1, OEM_BF16 = 2 };
  *                products; the float32 y is carried exactly as three bfloat16
  *                columns hi + mid + lo).
  *   SPLIT_BF16 : tcgen05 kind::f16, X float32 split as hi + lo bfloat16,
- *                products hi*hi + hi*lo + lo*hi + lo*lo (X float32).
+ *                products hi*hi + hi*lo + lo*hi, plus lo*lo on the diagonal
+ *                128 x 128 tiles (where lo_i^2 would otherwise bias G_ii)
+ *                (X float32).
  *   AUTO       : SPLIT_BF16 for float32, BF16 for bfloat16, FP64 for float64. */
 enum {
   OEM_GRAM_FP64 = 0,
