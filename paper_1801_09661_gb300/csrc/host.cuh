@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <vector>
@@ -38,6 +39,10 @@ struct oem_ctx {
   // groups): CTAs per task, instances per task, grid mode
   std::map<std::array<int64_t, 5>, std::array<int, 3>> iter_tuned;
   int64_t tune_runs = 0;
+  // iteration counts of the last oem_fit_path / oem_fit / oem_cv call (device
+  // [B][npen][L], in the workspace until the next call), for oem_iter_stats
+  const int32_t* last_iters = nullptr;
+  int last_B = 0, last_npen = 0, last_L = 0;
 };
 
 namespace oem {
@@ -713,6 +718,42 @@ inline void make_slices(int64_t p, int C, const std::vector<char>& allowed, int3
   *max_rows = mr;
 }
 
+// Even row slices for the replicated kernel (no group alignment: every CTA
+// holds all rows for the thresholds). align = 4 in cluster mode (16-byte
+// units of the exchanged words), 1 in grid mode.
+inline void make_slices_even(int64_t p, int C, int align, int32_t* slice, int* max_rows) {
+  slice[0] = 0;
+  for (int r = 1; r < C; ++r) {
+    int64_t bnd = (p * r) / C;
+    bnd = (bnd + align - 1) / align * align;
+    slice[r] = (int32_t)std::min<int64_t>(std::max<int64_t>(bnd, slice[r - 1]), p);
+  }
+  slice[C] = (int32_t)p;
+  int mr = 1;
+  for (int r = 0; r < C; ++r) mr = std::max(mr, slice[r + 1] - slice[r]);
+  *max_rows = mr;
+}
+
+// Which iteration kernel serves order p: the replicated one (oem_iter.cu)
+// up to kIterRepMaxP, the row-owned one (oem_iter_rows.cu) beyond.
+inline bool iter_rows_kernel(int64_t p) { return p > kIterRepMaxP; }
+
+// Bound of every device wait of the iteration kernels, in clock cycles
+// (about 2 s at 2 GHz). OEM_DEVICE_WAIT_CYCLES overrides it (tests of the
+// timeout path).
+inline int64_t iter_wait_cycles() {
+  const char* v = std::getenv("OEM_DEVICE_WAIT_CYCLES");
+  if (v && *v) {
+    const long long c = std::atoll(v);
+    if (c > 0) return c;
+  }
+  return 4000000000LL;
+}
+
+inline int iter_smem_probe(const IterLaunch& P, bool rows) {
+  return rows ? oem_iter_rows_max_cluster(P) : oem_iter_max_cluster(P);
+}
+
 constexpr size_t kIterSmemCap = 227 * 1024;
 
 // Iteration launch plan for B tasks of the same shape (a fit or the K+1
@@ -722,6 +763,7 @@ struct IterPlan {
   size_t smem = 0;
   int32_t slice[kMaxCluster + 1] = {0};
   bool grid = false;      // cooperative grid mode (C CTAs per task, any C)
+  bool rows = false;      // row-owned kernel (p > kIterRepMaxP)
   std::vector<int32_t> gslice;  // grid mode: C + 1 row boundaries
   bool groups = false;
   bool tune = false;      // time the candidate layouts at the first run
@@ -736,9 +778,13 @@ struct IterPlan {
   int gslice_cap = 0;     // boundaries per task
 };
 
+// Grid-mode exchange space of one task, the larger of the two kernels'
+// needs (row-owned: dbeta buffers, maxima slots, barrier words; replicated:
+// tagged words of G dbeta).
 inline size_t grid_xbuf_task_bytes(int64_t p) {
   const size_t ldgs = (size_t)((p + 3) & ~3LL);
-  return ((2 * ldgs * 8 * sizeof(double) + 3 * 16 * 4 + 2 * 4) + 255) & ~(size_t)255;
+  const size_t rows = ((2 * ldgs * 8 * sizeof(double) + 3 * 16 * 4 + 2 * 4) + 255) & ~(size_t)255;
+  return std::max(rows, oem_iter_xbuf_bytes((int)p, 8, OEM_ITER_F64));
 }
 
 // Cluster size C and Mg instances per task for B Grams of npen instances;
@@ -750,40 +796,53 @@ inline int layout_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, int pre
   I.Mg = Mg;
   I.M = oem_iter_mpad(Mg);
   I.grid = grid;
+  I.rows = iter_rows_kernel(p);
   const int ntasks = B * ((P.npen + Mg - 1) / Mg);
+  const bool rows = I.rows;
+  const bool wide = !rows && p > kIterWideP;
+  auto fixed_of = [&](int max_rows) {
+    return rows ? oem_iter_rows_smem_fixed((int)p, Mg, max_rows, prec)
+                : oem_iter_smem_fixed((int)p, Mg, max_rows, prec, grid, I.groups);
+  };
+  auto probe_of = [&](int CC) {
+    IterLaunch probe{};
+    probe.ntasks = ntasks; probe.C = CC; probe.M = I.M; probe.precision = prec;
+    probe.smem = I.smem; probe.max_rows = I.max_rows; probe.grid = grid ? 1 : 0;
+    probe.groups = I.groups ? 1 : 0; probe.wide = wide ? 1 : 0;
+    return iter_smem_probe(probe, rows);
+  };
   if (grid) {
     C = std::min<int>(C, ctx->num_sms / std::max(1, ntasks));
-    C = (int)std::min<int64_t>(C, (p + 3) / 4);
+    C = (int)std::min<int64_t>(C, rows ? (p + 3) / 4 : p);
     if (C < 2) return fail(ctx, OEM_EUNSUPPORTED, "grid mode needs at least 2 CTAs per task");
     I.gslice.assign((size_t)C + 1, 0);
-    make_slices(p, C, P.allowed, I.gslice.data(), &I.max_rows);
-    const size_t fixed = oem_iter_smem_fixed((int)p, Mg, I.max_rows, prec);
-    const size_t per = oem_iter_smem_per_row((int)p, prec);
+    if (rows) make_slices(p, C, P.allowed, I.gslice.data(), &I.max_rows);
+    else make_slices_even(p, C, 1, I.gslice.data(), &I.max_rows);
+    const size_t fixed = fixed_of(I.max_rows);
+    const size_t per = rows ? oem_iter_rows_smem_per_row((int)p, prec) : oem_iter_smem_per_row((int)p, prec);
     I.smem_rows = I.max_rows;
     I.smem = fixed + (size_t)I.max_rows * per;
     I.C = C;
     if (I.smem + 1024 > kIterSmemCap)
       return fail(ctx, OEM_EUNSUPPORTED, "grid mode: %d rows per CTA do not fit", I.max_rows);
-    IterLaunch probe{};
-    probe.ntasks = ntasks; probe.C = C; probe.M = I.M; probe.precision = prec;
-    probe.smem = I.smem; probe.max_rows = I.max_rows; probe.grid = 1;
-    if (oem_iter_max_cluster(probe) < 1)
-      return fail(ctx, OEM_EUNSUPPORTED, "grid mode: no CTA fits on an SM");
+    if (probe_of(C) < 1) return fail(ctx, OEM_EUNSUPPORTED, "grid mode: no CTA fits on an SM");
     return OEM_OK;
   }
   for (;; C /= 2) {
-    make_slices(p, C, P.allowed, I.slice, &I.max_rows);
-    const size_t fixed = oem_iter_smem_fixed((int)p, Mg, I.max_rows, prec);
+    if (rows) {
+      make_slices(p, C, P.allowed, I.slice, &I.max_rows);
+    } else {
+      make_slices_even(p, C, 4, I.slice, &I.max_rows);
+    }
+    const size_t fixed = fixed_of(I.max_rows);
     if (fixed + 1024 > kIterSmemCap)
-      return fail(ctx, OEM_EUNSUPPORTED, "p=%lld too large for the iteration kernel", (long long)p);
-    const size_t per = oem_iter_smem_per_row((int)p, prec);
+      return fail(ctx, OEM_EUNSUPPORTED, "p=%lld with %d instances per task too large for the iteration kernel",
+                  (long long)p, Mg);
+    const size_t per = rows ? oem_iter_rows_smem_per_row((int)p, prec) : oem_iter_smem_per_row((int)p, prec);
     I.smem_rows = (int)std::min<size_t>((size_t)I.max_rows, (kIterSmemCap - fixed) / per);
     I.smem = fixed + (size_t)I.smem_rows * per;
     I.C = C;
-    IterLaunch probe{};
-    probe.ntasks = ntasks; probe.C = C; probe.M = I.M; probe.precision = prec;
-    probe.smem = I.smem; probe.max_rows = I.max_rows;
-    if (oem_iter_max_cluster(probe) >= 1) return OEM_OK;
+    if (probe_of(C) >= 1) return OEM_OK;
     if (C == 1) return fail(ctx, OEM_ECUDA, "no cluster configuration of the iteration kernel fits");
   }
 }
@@ -816,6 +875,12 @@ inline int plan_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, const oem
     while (Mg > 1 && (int64_t)B * ((P.npen + Mg / 2 - 1) / (Mg / 2)) * C <= ctx->num_sms) Mg /= 2;
   }
   Mg = std::min(Mg, std::max(1, P.npen));
+  // the replicated kernel keeps every row of its Mg instances in shared
+  // memory: fewer instances per task where they do not fit
+  while (o->instances_per_task <= 0 && Mg > 1 && !iter_rows_kernel(p) &&
+         oem_iter_smem_fixed((int)p, Mg, (int)std::min<int64_t>(p, 256), prec, false, I.groups) + 1024 >
+             kIterSmemCap)
+    Mg /= 2;
   bool grid = o->cluster_ctas > kMaxCluster;
   I.gslice_cap = std::max(ctx->num_sms, o->cluster_ctas) + 1;
   if (grid) C = o->cluster_ctas;
@@ -907,7 +972,11 @@ inline int launch_iter_layout(oem_ctx* ctx, int64_t p, int B, const float* G32, 
   Lc.smem = I.smem;
   Lc.grid = I.grid ? 1 : 0;
   Lc.max_rows = I.max_rows;
-  LAUNCH(OEM_PROF_ITER, launch_oem_iter(Lc, s));
+  Lc.groups = I.groups ? 1 : 0;
+  Lc.wide = (!I.rows && p > kIterWideP) ? 1 : 0;
+  Lc.wait_cycles = iter_wait_cycles();
+  if (I.rows) LAUNCH(OEM_PROF_ITER, launch_oem_iter_rows(Lc, s));
+  else LAUNCH(OEM_PROF_ITER, launch_oem_iter(Lc, s));
   return OEM_OK;
 }
 

@@ -163,9 +163,9 @@ __device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned* p) {
 
 // Barrier of the nctas CTAs of one task in a cooperative launch (all of them
 // resident): bar[0] counts arrivals, bar[1] is the generation; gen is the
-// caller's copy of the generation (thread 0). Every wait is bounded (about
-// 2 s at 2 GHz); returns false in every thread of the CTA on timeout.
-__device__ __forceinline__ bool group_barrier(unsigned* bar, unsigned nctas, unsigned& gen) {
+// caller's copy of the generation (thread 0). Every wait is bounded (lim
+// cycles); returns false in every thread of the CTA on timeout.
+__device__ __forceinline__ bool group_barrier(unsigned* bar, unsigned nctas, unsigned& gen, long long lim) {
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
@@ -180,7 +180,7 @@ __device__ __forceinline__ bool group_barrier(unsigned* bar, unsigned nctas, uns
       int spins = 0;
       while (ld_acquire_gpu(&bar[1]) == g) {
         if (++spins > 8) __nanosleep(32);  // fewer polls on the shared line
-        if (clock64() - t0 > 4000000000LL) { ok = 0; break; }
+        if (clock64() - t0 > lim) { ok = 0; break; }
       }
     }
     __threadfence();
@@ -327,30 +327,50 @@ struct IterTask {
   // grid mode only (IterLaunch::grid): the C CTAs of the task exchange
   // through global memory instead of a cluster's shared memory
   const int32_t* gslice; // [C+1] CTA r owns rows [gslice[r], gslice[r+1])
-  void* xD;              // [2][round_up(p,4)][M] dbeta buffers (T), zeroed
-  unsigned* xslot;       // [3][2M] maxima slots, zeroed
-  unsigned* xbar;        // [2] barrier count and generation, zeroed
+  void* xD;              // zeroed before the launch; replicated kernel: [2][p][M]
+                         // tagged words of G dbeta (two per float64 value);
+                         // row-owned kernel: [2][round_up(p,4)][M] dbeta (T)
+  unsigned* xslot;       // [3][2M] maxima slots, zeroed (row-owned kernel)
+  unsigned* xbar;        // [2] barrier count and generation, zeroed (row-owned kernel)
 };
 struct IterLaunch {
   const IterTask* tasks; // device array
   int32_t ntasks, C, M, precision;
   int32_t grid;          // 1: cooperative launch, C CTAs per task, global-memory exchange
   int32_t max_rows;      // longest CTA slice of the launch (picks the row group)
+  int32_t groups;        // some task has a group penalty (group arrays in shared memory)
+  int32_t wide;          // column-segment mat-vec (p > kIterWideP; replicated kernel)
   double tol;
   int64_t max_iter;      // per lambda
   int64_t max_loops;     // per launch (<= 0: run to completion)
+  int64_t wait_cycles;   // bound of every device wait (clock64 cycles)
   unsigned* dstatus;
   size_t smem;
 };
 // Instances per Gram are padded to M in {1, 2, 4, 8}.
 int oem_iter_mpad(int npen);
-// Shared memory needed besides the resident Gram rows, and per resident row.
-size_t oem_iter_smem_fixed(int p, int npen, int max_rows, int precision);
+
+// Replicated-update kernel (oem_iter.cu), used for p <= kIterRepMaxP: every
+// CTA of a task keeps u, beta and dbeta of all p rows and applies the
+// thresholds to all of them; only the mat-vec rows are split between CTAs.
+constexpr int kIterRepMaxP = 4096;
+constexpr int kIterWideP = 1024;   // above: column-segment mat-vec, 512 threads
+// Shared memory besides the resident Gram rows, and per resident row.
+size_t oem_iter_smem_fixed(int p, int M, int max_rows, int precision, bool grid, bool groups);
 size_t oem_iter_smem_per_row(int p, int precision);
 // Clusters of this configuration the device can co-schedule (0: none); in
 // grid mode, CTAs per SM.
 int oem_iter_max_cluster(const IterLaunch& P);
 cudaError_t launch_oem_iter(const IterLaunch& P, cudaStream_t s);
+// Grid-mode exchange buffer of one task (tagged 64-bit words, both parities).
+size_t oem_iter_xbuf_bytes(int p, int M, int precision);
+
+// Row-owned kernel (oem_iter_rows.cu), used for p > kIterRepMaxP: CTA r owns
+// rows of u and beta and exchanges dbeta and the maxima.
+size_t oem_iter_rows_smem_fixed(int p, int npen, int max_rows, int precision);
+size_t oem_iter_rows_smem_per_row(int p, int precision);
+int oem_iter_rows_max_cluster(const IterLaunch& P);
+cudaError_t launch_oem_iter_rows(const IterLaunch& P, cudaStream_t s);
 
 // CV scoring from raw fold Grams of Z and the fold paths.
 // With ocol >= 0 the model has the intercept bprime [B][npen][L] on the

@@ -8,42 +8,35 @@
 // as the iteration converges, so float32 products stay accurate, and u is
 // kept as a float32 (hi, lo) pair so its rounding does not accumulate.
 //
-// One thread-block cluster per task (a Gram with its instances; tasks of one
-// launch may differ in p). CTA r of the cluster owns rows [slice[r],
-// slice[r+1]) of G, u and beta; inside the CTA every warp owns a contiguous
-// block of those rows (aligned to group starts for the group lasso). Per
-// iteration a warp, on its own rows and with no block-wide barrier:
-//   1. forms (G dbeta)_i for all instances of the task at once, 16 / M rows
-//      at a time so that one pass over dbeta serves the group (lane l reads
-//      columns 4l .. 4l+3, + 128, ...; G rows in registers when a warp has
-//      one row group and p <= 512, else resident in shared memory, the rest
-//      read from L2); a reduce-scatter leaves each (row, instance) sum in one
-//      lane pair, which updates u_i and, without groups, applies the
-//      threshold;
-//   2. for group penalties, forms the group norms and thresholds afterwards;
-//   3. writes its dbeta rows into the shared memory of every CTA of the
-//      cluster and its max|dbeta|, max|beta| per instance into the block's
-//      table.
-// One block barrier, then one warp sends the CTA's maxima to every CTA.
-// Float32 iteration: the dbeta rows and the maxima go out as st.async
-// stores, each counting its bytes on the receiving CTA's mbarrier for that
-// buffer, so a CTA waits (bounded) for exactly the bytes addressed to it and
-// there is no cluster barrier in the loop; one warp then takes the maximum
-// over the C entries. Float64 iteration: plain DSMEM stores, DSMEM atomic
-// max into every CTA's slot (order-preserving 32-bit images) and one cluster
-// barrier per iteration. Every thread then takes the same convergence
-// decisions from the same values. A launch may stop after a loop budget and
-// save its state (serving), to be resumed by a later launch.
-//
-// Grid mode (large p: the Gram rows of a task do not fit in the shared memory
-// of one cluster, at most 16 SMs, but fit in that of C > 16 CTAs): the C CTAs
-// of a task are an ordinary group of a cooperative launch, one per SM. Each
-// iteration a CTA reads the whole dbeta from global memory (L2) into its
-// shared memory, writes its own rows of the new dbeta back to global memory,
-// folds its maxima into a global slot with atomics, and waits at a
-// global-memory barrier of the group (bounded spin) instead of the cluster
-// barrier. The arithmetic is the same as in cluster mode.
+// Replicated update. A task (a Gram with M of its instances; tasks of one
+// launch may differ in p) runs on C CTAs: one thread-block cluster (C <= 16)
+// or, in grid mode, C CTAs of a cooperative launch. CTA r owns the mat-vec
+// rows [slice[r], slice[r+1]) of G, but every CTA keeps u, beta and dbeta of
+// ALL p rows and applies the thresholds to all of them. One iteration:
+//   A. every CTA forms y_i = (G dbeta)_i of its rows for the M instances and
+//      sends them to every CTA of the task (cluster: st.async stores into
+//      each peer's shared memory, counted on the receiver's mbarrier; float64
+//      iteration: DSMEM stores and a cluster barrier; grid mode: 64-bit words
+//      in global memory that carry the exchange number in their high half,
+//      so a reader polls for exactly the words it needs);
+//   B. every thread updates u of its elements by d dbeta - y (float32 TwoSum);
+//   C. the thresholds give beta and the new dbeta (group norms between two
+//      block barriers for group penalties);
+//   D. max|dbeta| and max|beta| per instance by a block reduction: every CTA
+//      holds all rows, so its block maxima are the task's maxima and every
+//      CTA takes the same convergence decisions with no second exchange.
+// The mat-vec keeps its G rows in registers where they fit, else in shared
+// memory, else reads them from L2. For p <= 1024 each warp owns rows and runs
+// over all columns (lane l reads columns 4l .. 4l+3, + 128, ...; one
+// reduce-scatter per row group); for larger p each warp owns 128-column
+// segments of all the CTA's rows and the segment sums are added in segment
+// order. Either way the order of every sum depends on p only, so every layout
+// (cluster size, grid mode, instances per task) gives the same bits. A launch
+// may stop after a loop budget and save its state (serving), to be resumed by
+// a later launch. Every wait is bounded (IterLaunch::wait_cycles): on expiry
+// the kernel sets the timeout status bit and returns.
 #include "oem_internal.cuh"
+#include "iter_common.cuh"
 
 #include <cooperative_groups.h>
 
@@ -53,200 +46,47 @@ namespace oem {
 
 int oem_iter_mpad(int npen) { return npen <= 1 ? 1 : npen <= 2 ? 2 : npen <= 4 ? 4 : 8; }
 
-// Threads per CTA. Every warp reads the whole dbeta once per group of its
-// rows, so more warps than needed to spread a CTA's rows only add
-// shared-memory traffic.
-template <typename T, int M>
-constexpr int iter_threads() { return 256; }
+constexpr int kWideRows = 16;  // wide mat-vec: G rows per CTA held in registers
 
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-template <typename T>
-__device__ __forceinline__ T warp_max(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
+__host__ __device__ constexpr int rep_threads(bool wide) { return wide ? 512 : 256; }
+__host__ __device__ inline int rep_nseg(int p) { return (p + 127) / 128; }
 
-// Reduce-scatter of V (4, 8 or 16) per-lane values over the warp: returns,
-// in lane l, the warp sum of value l / (32 / V) (the 32 / V lanes of a group
-// all hold it). The levels at lane offsets 16, 8, ... halve the values a lane
-// keeps until one is left; the remaining offsets add plainly. The pairing
-// tree of every value is the same as a full butterfly sum's.
-template <int V, typename T>
-__device__ __forceinline__ T reduce_scatter(const T (&a)[V], int lane) {
-  static_assert(V == 4 || V == 8 || V == 16, "V");
-  T b[V];
-#pragma unroll
-  for (int q = 0; q < V; ++q) b[q] = a[q];
-  int n = V, o = 16;
-#pragma unroll
-  for (int lv = 0; lv < 5; ++lv, o >>= 1) {
-    if (n > 1) {
-      const bool up = lane & o;
-      const int h = n >> 1;
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q < h) b[q] = (up ? b[q + h] : b[q]) + __shfl_xor_sync(0xffffffffu, up ? b[q] : b[q + h], o);
-      n = h;
-    } else {
-      b[0] += __shfl_xor_sync(0xffffffffu, b[0], o);
-    }
-  }
-  return b[0];
-}
-
-// Load the M entries of row j of a [rows][M] buffer.
-template <typename T, int M>
-__device__ __forceinline__ void load_col(const T* __restrict__ D, int j, T (&v)[M]) {
-  const T* s = D + (size_t)j * M;
-  if constexpr (sizeof(T) == 4 && M % 4 == 0) {
-#pragma unroll
-    for (int k = 0; k < M; k += 4) {
-      const float4 t = *reinterpret_cast<const float4*>(s + k);
-      v[k] = t.x; v[k + 1] = t.y; v[k + 2] = t.z; v[k + 3] = t.w;
-    }
-  } else if constexpr (sizeof(T) == 4 && M == 2) {
-    const float2 t = *reinterpret_cast<const float2*>(s);
-    v[0] = t.x; v[1] = t.y;
-  } else if constexpr (sizeof(T) == 8 && M % 2 == 0) {
-#pragma unroll
-    for (int k = 0; k < M; k += 2) {
-      const double2 t = *reinterpret_cast<const double2*>(s + k);
-      v[k] = t.x; v[k + 1] = t.y;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < M; ++k) v[k] = s[k];
-  }
-}
-
-template <typename T, int M>
-__device__ __forceinline__ void store_col(T* __restrict__ dst, const T* __restrict__ src) {
-  if constexpr (sizeof(T) == 4 && M % 4 == 0) {
-#pragma unroll
-    for (int k = 0; k < M; k += 4)
-      *reinterpret_cast<float4*>(dst + k) = *reinterpret_cast<const float4*>(src + k);
-  } else if constexpr (sizeof(T) == 4 && M == 2) {
-    *reinterpret_cast<float2*>(dst) = *reinterpret_cast<const float2*>(src);
-  } else if constexpr (sizeof(T) == 8 && M % 2 == 0) {
-#pragma unroll
-    for (int k = 0; k < M; k += 2)
-      *reinterpret_cast<double2*>(dst + k) = *reinterpret_cast<const double2*>(src + k);
-  } else {
-#pragma unroll
-    for (int k = 0; k < M; ++k) dst[k] = src[k];
-  }
-}
-
-// Position of element (row i, instance k) in a dbeta buffer [rows][M]. In
-// the float32 path a lane reads 4 consecutive rows (M float4 units) at a
-// time; the 16-byte units are XOR-swizzled within each run of 8 units by
-// (unit / 8) mod M, so that the 8 lanes of a shared-memory wavefront hit 8
-// different bank groups. The float64 path keeps the plain layout.
-template <typename T, int M>
-__device__ __forceinline__ int dpos(int i, int k) {
-  const int f = i * M + k;
-  if constexpr (sizeof(T) == 4 && M > 1) {
-    const int u = f >> 2;
-    return ((u ^ ((u >> 3) & (M - 1))) << 2) | (f & 3);
-  } else {
-    return f;
-  }
-}
-// Store the M values of row i (src[0..M)) at their positions in D.
-template <typename T, int M>
-__device__ __forceinline__ void store_row(T* __restrict__ D, int i, const T* __restrict__ src) {
-  if constexpr (sizeof(T) == 4 && M == 8) {
-    store_col<T, 4>(D + dpos<T, M>(i, 0), src);
-    store_col<T, 4>(D + dpos<T, M>(i, 4), src + 4);
-  } else {
-    store_col<T, M>(D + dpos<T, M>(i, 0), src);
-  }
-}
-
-// Order-preserving 32-bit images of non-negative maxima for the block table
-// and the DSMEM atomic max (32-bit atomics only across the cluster). A
-// float64 value is rounded up to float32 first, so a max|dbeta| is never
-// under-stated and no convergence is declared early; max|beta| moves by at
-// most 2^-24 relative.
-__device__ __forceinline__ float to_red(float v) { return v; }
-__device__ __forceinline__ float to_red(double v) { return __double2float_ru(v); }
-__device__ __forceinline__ float from_red(unsigned int b) { return __uint_as_float(b); }
-
-__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
-
-// Cluster-mode exchange by asynchronous stores: st.async writes into a peer
-// CTA's shared memory and counts its bytes on that CTA's mbarrier, so each
-// CTA waits for exactly the bytes addressed to it (no cluster barrier).
-__device__ __forceinline__ uint32_t xs_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ uint32_t xs_map(uint32_t a, int rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ void xs_st4(uint32_t a, float4 v, uint32_t bar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
-               ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar) : "memory");
-}
-__device__ __forceinline__ void xs_st1(uint32_t a, uint32_t v, uint32_t bar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
-               ::"r"(a), "r"(v), "r"(bar) : "memory");
-}
-__device__ __forceinline__ void xs_init(uint32_t bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void xs_arm(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool xs_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-
-// Shared-memory carve-up (byte offsets, 16-byte aligned). The dbeta buffers
-// have ldgs = round_up(p, 4) rows; rows p.. stay zero.
-struct IterSmem {
-  size_t dbuf, uhi, ulo, beta, w, gn, cgr, glen, st, lred, red, xbar, xslot, xred, gs, total;
+// Shared-memory carve-up (byte offsets, 16-byte aligned).
+struct RepSmem {
+  size_t db, yb, uh, ul, be, gn, cg, gl, part, lred, xbar, gs, total;
 };
-constexpr int kIterMaxWarps = 16;
-__host__ __device__ inline IterSmem iter_smem_layout(int p, int M, int maxR, int tsz, int smem_rows) {
+__host__ __device__ inline RepSmem rep_smem_layout(int p, int M, int tsz, bool wide, bool grid,
+                                                   bool groups, int maxR, int smem_rows) {
   const int ldgs = (p + 3) & ~3;
-  IterSmem L;
+  const int NW = rep_threads(wide) / 32;
+  const size_t pm = (size_t)p * M;
+  RepSmem L;
   size_t o = 0;
-  L.dbuf = o;  o = al16(o + (size_t)2 * ldgs * M * tsz);
-  L.uhi = o;   o = al16(o + (size_t)M * maxR * tsz);
-  L.ulo = o;   o = al16(o + (size_t)M * maxR * tsz);
-  L.beta = o;  o = al16(o + (size_t)M * maxR * tsz);
-  L.w = o;     o = al16(o + (size_t)M * maxR * tsz);
-  L.gn = o;    o = al16(o + (size_t)M * maxR * tsz);
-  L.cgr = o;   o = al16(o + (size_t)M * maxR * tsz);
-  L.glen = o;  o = al16(o + (size_t)M * maxR * 4);
-  L.st = o;    o = al16(o + (size_t)maxR * M * tsz);
-  L.lred = o;  o = al16(o + (size_t)kIterMaxWarps * M * 2 * 4);
-  L.red = o;   o = al16(o + (size_t)3 * M * 2 * 4);
-  L.xbar = o;  o = al16(o + 2 * 8);
-  L.xslot = o; o = al16(o + (size_t)2 * 16 * M * 2 * 4);
-  L.xred = o;  o = al16(o + (size_t)(M * 2 + 1) * 4);
-  L.gs = o;    o = al16(o + (size_t)smem_rows * ldgs * tsz);
+  L.db = o;   o = al16(o + 2 * (size_t)ldgs * M * tsz);           // dbeta, two parities
+  L.yb = o;   o = al16(o + (grid ? 0 : 2 * (size_t)ldgs * M * tsz));  // G dbeta received, two parities
+  L.uh = o;   o = al16(o + pm * tsz);
+  L.ul = o;   o = al16(o + pm * tsz);
+  L.be = o;   o = al16(o + pm * tsz);
+  L.gn = o;   o = al16(o + (groups ? pm * tsz : 0));              // group norm per element
+  L.cg = o;   o = al16(o + (groups ? pm * tsz : 0));              // group weight per element
+  L.gl = o;   o = al16(o + (groups ? pm * 4 : 0));                // group length at group starts
+  L.part = o; o = al16(o + (wide ? (size_t)rep_nseg(p) * maxR * M * tsz : 0));
+  L.lred = o; o = al16(o + (size_t)2 * NW * 2 * M * 4);
+  L.xbar = o; o = al16(o + 32);                                   // two mbarriers, timeout flag
+  L.gs = o;   o = al16(o + (size_t)smem_rows * ldgs * tsz);
   L.total = o;
   return L;
 }
 
-template <typename T, int M, int NT, bool kGrid, int RG>
+template <typename T, int M, int NT, bool kGrid, int RG, bool kWide>
 __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   constexpr int NW = NT / 32;
+  constexpr bool kF32 = sizeof(T) == 4;
+  constexpr bool kAsync = kF32 && !kGrid;
+  static_assert(NT % M == 0 && 32 % M == 0, "instances per lane layout");
+  // elements per thread whose state lives in registers (the wide mat-vec's
+  // G rows take most of the 128 registers a thread has at 512 threads)
+  constexpr int kRepJR = kWide ? 2 : 4;
   cg::cluster_group cluster = cg::this_cluster();
   const int C = P.C;
   const int rank = kGrid ? (int)(blockIdx.x % C) : (int)cluster.block_rank();
@@ -254,34 +94,29 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   const int p = tk.p, L = tk.L, m = tk.npen, maxR = tk.max_rows;
   const int i0 = kGrid ? tk.gslice[rank] : tk.slice[rank];
   const int R = (kGrid ? tk.gslice[rank + 1] : tk.slice[rank + 1]) - i0;
-  T* const xD = reinterpret_cast<T*>(tk.xD);  // grid mode
-  unsigned bar_gen = 0;
   const int ldgs = (p + 3) & ~3, smem_rows = tk.smem_rows;
+  const int PM = p * M;
+  const int nseg = kWide ? rep_nseg(p) : 0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr bool kF32 = sizeof(T) == 4;
+  const long long wait_lim = P.wait_cycles > 0 ? P.wait_cycles : 4000000000LL;
 
   extern __shared__ __align__(16) unsigned char smem[];
-  const IterSmem Ls = iter_smem_layout(p, M, maxR, (int)sizeof(T), tk.smem_rows);
-  T* Dbuf = reinterpret_cast<T*>(smem + Ls.dbuf);
-  T* uhi = reinterpret_cast<T*>(smem + Ls.uhi);
-  T* ulo = reinterpret_cast<T*>(smem + Ls.ulo);
-  T* bet = reinterpret_cast<T*>(smem + Ls.beta);
-  T* wv = reinterpret_cast<T*>(smem + Ls.w);
-  T* gn = reinterpret_cast<T*>(smem + Ls.gn);
-  T* cgr = reinterpret_cast<T*>(smem + Ls.cgr);
-  int* glen = reinterpret_cast<int*>(smem + Ls.glen);
-  T* st = reinterpret_cast<T*>(smem + Ls.st);
-  float* lred = reinterpret_cast<float*>(smem + Ls.lred);  // [warp][2M] block table
-  unsigned int* red = reinterpret_cast<unsigned int*>(smem + Ls.red);  // [3][2M] slots
-  T* Gs = reinterpret_cast<T*>(smem + Ls.gs);
-  constexpr bool kAsync = kF32 && !kGrid;
-  const uint32_t xbar0 = xs_u32(smem + Ls.xbar);  // mbarriers of dbeta buffers 0 / 1
-  unsigned int* xslot = reinterpret_cast<unsigned int*>(smem + Ls.xslot);  // [2][C][2M]
-  unsigned int* xred = reinterpret_cast<unsigned int*>(smem + Ls.xred);    // [2M], then the timeout flag
-  volatile unsigned int* xfail = xred + 2 * M;
+  const RepSmem Ls = rep_smem_layout(p, M, (int)sizeof(T), kWide, kGrid, P.groups != 0, maxR, smem_rows);
+  T* const Dbuf = reinterpret_cast<T*>(smem + Ls.db);
+  T* const Ybuf = reinterpret_cast<T*>(smem + Ls.yb);   // [2][ldgs][M]
+  T* const uhs = reinterpret_cast<T*>(smem + Ls.uh);
+  T* const uls = reinterpret_cast<T*>(smem + Ls.ul);
+  T* const bes = reinterpret_cast<T*>(smem + Ls.be);
+  T* const gns = reinterpret_cast<T*>(smem + Ls.gn);
+  T* const cgs = reinterpret_cast<T*>(smem + Ls.cg);
+  int* const gls = reinterpret_cast<int*>(smem + Ls.gl);
+  T* const part = reinterpret_cast<T*>(smem + Ls.part);
+  float* const lred = reinterpret_cast<float*>(smem + Ls.lred);  // [2][NW][2M]
+  const uint32_t xbar0 = xs_u32(smem + Ls.xbar);                 // mbarriers of Ybuf parities 0 / 1
+  T* const Gs = reinterpret_cast<T*>(smem + Ls.gs);
+  unsigned long long* const xw = reinterpret_cast<unsigned long long*>(tk.xD);  // grid: [2][PM][W]
   const T* Gglob = kF32 ? reinterpret_cast<const T*>(tk.G32) : reinterpret_cast<const T*>(tk.G64);
   const int ldgg = kF32 ? tk.ldg : p;
-  const double* cb = tk.c;
   const T dgram = (T)tk.d[0];
 
   // ---- per-instance parameters and control state (identical in every thread)
@@ -298,8 +133,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
       gamma[k] = kF32 ? (T)pen.gamma : (T)pen.gamma64;
       T de = dgram;
       if (pen.kind == OEM_MCP || pen.kind == OEM_GROUP_MCP) de = fmax(de, (T)(1.01 / pen.gamma64));
-      if (pen.kind == OEM_SCAD || pen.kind == OEM_GROUP_SCAD)
-        de = fmax(de, (T)(1.01 / (pen.gamma64 - 1.0)));
+      if (pen.kind == OEM_SCAD || pen.kind == OEM_GROUP_SCAD) de = fmax(de, (T)(1.01 / (pen.gamma64 - 1.0)));
       dk[k] = de;
       done[k] = 0;
       if (tk.resume) {
@@ -313,81 +147,9 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   bool has_group = false;
   for (int k = 0; k < m; ++k) has_group |= (tk.pens[k].kind >= OEM_GROUP_LASSO);
 
-  // ---- this warp's contiguous row block, aligned to allowed boundaries
-  int wlo, whi;
-  {
-    const int per = (R + NW - 1) / NW;
-    auto bound = [&](int wi) {
-      if (wi <= 0) return 0;
-      if (wi >= NW) return R;
-      int b = min(R, wi * per);
-      if (tk.allowed) while (b < R && !tk.allowed[i0 + b]) ++b;
-      return b;
-    };
-    wlo = bound(warp);
-    whi = max(wlo, bound(warp + 1));
-  }
-
-  // ---- initialise u, beta, weights, groups, the G rows kept in shared memory
-  for (int e = tid; e < M * maxR; e += NT) {
-    const int k = e / maxR, i = e % maxR;
-    T hi = T(0), lo = T(0), wt = T(1), cgv = T(0), b0 = T(0);
-    int gl = 0;
-    if (k < m && i < R) {
-      const DevPenalty& pen = tk.pens[k];
-      if (tk.resume) {
-        const size_t o = (size_t)k * p + i0 + i;
-        hi = (T)tk.st_u[2 * o];
-        lo = (T)tk.st_u[2 * o + 1];
-        b0 = (T)tk.st_beta[o];
-      } else {
-        const double cv = cb[i0 + i];
-        hi = (T)cv;
-        lo = (T)(cv - (double)hi);
-      }
-      if (kF32) { if (pen.w32) wt = (T)pen.w32[i0 + i]; }
-      else { if (pen.w64) wt = (T)pen.w64[i0 + i]; }
-      if (pen.kind >= OEM_GROUP_LASSO) {
-        const int g = pen.grp[i0 + i];
-        cgv = (T)pen.cg[g];
-        if (i == 0 || pen.grp[i0 + i - 1] != g) {
-          int len = 1;
-          while (i + len < R && pen.grp[i0 + i + len] == g) ++len;
-          gl = len;
-        }
-      }
-    }
-    uhi[e] = hi; ulo[e] = lo; bet[e] = b0; wv[e] = wt; cgr[e] = cgv; glen[e] = gl; gn[e] = T(0);
-  }
-  for (int e = tid; e < 2 * ldgs * M; e += NT) Dbuf[e] = T(0);
-  for (int e = tid; e < 3 * M * 2; e += NT) red[e] = 0u;
-  if (kAsync && tid == 0) {
-    xs_init(xbar0);
-    xs_init(xbar0 + 8);
-    *xfail = 0u;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  for (int e = tid; e < smem_rows * ldgs; e += NT) {
-    const int i = e / ldgs, j = e % ldgs;
-    Gs[e] = (i < R && j < p) ? Gglob[(size_t)(i0 + i) * ldgg + j] : T(0);
-  }
-  if constexpr (kGrid) {
-    if (!group_barrier(tk.xbar, (unsigned)C, bar_gen)) {
-      if (tid == 0) atomicOr(P.dstatus, kStatTimeout);
-      return;
-    }
-  } else {
-    cluster.sync();  // every CTA initialised before any DSMEM access
-  }
-
-  // Lane roles in the row-group mat-vec: a group is RG rows (V = RG M sums);
-  // after the reduce-scatter lane l holds the sum of value v = l / S,
-  // S = 32 / V, i.e. row rsub = v / M of the group and instance kq = v % M
-  // (the first lane of each group of S acts).
-  constexpr int V = RG * M, S = 32 / V;
-  static_assert(V == 4 || V == 8 || V == 16, "row group");
-  const int vq = lane / S, rsub = vq / M, kq = vq % M;
-  const bool even = (lane % S) == 0;
+  // ---- this thread's elements e = tid + NT j: row e / M, instance kq = tid % M
+  const int kq = tid % M;
+  const bool my_inst = kq < m;
   int my_kind = OEM_LASSO;
   T my_alpha = T(1), my_gamma = T(3), my_d = T(1), my_lam = T(0);
   int my_done = 1;
@@ -397,32 +159,98 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
       my_kind = kind[k]; my_alpha = alpha[k]; my_gamma = gamma[k]; my_d = dk[k];
       my_lam = lamv[k]; my_done = done[k];
     }
-  const bool my_inst = kq < m;
+  const float* w32 = my_inst ? tk.pens[kq].w32 : nullptr;
+  const double* w64 = my_inst ? tk.pens[kq].w64 : nullptr;
+  auto weight = [&](int i) -> T {
+    if constexpr (kF32) return w32 ? (T)w32[i] : T(1);
+    else return w64 ? (T)w64[i] : T(1);
+  };
+  const int nJ = (PM + NT - 1) / NT;
+  T r_uh[kRepJR], r_ul[kRepJR], r_b[kRepJR], r_w[kRepJR], r_dn[kRepJR];
 
-  const T tol = (T)P.tol;
-  // Float32 with one row group per warp and p <= 512: the warp's G rows live
-  // in registers (lane l holds columns 4l .. 4l+3 + 128 s of each row), so the
-  // mat-vec reads only dbeta from shared memory. Same products in the same
-  // order as from shared memory.
-  constexpr int kGS = 4;                          // column steps of 128
-  constexpr bool kGregT = kF32 && RG <= 4;        // register budget: RG * kGS float4
+  // ---- initialise u, beta (every row), weights, group arrays, dbeta, G rows
+  for (int j = 0; j < nJ; ++j) {
+    const int e = tid + NT * j;
+    if (e >= PM) break;
+    const int i = e / M;
+    T hi = T(0), lo = T(0), b0 = T(0);
+    if (my_inst) {
+      if (tk.resume) {
+        const size_t o = (size_t)kq * p + i;
+        hi = (T)tk.st_u[2 * o];
+        lo = (T)tk.st_u[2 * o + 1];
+        b0 = (T)tk.st_beta[o];
+      } else {
+        const double cv = tk.c[i];
+        hi = (T)cv;
+        lo = (T)(cv - (double)hi);
+      }
+    }
+    uhs[e] = hi; uls[e] = lo; bes[e] = b0;
+#pragma unroll
+    for (int q = 0; q < kRepJR; ++q)
+      if (q == j) { r_uh[q] = hi; r_ul[q] = lo; r_b[q] = b0; r_w[q] = weight(i); r_dn[q] = T(0); }
+  }
+  if (P.groups) {
+    for (int e2 = tid; e2 < PM; e2 += NT) {
+      const int k = e2 / p, i = e2 % p;
+      T cgv = T(0);
+      int gl = 0;
+      if (k < m && tk.pens[k].kind >= OEM_GROUP_LASSO) {
+        const DevPenalty& pen = tk.pens[k];
+        const int g = pen.grp[i];
+        cgv = (T)pen.cg[g];
+        if (i == 0 || pen.grp[i - 1] != g) {
+          int len = 1;
+          while (i + len < p && pen.grp[i + len] == g) ++len;
+          gl = len;
+        }
+      }
+      cgs[e2] = cgv; gls[e2] = gl; gns[e2] = T(0);
+    }
+  }
+  for (int e = tid; e < 2 * ldgs * M; e += NT) Dbuf[e] = T(0);
+  if (kAsync && tid == 0) {
+    xs_init_n(xbar0, NW);
+    xs_init_n(xbar0 + 8, NW);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int e = tid; e < smem_rows * ldgs; e += NT) {
+    const int i = e / ldgs, j = e % ldgs;
+    Gs[e] = (i < R && j < p) ? Gglob[(size_t)(i0 + i) * ldgg + j] : T(0);
+  }
+
+  // ---- mat-vec roles
+  // row-owned (p <= 1024): warp w owns rows [wlo, whi) of the CTA's slice;
+  // a row group is RG rows (V = RG M sums); after the reduce-scatter lane l
+  // holds the sum of value v = l / S, S = 32 / V: row rsub = v / M of the
+  // group and instance kv = v % M (the first lane of each group of S acts).
+  constexpr int V = RG * M, S = 32 / V;
+  static_assert(V == 4 || V == 8 || V == 16, "row group");
+  const int vq = lane / S, rsub = vq / M, kv = vq % M;
+  const bool even = (lane % S) == 0;
+  int wlo = 0, whi = 0;
+  if constexpr (!kWide) {
+    const int per = (R + NW - 1) / NW;
+    wlo = min(R, warp * per);
+    whi = min(R, wlo + per);
+  }
+  // Float32 G rows in registers: row-owned with one row group per warp and
+  // p <= 512 (lane l holds columns 4l .. 4l+3 + 128 s of each row); wide with
+  // at most kWideRows rows per CTA and one segment per warp (lane l holds
+  // columns 128 w + 4l .. 4l+3 of every row). Same products in the same order
+  // as from shared memory.
+  constexpr int kGS = 4;
+  constexpr bool kGregT = kF32 && !kWide && RG <= 4;
   const bool greg_on = kGregT && (whi - wlo) <= RG && p <= 128 * kGS;
   float4 greg[kGregT ? RG : 1][kGregT ? kGS : 1];
-  // With one row group per warp and scalar penalties, the lane that owns row
-  // wlo + rsub of instance kq keeps u (hi, lo), beta, w and its last dbeta
-  // in registers for the whole launch (beta is still stored for the outputs,
-  // u written back at the end); the same values as in shared memory.
-  const bool regst = kF32 && greg_on && !has_group;
-  const int i_own = wlo + rsub;
-  const bool own = even && i_own < whi;
-  T r_uhi = T(0), r_ulo = T(0), r_bet = T(0), r_w = T(1), r_dn = T(0);
-  if (regst && own) {
-    const int idx = kq * maxR + i_own;
-    r_uhi = uhi[idx];
-    r_ulo = ulo[idx];
-    r_bet = bet[idx];
-    r_w = wv[idx];
-  }
+  constexpr bool kWregT = kF32 && kWide;
+  const bool wreg_on = kWregT && R <= kWideRows && nseg <= NW;
+  float4 wreg[kWregT ? kWideRows : 1];
+  auto grow = [&](int ib) -> const T* {  // local row ib of this CTA's slice
+    return ib < smem_rows ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
+  };
+  __syncthreads();
   if constexpr (kGregT) {
 #pragma unroll
     for (int r = 0; r < RG; ++r)
@@ -430,97 +258,178 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
       for (int sx = 0; sx < kGS; ++sx) {
         float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
         const int j4 = lane * 4 + 128 * sx;
-        if (greg_on && r < whi - wlo && j4 < p) {
-          const int ib = wlo + r;
-          const float* rowp = reinterpret_cast<const float*>(
-              ib < smem_rows ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg);
-          g = *reinterpret_cast<const float4*>(rowp + j4);
-        }
+        if (greg_on && r < whi - wlo && j4 < p) g = *reinterpret_cast<const float4*>(grow(wlo + r) + j4);
         greg[r][sx] = g;
       }
   }
-  int skip_mv = 1;      // dbeta of the previous iteration is all zero
+  if constexpr (kWregT) {
+#pragma unroll
+    for (int r = 0; r < kWideRows; ++r) {
+      float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+      const int j4 = 128 * warp + lane * 4;
+      if (wreg_on && r < R && j4 < p) g = *reinterpret_cast<const float4*>(grow(r) + j4);
+      wreg[r] = g;
+    }
+  }
+  if constexpr (!kGrid) cluster.sync();  // every CTA initialised before any DSMEM access
+
+  const T tol = (T)P.tol;
+  int skip_mv = 1;  // dbeta of the previous iteration is all zero (y = 0)
   int all_done = 1;
   for (int k = 0; k < m; ++k) all_done &= done[k];
+  unsigned xc = 0;  // exchanges done (grid-mode tags are xc + 1)
   int64_t loops = 0;
   int t = 0;
-  while (!all_done) {
-    const int cur = t & 1, nxt = cur ^ 1;
-    const T* Dc = Dbuf + (size_t)cur * ldgs * M;
-    const int nr = whi - wlo;
-    if constexpr (kGrid) {
-      // the whole dbeta of the last iteration, from L2 (not L1: other SMs
-      // wrote it)
-      if (!skip_mv) {
-        const float4* src = reinterpret_cast<const float4*>(xD + (size_t)cur * ldgs * M);
-        float4* dst = reinterpret_cast<float4*>(Dbuf + (size_t)cur * ldgs * M);
-        const int nv4 = (int)((size_t)ldgs * M * sizeof(T) / 16);
-        for (int e = tid; e < nv4; e += NT) dst[e] = __ldcg(src + e);
-      }
-      __syncthreads();
-    }
-    T lmd = T(0), lmb = T(0);  // this lane's running max |dbeta|, |beta| (instance kq)
-    // ---- 1. per group of RG rows: y = G dbeta for all instances (one pass
-    // over dbeta for the group), u update and, without groups, the threshold
-    for (int gb = wlo; gb < whi; gb += RG) {
-      const int nv = min(RG, whi - gb);
-      T y = T(0);
-      if (!skip_mv) {
-        T acc[V];
-#pragma unroll
-        for (int q = 0; q < V; ++q) acc[q] = T(0);
-        const T* gr[RG];
-#pragma unroll
-        for (int r = 0; r < RG; ++r) {
-          const int ib = gb + min(r, nv - 1);
-          gr[r] = ib < smem_rows ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
+  bool final_pass = false;  // one more mat-vec and u update before saving the state
+  bool fail = false;
+  while (!all_done || final_pass) {
+    const T* Dp = Dbuf + (size_t)((t & 1) ^ 1) * ldgs * M;  // dbeta of the last iteration
+    T* Dn = Dbuf + (size_t)(t & 1) * ldgs * M;              // dbeta of this one
+    const bool got_y = !skip_mv;
+    const unsigned b = xc & 1;
+    const unsigned tag = xc + 1;
+    T* Yb = Ybuf + (size_t)b * ldgs * M;  // parities 16-byte aligned
+    if (got_y) {
+      // ---- A. y = G dbeta for this CTA's rows, delivered to every CTA
+      auto deliver = [&](int il, int k, T y) {  // local row il, instance k
+        const int e = (i0 + il) * M + k;
+        if constexpr (kGrid) {
+          if constexpr (kF32) {
+            st_tag1(xw + (size_t)b * PM + e, tag_word(__float_as_uint(y), tag));
+          } else {
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(y);
+            st_tag2(xw + ((size_t)b * PM + e) * 2, tag_word((uint32_t)bits, tag),
+                    tag_word((uint32_t)(bits >> 32), tag));
+          }
+        } else if constexpr (kF32) {
+          Yb[e] = y;
+        } else {
+          for (int r = 0; r < C; ++r) cluster.map_shared_rank(Yb, r)[e] = y;
         }
-        if constexpr (kF32) {
-          // lane l takes columns 4l .. 4l+3, then + 128: one float4 of each
-          // G row and M float4 units of dbeta per step (rows are zero-padded
-          // to ldgs, a multiple of 4). Rows resident in shared memory are
-          // addressed from Gs (shared loads), the others through gr.
-          const float* g0 = Gs + (size_t)gb * ldgs;
-          auto matvec = [&](auto row) {
-            for (int j4 = lane * 4; j4 < p; j4 += 128) {
+      };
+      if constexpr (!kWide) {
+        for (int gb = wlo; gb < whi; gb += RG) {
+          const int nv = min(RG, whi - gb);
+          T acc[V];
+#pragma unroll
+          for (int q = 0; q < V; ++q) acc[q] = T(0);
+          if constexpr (kF32) {
+            auto step4 = [&](int j4, auto gload) {
               float dv[4][M];
 #pragma unroll
               for (int q = 0; q < M; ++q) {
                 const int u = (j4 * M >> 2) + q;
-                const float4 t = *reinterpret_cast<const float4*>(Dc + ((u ^ ((u >> 3) & (M - 1))) << 2));
-                const float tv[4] = {t.x, t.y, t.z, t.w};
+                const float4 tq = *reinterpret_cast<const float4*>(Dp + ((u ^ ((u >> 3) & (M - 1))) << 2));
+                const float tv[4] = {tq.x, tq.y, tq.z, tq.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) dv[(q * 4 + e) / M][(q * 4 + e) % M] = tv[e];
               }
 #pragma unroll
               for (int r = 0; r < RG; ++r) {
-                float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (r < nv) g4 = *reinterpret_cast<const float4*>(row(r) + j4);
+                const float4 g4 = gload(r);
                 const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
 #pragma unroll
                   for (int k = 0; k < M; ++k) acc[r * M + k] = fma(gv[c], dv[c][k], acc[r * M + k]);
               }
+            };
+            if (kGregT && greg_on) {
+#pragma unroll
+              for (int sx = 0; sx < kGS; ++sx) {
+                const int j4 = lane * 4 + 128 * sx;
+                if (j4 < p) step4(j4, [&](int r) { return greg[kGregT ? r : 0][kGregT ? sx : 0]; });
+              }
+            } else {
+              const T* gr[RG];
+#pragma unroll
+              for (int r = 0; r < RG; ++r) gr[r] = grow(gb + min(r, nv - 1));
+              for (int j4 = lane * 4; j4 < p; j4 += 128)
+                step4(j4, [&](int r) {
+                  return r < nv ? *reinterpret_cast<const float4*>(gr[r] + j4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                });
             }
-          };
-          if (kGregT && greg_on) {
+          } else {
+            const T* gr[RG];
 #pragma unroll
-            for (int sx = 0; sx < kGS; ++sx) {
-              const int j4 = lane * 4 + 128 * sx;
+            for (int r = 0; r < RG; ++r) gr[r] = grow(gb + min(r, nv - 1));
+#pragma unroll 4
+            for (int j = lane; j < p; j += 32) {
+              T dv[M];
+              load_col<T, M>(Dp, j, dv);
+#pragma unroll
+              for (int r = 0; r < RG; ++r) {
+                const T g = r < nv ? gr[r][j] : T(0);
+#pragma unroll
+                for (int k = 0; k < M; ++k) acc[r * M + k] = fma(g, dv[k], acc[r * M + k]);
+              }
+            }
+          }
+          const T y = reduce_scatter<V>(acc, lane);
+          if (even && gb + rsub < whi) deliver(gb + rsub, kv, y);
+        }
+        if constexpr (kAsync) {
+          // this warp's words to every peer: a 16-byte unit inside the warp's
+          // rows as one float4 store, a unit shared with a neighbour warp word
+          // by word (i0 M is a multiple of 4: units are aligned)
+          __syncwarp();
+          const int f0 = (i0 + wlo) * M, f1 = (i0 + whi) * M;
+          const int u0 = f0 >> 2, nu = f1 > f0 ? ((f1 + 3) >> 2) - u0 : 0;
+          const uint32_t bar = xbar0 + 8 * b;
+          for (int e = lane; e < nu * (C - 1); e += 32) {
+            const int u = u0 + e / (C - 1);
+            int r = e % (C - 1);
+            r += (r >= rank);
+            const float* src = Yb + 4 * u;
+            const uint32_t ra = xs_map(xs_u32(src), r), rb = xs_map(bar, r);
+            if (4 * u >= f0 && 4 * u + 4 <= f1) {
+              xs_st4(ra, *reinterpret_cast<const float4*>(src), rb);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                if (4 * u + q >= f0 && 4 * u + q < f1) xs_st1(ra + 4 * q, __float_as_uint(src[q]), rb);
+            }
+          }
+        }
+      } else {
+        // column segments: warp w takes segments w, w + NW, ...; per segment
+        // and group of 16 / M rows one reduce-scatter of the lanes' partial
+        // sums into part[segment][row][instance]
+        constexpr int RGW = 16 / M;
+        for (int s = warp; s < nseg; s += NW) {
+          const int j4 = 128 * s + lane * 4;
+          float dv[4][M];
+          if constexpr (kF32) {
+#pragma unroll
+            for (int q = 0; q < M; ++q) {
+              float4 tq = make_float4(0.f, 0.f, 0.f, 0.f);
               if (j4 < p) {
-                float dv[4][M];
+                const int u = (j4 * M >> 2) + q;
+                tq = *reinterpret_cast<const float4*>(Dp + ((u ^ ((u >> 3) & (M - 1))) << 2));
+              }
+              const float tv[4] = {tq.x, tq.y, tq.z, tq.w};
 #pragma unroll
-                for (int q = 0; q < M; ++q) {
-                  const int u = (j4 * M >> 2) + q;
-                  const float4 t = *reinterpret_cast<const float4*>(Dc + ((u ^ ((u >> 3) & (M - 1))) << 2));
-                  const float tv[4] = {t.x, t.y, t.z, t.w};
+              for (int e = 0; e < 4; ++e) dv[(q * 4 + e) / M][(q * 4 + e) % M] = tv[e];
+            }
+          }
+          for (int rg = 0; rg < R; rg += RGW) {
+            T acc[16];
 #pragma unroll
-                  for (int e = 0; e < 4; ++e) dv[(q * 4 + e) / M][(q * 4 + e) % M] = tv[e];
-                }
+            for (int q = 0; q < 16; ++q) acc[q] = T(0);
+            if constexpr (kF32) {
+              if (j4 < p) {
 #pragma unroll
-                for (int r = 0; r < RG; ++r) {
-                  const float4 g4 = greg[kGregT ? r : 0][kGregT ? sx : 0];
+                for (int r = 0; r < RGW; ++r) {
+                  float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                  if (rg + r < R) {
+                    if (kWregT && wreg_on) {
+#pragma unroll
+                      for (int q = 0; q < kWideRows; ++q)
+                        if (q == rg + r) g4 = wreg[kWregT ? q : 0];
+                    } else {
+                      g4 = *reinterpret_cast<const float4*>(grow(rg + r) + j4);
+                    }
+                  }
                   const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
                   for (int c = 0; c < 4; ++c)
@@ -528,419 +437,417 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
                     for (int k = 0; k < M; ++k) acc[r * M + k] = fma(gv[c], dv[c][k], acc[r * M + k]);
                 }
               }
-            }
-          } else if (gb + nv <= smem_rows) {
-            matvec([&](int r) { return g0 + (size_t)r * ldgs; });
-          } else {
-            matvec([&](int r) { return gr[r]; });
-          }
-        } else {
-#pragma unroll 4
-          for (int j = lane; j < p; j += 32) {
-            T dv[M];
-            load_col<T, M>(Dc, j, dv);
-#pragma unroll
-            for (int r = 0; r < RG; ++r) {
-              const T g = r < nv ? gr[r][j] : T(0);
-#pragma unroll
-              for (int k = 0; k < M; ++k) acc[r * M + k] = fma(g, dv[k], acc[r * M + k]);
-            }
-          }
-        }
-        y = reduce_scatter<V>(acc, lane);
-      }
-      const int i = gb + rsub;  // this lane's row (local index)
-      if (regst) {
-        if (own) {
-          if (my_inst && !skip_mv) {
-            const T incr = fma(my_d, r_dn, -y);
-            if (incr != T(0)) {
-              const T h = r_uhi;
-              const T s1 = h + incr, bb = s1 - h;
-              const T e = (h - (s1 - bb)) + (incr - bb);
-              const T lo = r_ulo + e;
-              const T hi2 = s1 + lo;
-              r_ulo = lo - (hi2 - s1);
-              r_uhi = hi2;
-            }
-          }
-          T dn = T(0);
-          if (my_inst) {
-            if (!my_done) {
-              const T bn = thr_scalar<T>(my_kind, r_uhi, r_w * my_lam, my_alpha, my_gamma, my_d);
-              dn = bn - r_bet;
-              r_bet = bn;
-              bet[kq * maxR + i] = bn;
-              lmd = fmax(lmd, fabs(dn));
-              lmb = fmax(lmb, fabs(bn));
             } else {
-              lmb = fmax(lmb, fabs(r_bet));
-            }
-          }
-          st[(size_t)i * M + kq] = dn;
-          r_dn = dn;
-        }
-      } else if (even && i < whi) {
-        const int idx = kq * maxR + i;
-        if (my_inst && !skip_mv) {
-          const T incr = fma(my_d, Dc[dpos<T, M>(i0 + i, kq)], -y);
-          // an instance whose dbeta was zero (y == 0 exactly) keeps its u
-          // bit for bit, however the instances are grouped into tasks
-          if (incr == T(0)) {
-          } else if (kF32) {
-            const T h = uhi[idx];
-            const T s1 = h + incr, bb = s1 - h;
-            const T e = (h - (s1 - bb)) + (incr - bb);
-            const T lo = ulo[idx] + e;
-            const T hi2 = s1 + lo;
-            ulo[idx] = lo - (hi2 - s1);
-            uhi[idx] = hi2;
-          } else {
-            uhi[idx] += incr;
-          }
-        }
-        if (!has_group) {
-          T dn = T(0);
-          if (my_inst) {
-            if (!my_done) {
-              const T bn = thr_scalar<T>(my_kind, uhi[idx], wv[idx] * my_lam, my_alpha, my_gamma, my_d);
-              dn = bn - bet[idx];
-              bet[idx] = bn;
-              lmd = fmax(lmd, fabs(dn));
-              lmb = fmax(lmb, fabs(bn));
-            } else {
-              lmb = fmax(lmb, fabs(bet[idx]));
-            }
-          }
-          st[(size_t)i * M + kq] = dn;
-        }
-      }
-    }
-    __syncwarp();
-    if (has_group) {
-      // ---- 2a. group norms over the warp's rows: ||u_g||, or for the
-      // sparse group lasso ||v_g|| with v = S(u, w lambda tau) / d
-      for (int e = lane; e < M * nr; e += 32) {
-        const int k = e / nr, i = wlo + e % nr;
-        const int idx = k * maxR + i;
-        const int len = glen[idx];
-        if (len > 0) {
-          int kd = OEM_LASSO;
-          T lt = T(0), dd = T(1);
 #pragma unroll
-          for (int kk = 0; kk < M; ++kk)
-            if (kk == k) { kd = kind[kk]; lt = lamv[kk] * alpha[kk]; dd = dk[kk]; }
-          T s2 = T(0);
-          if (kd == OEM_SPARSE_GROUP_LASSO) {
-            for (int q = 0; q < len; ++q) {
-              const T v = fmax(fabs(uhi[idx + q]) - wv[idx + q] * lt, T(0)) / dd;
-              s2 = fma(v, v, s2);
-            }
-          } else {
-            for (int q = 0; q < len; ++q) s2 = fma(uhi[idx + q], uhi[idx + q], s2);
-          }
-          s2 = sqrt(s2);
-          for (int q = 0; q < len; ++q) gn[idx + q] = s2;
-        }
-      }
-      __syncwarp();
-      // ---- 2b. thresholds and the new dbeta (rows of this warp)
-      T mx_d[M], mx_b[M];
+              for (int c = 0; c < 4; ++c) {
+                const int j = j4 + c;
+                if (j < p) {
+                  T dd[M];
+                  load_col<T, M>(Dp, j, dd);
 #pragma unroll
-      for (int k = 0; k < M; ++k) { mx_d[k] = T(0); mx_b[k] = T(0); }
-      for (int e = lane; e < M * nr; e += 32) {
-        const int k = e / nr, i = wlo + e % nr;
-        const int idx = k * maxR + i;
-        T dn = T(0);
+                  for (int r = 0; r < RGW; ++r) {
+                    const T g = rg + r < R ? grow(rg + r)[j] : T(0);
 #pragma unroll
-        for (int kk = 0; kk < M; ++kk) {
-          if (kk == k && kk < m) {
-            if (!done[kk]) {
-              const T u = uhi[idx];
-              T bn;
-              if (kind[kk] == OEM_GROUP_LASSO) {
-                const T nrm = gn[idx];
-                const T f = nrm > T(0) ? T(1) - cgr[idx] * lamv[kk] / nrm : T(0);
-                bn = f > T(0) ? u / dk[kk] * f : T(0);
-              } else if (kind[kk] == OEM_GROUP_MCP || kind[kk] == OEM_GROUP_SCAD) {
-                // Eqs. gmcp / gscad: the scalar rule on the norm, u's direction
-                const T nrm = gn[idx];
-                const T bnorm = nrm > T(0) ? thr_scalar<T>(kind[kk] == OEM_GROUP_MCP ? OEM_MCP : OEM_SCAD, nrm,
-                                                           cgr[idx] * lamv[kk], alpha[kk], gamma[kk], dk[kk])
-                                           : T(0);
-                bn = nrm > T(0) ? u * (bnorm / nrm) : T(0);
-              } else if (kind[kk] == OEM_SPARSE_GROUP_LASSO) {
-                // Eq. sglasso (reading: the group step shrinks v by
-                // c_k lambda (1 - tau) / d)
-                const T nrm = gn[idx];
-                const T v = copysign(fmax(fabs(u) - wv[idx] * lamv[kk] * alpha[kk], T(0)) / dk[kk], u);
-                const T f = nrm > T(0) ? T(1) - cgr[idx] * lamv[kk] * (T(1) - alpha[kk]) / (dk[kk] * nrm) : T(0);
-                bn = f > T(0) ? v * f : T(0);
-              } else {
-                bn = thr_scalar<T>(kind[kk], u, wv[idx] * lamv[kk], alpha[kk], gamma[kk], dk[kk]);
-              }
-              dn = bn - bet[idx];
-              bet[idx] = bn;
-              mx_d[kk] = fmax(mx_d[kk], fabs(dn));
-              mx_b[kk] = fmax(mx_b[kk], fabs(bn));
-            } else {
-              mx_b[kk] = fmax(mx_b[kk], fabs(bet[idx]));
-            }
-          }
-        }
-        st[(size_t)i * M + k] = dn;
-      }
-#pragma unroll
-      for (int k = 0; k < M; ++k) {
-        const T a1 = warp_max(mx_d[k]), a2 = warp_max(mx_b[k]);
-        if (k == kq) { lmd = a1; lmb = a2; }
-      }
-      __syncwarp();
-    }
-    // ---- 3. DSMEM: dbeta rows to every CTA, maxima into every CTA's slot
-    {
-      if constexpr (kF32) {
-        // by 16-byte units of the buffer: a unit inside the warp's rows goes
-        // as one float4 store, a unit shared with a neighbour warp element by
-        // element (i0 is a multiple of 4, so st is unit-aligned)
-        const int f0 = (i0 + wlo) * M, f1 = (i0 + whi) * M;
-        const int u0 = f0 >> 2, nu = ((f1 + 3) >> 2) - u0;
-        T* Dn = (kGrid ? xD : Dbuf) + (size_t)nxt * ldgs * M;
-        const int CC = kGrid ? 1 : C;
-        if constexpr (kAsync) {
-          const uint32_t bar = xbar0 + 8 * nxt;
-          for (int e = lane; e < nu * C; e += 32) {
-            const int u = u0 + e / C, r = e % C;
-            float* dl = Dn + ((u ^ ((u >> 3) & (M - 1))) << 2);
-            const float* src = st + (4 * u - i0 * M);
-            const bool whole = 4 * u >= f0 && 4 * u + 4 <= f1;
-            if (r == rank) {
-              if (whole) {
-                *reinterpret_cast<float4*>(dl) = *reinterpret_cast<const float4*>(src);
-              } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                  if (4 * u + q >= f0 && 4 * u + q < f1) dl[q] = src[q];
-              }
-            } else {
-              const uint32_t ra = xs_map(xs_u32(dl), r), rb = xs_map(bar, r);
-              if (whole) {
-                xs_st4(ra, *reinterpret_cast<const float4*>(src), rb);
-              } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                  if (4 * u + q >= f0 && 4 * u + q < f1) xs_st1(ra + 4 * q, __float_as_uint(src[q]), rb);
+                    for (int k = 0; k < M; ++k) acc[r * M + k] = fma(g, dd[k], acc[r * M + k]);
+                  }
+                }
               }
             }
+            const T y = reduce_scatter<16>(acc, lane);
+            const int row = rg + (lane >> 1) / M, k = (lane >> 1) % M;
+            if ((lane & 1) == 0 && row < R) part[((size_t)s * maxR + row) * M + k] = y;
           }
-        } else {
-          for (int e = lane; e < nu * CC; e += 32) {
-            const int u = u0 + e / CC, r = e % CC;
-            float* dst = (kGrid ? Dn : cluster.map_shared_rank(Dn, r)) + ((u ^ ((u >> 3) & (M - 1))) << 2);
-            const float* src = st + (4 * u - i0 * M);
-            if (4 * u >= f0 && 4 * u + 4 <= f1) {
-              *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(src);
+        }
+        __syncthreads();
+        // segment sums in segment order, 4 consecutive words per thread
+        const int nw = R * M;
+        for (int u = tid; 4 * u < nw; u += NT) {
+          T yv4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int wd = 4 * u + q;
+            T y = T(0);
+            if (wd < nw)
+              for (int s = 0; s < nseg; ++s) y += part[((size_t)s * maxR + wd / M) * M + wd % M];
+            yv4[q] = y;
+          }
+          if constexpr (kAsync) {
+            float* dst = Yb + i0 * M + 4 * u;
+            const uint32_t bar = xbar0 + 8 * b;
+            if (4 * u + 4 <= nw) {
+              const float4 v4 = make_float4(yv4[0], yv4[1], yv4[2], yv4[3]);
+              *reinterpret_cast<float4*>(dst) = v4;
+              for (int r = 0; r < C; ++r)
+                if (r != rank) xs_st4(xs_map(xs_u32(dst), r), v4, xs_map(bar, r));
             } else {
-#pragma unroll
-              for (int q = 0; q < 4; ++q)
-                if (4 * u + q >= f0 && 4 * u + q < f1) dst[q] = src[q];
+              for (int q = 0; 4 * u + q < nw; ++q) {
+                dst[q] = yv4[q];
+                for (int r = 0; r < C; ++r)
+                  if (r != rank) xs_st1(xs_map(xs_u32(dst + q), r), __float_as_uint(yv4[q]), xs_map(bar, r));
+              }
             }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (4 * u + q < nw) deliver((4 * u + q) / M, (4 * u + q) % M, yv4[q]);
           }
         }
-      } else if constexpr (kGrid) {
-        T* Dn = xD + (size_t)nxt * ldgs * M;
-        for (int i = wlo + lane; i < whi; i += 32) store_row<T, M>(Dn, i0 + i, st + (size_t)i * M);
-      } else {
-        T* Dn = Dbuf + (size_t)nxt * ldgs * M;
-        for (int e = lane; e < nr * C; e += 32) {
-          const int i = wlo + e / C, r = e % C;
-          store_row<T, M>(cluster.map_shared_rank(Dn, r), i0 + i, st + (size_t)i * M);
-        }
       }
-      // instance kq's warp maxima end in lane S kq (lanes of one instance
-      // differ in the row bits 32 / RG .. 16 of the lane index)
-#pragma unroll
-      for (int o = 32 / RG; o < 32; o <<= 1) {
-        lmd = fmax(lmd, __shfl_xor_sync(0xffffffffu, lmd, o));
-        lmb = fmax(lmb, __shfl_xor_sync(0xffffffffu, lmb, o));
-      }
-      if (even && rsub == 0) {
-        lred[(warp * M + kq) * 2] = to_red(lmd);
-        lred[(warp * M + kq) * 2 + 1] = to_red(lmb);
-      }
-    }
-    __syncthreads();
-    // ---- 3b. warp 0: the block's maxima into slot t % 3 of every CTA (the
-    // slot is zeroed after its decisions, two iterations before its reuse)
-    if (warp == 0) {
-      constexpr int E = 2 * M;  // values per slot
-      float v = 0.f;
-      if (lane < E)
-        for (int w = 0; w < NW; ++w) v = fmax(v, lred[w * E + lane]);
+      // ---- wait for every CTA's y
       if constexpr (kAsync) {
-        // this CTA's maxima into entry [nxt][rank] of every CTA; then the
-        // wait for every peer's dbeta rows and maxima (bounded), and the
-        // maxima over the C entries into xred
-        const uint32_t bar = xbar0 + 8 * nxt;
-        unsigned int* sl = xslot + (size_t)nxt * 16 * E;
-        for (int base = 0; base < C * E; base += 32) {
-          const int e = base + lane, q = e % E, r = e / E;
-          const float val = __shfl_sync(0xffffffffu, v, q);
-          if (e < C * E) {
-            if (r == rank) sl[rank * E + q] = __float_as_uint(val);
-            else xs_st1(xs_map(xs_u32(sl + rank * E + q), r), __float_as_uint(val), xs_map(bar, r));
-          }
+        __syncwarp();
+        const uint32_t bar = xbar0 + 8 * b;
+        if (lane == 0) {
+          if (warp == 0) xs_arm(bar, (uint32_t)((p - R) * M * 4));
+          else xs_arrive(bar);
         }
-        if (lane == 0) xs_arm(bar, (uint32_t)(((p - R) * M + (C - 1) * E) * 4));
-        const uint32_t par = (uint32_t)((t >> 1) & 1);
+        const uint32_t par = (xc >> 1) & 1u;
         bool ok = xs_try(bar, par);
         if (!ok) {
           const long long t0 = clock64();
           while (!(ok = xs_try(bar, par)))
-            if (clock64() - t0 > 4000000000LL) break;
+            if (clock64() - t0 > wait_lim) break;
         }
-        ok = __all_sync(0xffffffffu, ok);
-        unsigned int mx = 0u;
-        for (int e = lane; e < C * E; e += 32) mx = max(mx, sl[e]);
-        for (int o = E; o < 32; o <<= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane < E) xred[lane] = mx;
-        if (lane == 0 && !ok) *xfail = 1u;
-      } else if constexpr (kGrid) {
-        if (lane < E && v > 0.f) atomicMax(tk.xslot + (size_t)(t % 3) * E + lane, __float_as_uint(v));
+        if (!ok) fail = true;
+      } else if constexpr (!kGrid) {
+        cluster.sync();
+      }
+      ++xc;
+    }
+
+    // ---- B, C. u update, thresholds, dbeta and maxima for this thread's elements
+    // y of element e (grid mode: polled until its tag is this exchange's)
+    auto poll = [&](int e) -> T {
+      if constexpr (kGrid) {
+        if (fail) return T(0);  // a wait of this iteration expired already
+        const unsigned want = tag;
+        long long t0 = 0;
+        for (int tries = 0;; ++tries) {
+          if constexpr (kF32) {
+            const unsigned long long w = ld_tag1(xw + (size_t)b * PM + e);
+            if ((unsigned)(w >> 32) == want) return __uint_as_float((uint32_t)w);
+          } else {
+            unsigned long long w0, w1;
+            ld_tag2(xw + ((size_t)b * PM + e) * 2, w0, w1);
+            if ((unsigned)(w0 >> 32) == want && (unsigned)(w1 >> 32) == want)
+              return __longlong_as_double((long long)(((w1 & 0xffffffffull) << 32) | (w0 & 0xffffffffull)));
+          }
+          if (tries == 0) t0 = clock64();
+          else if (clock64() - t0 > wait_lim) { fail = true; return T(0); }
+        }
       } else {
-        unsigned int* slot = red + (size_t)(t % 3) * E;
-        for (int base = 0; base < C * E; base += 32) {
-          const int e = base + lane, q = e % E;
-          const float val = __shfl_sync(0xffffffffu, v, q);
-          if (e < C * E && val > 0.f)
-            atomicMax(cluster.map_shared_rank(slot + q, e / E), __float_as_uint(val));
-        }
+        return Yb[e];
       }
-    }
-    if constexpr (kGrid) {
-      if (!group_barrier(tk.xbar, (unsigned)C, bar_gen)) {
-        if (tid == 0) atomicOr(P.dstatus, kStatTimeout);
-        break;
-      }
-      // the slot into this CTA's table (read below like the cluster slot)
-      if (tid < 2 * M) red[(size_t)(t % 3) * M * 2 + tid] = ld_relaxed_gpu(tk.xslot + (size_t)(t % 3) * M * 2 + tid);
-      __syncthreads();
-    } else if constexpr (kAsync) {
-      __syncthreads();
-      if (*xfail) {
-        if (tid == 0) atomicOr(P.dstatus, kStatTimeout);
-        break;
-      }
-    } else {
-      cluster.sync();
-    }
-    // ---- 4. decisions (every thread, same data, same result)
-    {
-      const unsigned int* slot = kAsync ? xred : red + (size_t)(t % 3) * M * 2;
-      int anyd = 0;
-      all_done = 1;
+    };
+    T yr[kRepJR];
 #pragma unroll
-      for (int k = 0; k < M; ++k) {
-        if (k >= m || done[k]) continue;
-        const T md = (T)from_red(slot[2 * k]), mb = (T)from_red(slot[2 * k + 1]);
-        if (md > T(0)) anyd = 1;
-        const int it = ++its[k];
-        const bool conv = md <= tol * fmax(T(1), mb);
-        if (conv || it >= P.max_iter) {
-          const int l = lidx[k];
-          if (rank == 0 && tid == 0) {
-            const size_t o = (size_t)k * L + l;
-            tk.iters[o] = it;
-            tk.conv[o] = conv ? 1 : 0;
-            if (!conv) atomicOr(P.dstatus, kStatNotConv);
-          }
-          double* out = tk.beta + ((size_t)k * L + l) * p + i0;
-          for (int i = wlo + lane; i < whi; i += 32) out[i] = (double)bet[k * maxR + i];
-          its[k] = 0;
-          lidx[k] = l + 1;
-          if (l + 1 >= L) done[k] = 1;
-          else lamv[k] = (T)tk.lam[(size_t)k * L + l + 1];
-        }
-        all_done &= done[k];
-      }
-      skip_mv = !anyd;
+    for (int j = 0; j < kRepJR; ++j) yr[j] = T(0);
+    if (got_y) {
+      if constexpr (kGrid) {
+        // first the loads of every register element, then the checks
+        unsigned long long wv[kRepJR][2];
 #pragma unroll
-      for (int k = 0; k < M; ++k)
-        if (k == kq) { my_lam = lamv[k]; my_done = done[k]; }
-      if (tid < M * 2) {
-        red[(size_t)((t + 2) % 3) * M * 2 + tid] = 0u;
-        if (kGrid && rank == 0) tk.xslot[(size_t)((t + 2) % 3) * M * 2 + tid] = 0u;
-      }
-    }
-    ++t;
-    ++loops;
-    if (P.max_loops > 0 && loops >= P.max_loops) break;
-  }
-  if (regst && own) {
-    uhi[kq * maxR + i_own] = r_uhi;
-    ulo[kq * maxR + i_own] = r_ulo;
-  }
-  __syncwarp();
-  // ---- save the state for a later launch (serving): apply the pending dbeta
-  if (tk.st_u) {
-    if (!all_done && !skip_mv) {
-      const T* Dc = Dbuf + (size_t)(t & 1) * ldgs * M;
-      for (int ib = wlo; ib < whi; ++ib) {
-        const T* g0 = (ib < smem_rows) ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
-        T acc[M];
-#pragma unroll
-        for (int k = 0; k < M; ++k) acc[k] = T(0);
-        // same column order and lane tree as the loop's mat-vec, so a resumed
-        // path is the same as an uninterrupted one
-        if constexpr (kF32) {
-          for (int j4 = lane * 4; j4 < p; j4 += 128) {
-            const float4 g4 = *reinterpret_cast<const float4*>(g0 + j4);
-            const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-#pragma unroll
-              for (int k = 0; k < M; ++k) acc[k] = fma(gv[c], Dc[dpos<T, M>(j4 + c, k)], acc[k]);
-          }
-        } else {
-          for (int j = lane; j < p; j += 32) {
-            T dv[M];
-            load_col<T, M>(Dc, j, dv);
-            const T g = g0[j];
-#pragma unroll
-            for (int k = 0; k < M; ++k) acc[k] = fma(g, dv[k], acc[k]);
+        for (int j = 0; j < kRepJR; ++j) {
+          const int e = tid + NT * j;
+          wv[j][0] = wv[j][1] = 0ull;
+          if (e < PM) {
+            if constexpr (kF32) wv[j][0] = ld_tag1(xw + (size_t)b * PM + e);
+            else ld_tag2(xw + ((size_t)b * PM + e) * 2, wv[j][0], wv[j][1]);
           }
         }
 #pragma unroll
-        for (int k = 0; k < M; ++k) acc[k] = warp_sum(acc[k]);
-        if (lane == 0) {
-#pragma unroll
-          for (int k = 0; k < M; ++k) {
-            if (k >= m) continue;
-            const int idx = k * maxR + ib;
-            const T incr = fma(dk[k], Dc[dpos<T, M>(i0 + ib, k)], -acc[k]);
-            if (incr == T(0)) {
-            } else if (kF32) {
-              const T h = uhi[idx];
-              const T s = h + incr, bb = s - h;
-              const T e = (h - (s - bb)) + (incr - bb);
-              const T lo = ulo[idx] + e;
-              const T hi2 = s + lo;
-              ulo[idx] = lo - (hi2 - s);
-              uhi[idx] = hi2;
+        for (int j = 0; j < kRepJR; ++j) {
+          const int e = tid + NT * j;
+          if (e < PM) {
+            bool hit;
+            if constexpr (kF32) hit = (unsigned)(wv[j][0] >> 32) == tag;
+            else hit = (unsigned)(wv[j][0] >> 32) == tag && (unsigned)(wv[j][1] >> 32) == tag;
+            if (hit) {
+              if constexpr (kF32) yr[j] = __uint_as_float((uint32_t)wv[j][0]);
+              else yr[j] = __longlong_as_double((long long)(((wv[j][1] & 0xffffffffull) << 32) | (wv[j][0] & 0xffffffffull)));
             } else {
-              uhi[idx] += incr;
+              yr[j] = poll(e);
             }
           }
         }
+      } else {
+#pragma unroll
+        for (int j = 0; j < kRepJR; ++j) {
+          const int e = tid + NT * j;
+          if (e < PM) yr[j] = Yb[e];
+        }
       }
-      __syncwarp();
     }
-    for (int e = lane; e < m * (whi - wlo); e += 32) {
-      const int k = e / (whi - wlo), i = wlo + e % (whi - wlo);
-      const size_t o = (size_t)k * p + i0 + i;
-      tk.st_u[2 * o] = (double)uhi[k * maxR + i];
-      tk.st_u[2 * o + 1] = (double)ulo[k * maxR + i];
-      tk.st_beta[o] = (double)bet[k * maxR + i];
+    const bool upd = got_y && my_inst;
+    // u <- u + (d dbeta - y), TwoSum in float32
+    auto u_update = [&](T& uh, T& ul, T dnp, T y) {
+      if (!upd) return;
+      const T incr = fma(my_d, dnp, -y);
+      // an instance whose dbeta was zero (y == 0 exactly) keeps its u bit
+      // for bit, however the instances are grouped into tasks
+      if (incr == T(0)) return;
+      if constexpr (kF32) {
+        const T h = uh;
+        const T s1 = h + incr, bb = s1 - h;
+        const T e = (h - (s1 - bb)) + (incr - bb);
+        const T lo = ul + e;
+        const T hi2 = s1 + lo;
+        ul = lo - (hi2 - s1);
+        uh = hi2;
+      } else {
+        uh += incr;
+      }
+    };
+    T lmd = T(0), lmb = T(0);  // this thread's running max |dbeta|, |beta| (instance kq)
+    if (final_pass) {
+      // the pending dbeta applied to u, for a resumed launch to continue from
+#pragma unroll
+      for (int j = 0; j < kRepJR; ++j) {
+        const int e = tid + NT * j;
+        if (e < PM) { u_update(r_uh[j], r_ul[j], r_dn[j], yr[j]); uhs[e] = r_uh[j]; uls[e] = r_ul[j]; }
+      }
+      for (int j = kRepJR; j < nJ; ++j) {
+        const int e = tid + NT * j;
+        if (e >= PM) break;
+        T uh = uhs[e], ul = uls[e];
+        u_update(uh, ul, Dp[dpos<T, M>(e / M, kq)], got_y ? poll(e) : T(0));
+        uhs[e] = uh; uls[e] = ul;
+      }
+      break;
+    }
+    if (!has_group) {
+      auto scalar_step = [&](T& uh, T& ul, T& bv, T wt, T dnp, T y) -> T {
+        u_update(uh, ul, dnp, y);
+        T dn = T(0);
+        if (my_inst) {
+          if (!my_done) {
+            const T bn = thr_scalar<T>(my_kind, uh, wt * my_lam, my_alpha, my_gamma, my_d);
+            dn = bn - bv;
+            bv = bn;
+            lmd = fmax(lmd, fabs(dn));
+            lmb = fmax(lmb, fabs(bn));
+          } else {
+            lmb = fmax(lmb, fabs(bv));
+          }
+        }
+        return dn;
+      };
+#pragma unroll
+      for (int j = 0; j < kRepJR; ++j) {
+        const int e = tid + NT * j;
+        if (e < PM) {
+          const T dn = scalar_step(r_uh[j], r_ul[j], r_b[j], r_w[j], r_dn[j], yr[j]);
+          r_dn[j] = dn;
+          Dn[dpos<T, M>(e / M, kq)] = dn;
+        }
+      }
+      for (int j = kRepJR; j < nJ; ++j) {
+        const int e = tid + NT * j;
+        if (e >= PM) break;
+        const int i = e / M;
+        T uh = uhs[e], ul = uls[e], bv = bes[e];
+        const T dn = scalar_step(uh, ul, bv, weight(i), Dp[dpos<T, M>(i, kq)], got_y ? poll(e) : T(0));
+        uhs[e] = uh; uls[e] = ul; bes[e] = bv;
+        Dn[dpos<T, M>(i, kq)] = dn;
+      }
+    } else {
+      // ---- C1. u update of every element (kept in shared memory for the norms)
+#pragma unroll
+      for (int j = 0; j < kRepJR; ++j) {
+        const int e = tid + NT * j;
+        if (e < PM) { u_update(r_uh[j], r_ul[j], r_dn[j], yr[j]); uhs[e] = r_uh[j]; }
+      }
+      for (int j = kRepJR; j < nJ; ++j) {
+        const int e = tid + NT * j;
+        if (e >= PM) break;
+        T uh = uhs[e], ul = uls[e];
+        u_update(uh, ul, Dp[dpos<T, M>(e / M, kq)], got_y ? poll(e) : T(0));
+        uhs[e] = uh; uls[e] = ul;
+      }
+      __syncthreads();
+      // ---- C2. group norms ||u_g|| (sparse group lasso: ||v_g||, v = S(u, w lambda tau) / d)
+      for (int e2 = tid; e2 < PM; e2 += NT) {
+        const int len = gls[e2];
+        if (len == 0) continue;
+        const int k = e2 / p, i = e2 % p;
+        int kd = OEM_LASSO;
+        T lt = T(0), dd = T(1);
+        const float* gw32 = nullptr;
+        const double* gw64 = nullptr;
+#pragma unroll
+        for (int kk = 0; kk < M; ++kk)
+          if (kk == k) { kd = kind[kk]; lt = lamv[kk] * alpha[kk]; dd = dk[kk]; }
+        if (kd == OEM_SPARSE_GROUP_LASSO) { gw32 = tk.pens[k].w32; gw64 = tk.pens[k].w64; }
+        T s2 = T(0);
+        for (int q = 0; q < len; ++q) {
+          const T u = uhs[(i + q) * M + k];
+          if (kd == OEM_SPARSE_GROUP_LASSO) {
+            T wq = T(1);
+            if constexpr (kF32) { if (gw32) wq = (T)gw32[i + q]; }
+            else { if (gw64) wq = (T)gw64[i + q]; }
+            const T v = fmax(fabs(u) - wq * lt, T(0)) / dd;
+            s2 = fma(v, v, s2);
+          } else {
+            s2 = fma(u, u, s2);
+          }
+        }
+        s2 = sqrt(s2);
+        for (int q = 0; q < len; ++q) gns[e2 + q] = s2;
+      }
+      __syncthreads();
+      // ---- C3. thresholds (Eqs. glasso, gmcp, gscad, sglasso; scalar ones for
+      // scalar instances of the task)
+      auto group_step = [&](T uh, T& bv, T wt, int i) -> T {
+        T dn = T(0);
+        if (my_inst) {
+          if (!my_done) {
+            const T u = uh;
+            const int g2 = kq * p + i;
+            T bn;
+            if (my_kind == OEM_GROUP_LASSO) {
+              const T nrm = gns[g2];
+              const T f = nrm > T(0) ? T(1) - cgs[g2] * my_lam / nrm : T(0);
+              bn = f > T(0) ? u / my_d * f : T(0);
+            } else if (my_kind == OEM_GROUP_MCP || my_kind == OEM_GROUP_SCAD) {
+              const T nrm = gns[g2];
+              const T bnorm = nrm > T(0) ? thr_scalar<T>(my_kind == OEM_GROUP_MCP ? OEM_MCP : OEM_SCAD, nrm,
+                                                         cgs[g2] * my_lam, my_alpha, my_gamma, my_d)
+                                         : T(0);
+              bn = nrm > T(0) ? u * (bnorm / nrm) : T(0);
+            } else if (my_kind == OEM_SPARSE_GROUP_LASSO) {
+              // reading of Eq. sglasso: the group step shrinks v by c_k lambda (1 - tau) / d
+              const T nrm = gns[g2];
+              const T v = copysign(fmax(fabs(u) - wt * my_lam * my_alpha, T(0)) / my_d, u);
+              const T f = nrm > T(0) ? T(1) - cgs[g2] * my_lam * (T(1) - my_alpha) / (my_d * nrm) : T(0);
+              bn = f > T(0) ? v * f : T(0);
+            } else {
+              bn = thr_scalar<T>(my_kind, u, wt * my_lam, my_alpha, my_gamma, my_d);
+            }
+            dn = bn - bv;
+            bv = bn;
+            lmd = fmax(lmd, fabs(dn));
+            lmb = fmax(lmb, fabs(bn));
+          } else {
+            lmb = fmax(lmb, fabs(bv));
+          }
+        }
+        return dn;
+      };
+#pragma unroll
+      for (int j = 0; j < kRepJR; ++j) {
+        const int e = tid + NT * j;
+        if (e < PM) {
+          const T dn = group_step(r_uh[j], r_b[j], r_w[j], e / M);
+          r_dn[j] = dn;
+          Dn[dpos<T, M>(e / M, kq)] = dn;
+        }
+      }
+      for (int j = kRepJR; j < nJ; ++j) {
+        const int e = tid + NT * j;
+        if (e >= PM) break;
+        const int i = e / M;
+        T bv = bes[e];
+        const T dn = group_step(uhs[e], bv, weight(i), i);
+        bes[e] = bv;
+        Dn[dpos<T, M>(i, kq)] = dn;
+      }
+    }
+    // ---- D. block maxima per instance: every CTA holds all rows, so these
+    // are the task's maxima
+    {
+#pragma unroll
+      for (int o = M; o < 32; o <<= 1) {
+        lmd = fmax(lmd, __shfl_xor_sync(0xffffffffu, lmd, o));
+        lmb = fmax(lmb, __shfl_xor_sync(0xffffffffu, lmb, o));
+      }
+      float* lr = lred + (size_t)(t & 1) * NW * 2 * M;
+      if (lane < M) {
+        lr[(warp * M + lane) * 2] = to_red(lmd);
+        lr[(warp * M + lane) * 2 + 1] = to_red(lmb);
+      }
+    }
+    if (__syncthreads_or(fail ? 1 : 0)) {
+      fail = true;
+      break;
+    }
+    float mx[2 * M];
+    {
+      const float* lr = lred + (size_t)(t & 1) * NW * 2 * M;
+      constexpr int E = 2 * M;
+      float v = 0.f;
+      for (int e = lane; e < NW * E; e += 32) v = fmax(v, lr[e]);  // e % E == lane % E
+#pragma unroll
+      for (int o = E; o < 32; o <<= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+#pragma unroll
+      for (int q = 0; q < E; ++q) mx[q] = __shfl_sync(0xffffffffu, v, q);
+    }
+    // ---- decisions (every thread, same data, same result)
+    int anyd = 0;
+    all_done = 1;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      if (k >= m || done[k]) continue;
+      const T md = (T)mx[2 * k], mb = (T)mx[2 * k + 1];
+      if (md > T(0)) anyd = 1;
+      const int it = ++its[k];
+      const bool conv = md <= tol * fmax(T(1), mb);
+      if (conv || it >= P.max_iter) {
+        const int l = lidx[k];
+        if (rank == 0 && tid == 0) {
+          const size_t o = (size_t)k * L + l;
+          tk.iters[o] = it;
+          tk.conv[o] = conv ? 1 : 0;
+          if (!conv) atomicOr(P.dstatus, kStatNotConv);
+        }
+        if (k == kq) {  // this CTA writes the rows of its slice
+          double* out = tk.beta + ((size_t)k * L + l) * p;
+#pragma unroll
+          for (int j = 0; j < kRepJR; ++j) {
+            const int e = tid + NT * j, i = e / M;
+            if (e < PM && i >= i0 && i < i0 + R) out[i] = (double)r_b[j];
+          }
+          for (int j = kRepJR; j < nJ; ++j) {
+            const int e = tid + NT * j, i = e / M;
+            if (e >= PM) break;
+            if (i >= i0 && i < i0 + R) out[i] = (double)bes[e];
+          }
+        }
+        its[k] = 0;
+        lidx[k] = l + 1;
+        if (l + 1 >= L) done[k] = 1;
+        else lamv[k] = (T)tk.lam[(size_t)k * L + l + 1];
+      }
+      all_done &= done[k];
+    }
+    skip_mv = !anyd;
+#pragma unroll
+    for (int k = 0; k < M; ++k)
+      if (k == kq) { my_lam = lamv[k]; my_done = done[k]; }
+    ++t;
+    ++loops;
+    if (!all_done && P.max_loops > 0 && loops >= P.max_loops) {
+      if (tk.st_u && !skip_mv) final_pass = true;
+      else break;
+    }
+  }
+  if (__syncthreads_or(fail ? 1 : 0) && tid == 0) atomicOr(P.dstatus, kStatTimeout);
+  // ---- save the state for a later launch (serving): each CTA its slice
+  if (tk.st_u) {
+#pragma unroll
+    for (int j = 0; j < kRepJR; ++j) {
+      const int e = tid + NT * j, i = e / M;
+      if (e < PM) { uhs[e] = r_uh[j]; uls[e] = r_ul[j]; bes[e] = r_b[j]; }
+      (void)i;
+    }
+    for (int j = 0; j < nJ; ++j) {
+      const int e = tid + NT * j, i = e / M;
+      if (e >= PM) break;
+      if (my_inst && i >= i0 && i < i0 + R) {
+        const size_t o = (size_t)kq * p + i;
+        tk.st_u[2 * o] = (double)uhs[e];
+        tk.st_u[2 * o + 1] = (double)uls[e];
+        tk.st_beta[o] = (double)bes[e];
+      }
     }
     if (rank == 0 && tid == 0) {
       for (int k = 0; k < m; ++k) {
@@ -958,10 +865,9 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
     cluster.sync();  // no CTA leaves while a peer could still address its shared memory
 }
 
-size_t oem_iter_smem_fixed(int p, int npen, int max_rows, int precision) {
-  const int M = oem_iter_mpad(npen);
+size_t oem_iter_smem_fixed(int p, int M, int max_rows, int precision, bool grid, bool groups) {
   const int tsz = precision == OEM_ITER_F64 ? 8 : 4;
-  return iter_smem_layout(p, M, max_rows, tsz, 0).total;
+  return rep_smem_layout(p, oem_iter_mpad(M), tsz, p > kIterWideP, grid, groups, max_rows, 0).total;
 }
 
 size_t oem_iter_smem_per_row(int p, int precision) {
@@ -969,10 +875,15 @@ size_t oem_iter_smem_per_row(int p, int precision) {
   return (size_t)((p + 3) & ~3) * tsz;
 }
 
-template <typename T, int M, bool kGrid, int RG>
+size_t oem_iter_xbuf_bytes(int p, int M, int precision) {
+  const int W = precision == OEM_ITER_F64 ? 2 : 1;
+  return (2 * (size_t)p * oem_iter_mpad(M) * W * 8 + 255) & ~(size_t)255;
+}
+
+template <typename T, int M, bool kGrid, int RG, bool kWide>
 static cudaError_t launch_t(const IterLaunch& P, cudaStream_t s, bool query, int* out) {
-  constexpr int NT = iter_threads<T, M>();
-  auto kfn = oem_iter_kernel<T, M, NT, kGrid, RG>;
+  constexpr int NT = rep_threads(kWide);
+  auto kfn = oem_iter_kernel<T, M, NT, kGrid, RG, kWide>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -1009,22 +920,23 @@ static cudaError_t launch_t(const IterLaunch& P, cudaStream_t s, bool query, int
   return cudaLaunchKernelEx(&cfg, kfn, P);
 }
 
-// Row group: 16 / M rows, or 4 when no warp owns more than 4 rows (the
-// instances then fill fewer sums per lane and no load is wasted).
-template <typename T, int M, int RG>
-static cudaError_t dispatch_r(const IterLaunch& P, cudaStream_t s, bool q, int* out) {
-  return P.grid ? launch_t<T, M, true, RG>(P, s, q, out) : launch_t<T, M, false, RG>(P, s, q, out);
+// Row group of the row-owned mat-vec: 16 / M rows, or 4 when no warp owns
+// more than 4 rows (the instances then fill fewer sums per lane and no load
+// is wasted); the wide mat-vec always takes 16 / M.
+template <typename T, int M, bool kGrid>
+static cudaError_t dispatch_w(const IterLaunch& P, cudaStream_t s, bool q, int* out) {
+  if (P.wide) return launch_t<T, M, kGrid, 16 / M, true>(P, s, q, out);
+  constexpr int RGF = 16 / M;
+  if constexpr (RGF > 4) {
+    constexpr int NW = rep_threads(false) / 32;
+    if ((P.max_rows + NW - 1) / NW <= 4) return launch_t<T, M, kGrid, 4, false>(P, s, q, out);
+  }
+  return launch_t<T, M, kGrid, RGF, false>(P, s, q, out);
 }
 template <typename T, int M>
 static cudaError_t dispatch_g(const IterLaunch& P, cudaStream_t s, bool q, int* out) {
-  constexpr int RGF = 16 / M;
-  if constexpr (RGF > 4) {
-    constexpr int NW = iter_threads<T, M>() / 32;
-    if ((P.max_rows + NW - 1) / NW <= 4) return dispatch_r<T, M, 4>(P, s, q, out);
-  }
-  return dispatch_r<T, M, RGF>(P, s, q, out);
+  return P.grid ? dispatch_w<T, M, true>(P, s, q, out) : dispatch_w<T, M, false>(P, s, q, out);
 }
-
 template <typename T>
 static cudaError_t dispatch_m(const IterLaunch& P, cudaStream_t s, bool q, int* out) {
   switch (P.M) {

@@ -1,0 +1,900 @@
+// The OEM iteration (Section 2.1 Step 2, Section 2.2 updates) for every
+// (Gram, penalty) instance, warm-started along each instance's lambda grid:
+// the row-owned kernel, used where the replicated kernel of oem_iter.cu does
+// not fit (p above kIterRepMaxP: u, beta and dbeta of all rows would not fit
+// in one CTA's shared memory).
+//
+// Per instance and iteration: u = c + d beta - G beta; beta <- threshold(u).
+// The code carries u itself and updates it by the change of beta,
+//   u_{t+1} = u_t + d (beta_{t+1} - beta_t) - G (beta_{t+1} - beta_t),
+// which is the same quantity; the mat-vec then acts on a vector that shrinks
+// as the iteration converges, so float32 products stay accurate, and u is
+// kept as a float32 (hi, lo) pair so its rounding does not accumulate.
+//
+// One thread-block cluster per task (a Gram with its instances; tasks of one
+// launch may differ in p). CTA r of the cluster owns rows [slice[r],
+// slice[r+1]) of G, u and beta; inside the CTA every warp owns a contiguous
+// block of those rows (aligned to group starts for the group lasso). Per
+// iteration a warp, on its own rows and with no block-wide barrier:
+//   1. forms (G dbeta)_i for all instances of the task at once, 16 / M rows
+//      at a time so that one pass over dbeta serves the group (lane l reads
+//      columns 4l .. 4l+3, + 128, ...; G rows in registers when a warp has
+//      one row group and p <= 512, else resident in shared memory, the rest
+//      read from L2); a reduce-scatter leaves each (row, instance) sum in one
+//      lane pair, which updates u_i and, without groups, applies the
+//      threshold;
+//   2. for group penalties, forms the group norms and thresholds afterwards;
+//   3. writes its dbeta rows into the shared memory of every CTA of the
+//      cluster and its max|dbeta|, max|beta| per instance into the block's
+//      table.
+// One block barrier, then one warp sends the CTA's maxima to every CTA.
+// Float32 iteration: the dbeta rows and the maxima go out as st.async
+// stores, each counting its bytes on the receiving CTA's mbarrier for that
+// buffer, so a CTA waits (bounded) for exactly the bytes addressed to it and
+// there is no cluster barrier in the loop; one warp then takes the maximum
+// over the C entries. Float64 iteration: plain DSMEM stores, DSMEM atomic
+// max into every CTA's slot (order-preserving 32-bit images) and one cluster
+// barrier per iteration. Every thread then takes the same convergence
+// decisions from the same values. A launch may stop after a loop budget and
+// save its state (serving), to be resumed by a later launch.
+//
+// Grid mode (large p: the Gram rows of a task do not fit in the shared memory
+// of one cluster, at most 16 SMs, but fit in that of C > 16 CTAs): the C CTAs
+// of a task are an ordinary group of a cooperative launch, one per SM. Each
+// iteration a CTA reads the whole dbeta from global memory (L2) into its
+// shared memory, writes its own rows of the new dbeta back to global memory,
+// folds its maxima into a global slot with atomics, and waits at a
+// global-memory barrier of the group (bounded spin) instead of the cluster
+// barrier. The arithmetic is the same as in cluster mode.
+#include "oem_internal.cuh"
+#include "iter_common.cuh"
+
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
+namespace oem {
+
+
+// Threads per CTA. Every warp reads the whole dbeta once per group of its
+// rows, so more warps than needed to spread a CTA's rows only add
+// shared-memory traffic.
+template <typename T, int M>
+constexpr int iter_threads() { return 256; }
+
+// Shared-memory carve-up (byte offsets, 16-byte aligned). The dbeta buffers
+// have ldgs = round_up(p, 4) rows; rows p.. stay zero.
+struct IterSmem {
+  size_t dbuf, uhi, ulo, beta, w, gn, cgr, glen, st, lred, red, xbar, xslot, xred, gs, total;
+};
+constexpr int kIterMaxWarps = 16;
+__host__ __device__ inline IterSmem iter_smem_layout(int p, int M, int maxR, int tsz, int smem_rows) {
+  const int ldgs = (p + 3) & ~3;
+  IterSmem L;
+  size_t o = 0;
+  L.dbuf = o;  o = al16(o + (size_t)2 * ldgs * M * tsz);
+  L.uhi = o;   o = al16(o + (size_t)M * maxR * tsz);
+  L.ulo = o;   o = al16(o + (size_t)M * maxR * tsz);
+  L.beta = o;  o = al16(o + (size_t)M * maxR * tsz);
+  L.w = o;     o = al16(o + (size_t)M * maxR * tsz);
+  L.gn = o;    o = al16(o + (size_t)M * maxR * tsz);
+  L.cgr = o;   o = al16(o + (size_t)M * maxR * tsz);
+  L.glen = o;  o = al16(o + (size_t)M * maxR * 4);
+  L.st = o;    o = al16(o + (size_t)maxR * M * tsz);
+  L.lred = o;  o = al16(o + (size_t)kIterMaxWarps * M * 2 * 4);
+  L.red = o;   o = al16(o + (size_t)3 * M * 2 * 4);
+  L.xbar = o;  o = al16(o + 2 * 8);
+  L.xslot = o; o = al16(o + (size_t)2 * 16 * M * 2 * 4);
+  L.xred = o;  o = al16(o + (size_t)(M * 2 + 1) * 4);
+  L.gs = o;    o = al16(o + (size_t)smem_rows * ldgs * tsz);
+  L.total = o;
+  return L;
+}
+
+template <typename T, int M, int NT, bool kGrid, int RG>
+__global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
+  constexpr int NW = NT / 32;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = P.C;
+  const int rank = kGrid ? (int)(blockIdx.x % C) : (int)cluster.block_rank();
+  const IterTask& tk = P.tasks[blockIdx.x / C];
+  const int p = tk.p, L = tk.L, m = tk.npen, maxR = tk.max_rows;
+  const int i0 = kGrid ? tk.gslice[rank] : tk.slice[rank];
+  const int R = (kGrid ? tk.gslice[rank + 1] : tk.slice[rank + 1]) - i0;
+  T* const xD = reinterpret_cast<T*>(tk.xD);  // grid mode
+  unsigned bar_gen = 0;
+  const long long wait_lim = P.wait_cycles > 0 ? P.wait_cycles : 4000000000LL;
+  const int ldgs = (p + 3) & ~3, smem_rows = tk.smem_rows;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr bool kF32 = sizeof(T) == 4;
+
+  extern __shared__ __align__(16) unsigned char smem[];
+  const IterSmem Ls = iter_smem_layout(p, M, maxR, (int)sizeof(T), tk.smem_rows);
+  T* Dbuf = reinterpret_cast<T*>(smem + Ls.dbuf);
+  T* uhi = reinterpret_cast<T*>(smem + Ls.uhi);
+  T* ulo = reinterpret_cast<T*>(smem + Ls.ulo);
+  T* bet = reinterpret_cast<T*>(smem + Ls.beta);
+  T* wv = reinterpret_cast<T*>(smem + Ls.w);
+  T* gn = reinterpret_cast<T*>(smem + Ls.gn);
+  T* cgr = reinterpret_cast<T*>(smem + Ls.cgr);
+  int* glen = reinterpret_cast<int*>(smem + Ls.glen);
+  T* st = reinterpret_cast<T*>(smem + Ls.st);
+  float* lred = reinterpret_cast<float*>(smem + Ls.lred);  // [warp][2M] block table
+  unsigned int* red = reinterpret_cast<unsigned int*>(smem + Ls.red);  // [3][2M] slots
+  T* Gs = reinterpret_cast<T*>(smem + Ls.gs);
+  constexpr bool kAsync = kF32 && !kGrid;
+  const uint32_t xbar0 = xs_u32(smem + Ls.xbar);  // mbarriers of dbeta buffers 0 / 1
+  unsigned int* xslot = reinterpret_cast<unsigned int*>(smem + Ls.xslot);  // [2][C][2M]
+  unsigned int* xred = reinterpret_cast<unsigned int*>(smem + Ls.xred);    // [2M], then the timeout flag
+  volatile unsigned int* xfail = xred + 2 * M;
+  const T* Gglob = kF32 ? reinterpret_cast<const T*>(tk.G32) : reinterpret_cast<const T*>(tk.G64);
+  const int ldgg = kF32 ? tk.ldg : p;
+  const double* cb = tk.c;
+  const T dgram = (T)tk.d[0];
+
+  // ---- per-instance parameters and control state (identical in every thread)
+  int kind[M], lidx[M], its[M], done[M];
+  T alpha[M], gamma[M], dk[M], lamv[M];
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    lidx[k] = 0; its[k] = 0; done[k] = 1;
+    kind[k] = OEM_LASSO; alpha[k] = T(1); gamma[k] = T(3); dk[k] = T(1); lamv[k] = T(0);
+    if (k < m) {
+      const DevPenalty& pen = tk.pens[k];
+      kind[k] = pen.kind;
+      alpha[k] = kF32 ? (T)pen.alpha : (T)pen.alpha64;
+      gamma[k] = kF32 ? (T)pen.gamma : (T)pen.gamma64;
+      T de = dgram;
+      if (pen.kind == OEM_MCP || pen.kind == OEM_GROUP_MCP) de = fmax(de, (T)(1.01 / pen.gamma64));
+      if (pen.kind == OEM_SCAD || pen.kind == OEM_GROUP_SCAD)
+        de = fmax(de, (T)(1.01 / (pen.gamma64 - 1.0)));
+      dk[k] = de;
+      done[k] = 0;
+      if (tk.resume) {
+        lidx[k] = tk.st_ctl[k * 4 + 0];
+        its[k] = tk.st_ctl[k * 4 + 1];
+        done[k] = tk.st_ctl[k * 4 + 2];
+      }
+      if (!done[k]) lamv[k] = (T)tk.lam[(size_t)k * L + lidx[k]];
+    }
+  }
+  bool has_group = false;
+  for (int k = 0; k < m; ++k) has_group |= (tk.pens[k].kind >= OEM_GROUP_LASSO);
+
+  // ---- this warp's contiguous row block, aligned to allowed boundaries
+  int wlo, whi;
+  {
+    const int per = (R + NW - 1) / NW;
+    auto bound = [&](int wi) {
+      if (wi <= 0) return 0;
+      if (wi >= NW) return R;
+      int b = min(R, wi * per);
+      if (tk.allowed) while (b < R && !tk.allowed[i0 + b]) ++b;
+      return b;
+    };
+    wlo = bound(warp);
+    whi = max(wlo, bound(warp + 1));
+  }
+
+  // ---- initialise u, beta, weights, groups, the G rows kept in shared memory
+  for (int e = tid; e < M * maxR; e += NT) {
+    const int k = e / maxR, i = e % maxR;
+    T hi = T(0), lo = T(0), wt = T(1), cgv = T(0), b0 = T(0);
+    int gl = 0;
+    if (k < m && i < R) {
+      const DevPenalty& pen = tk.pens[k];
+      if (tk.resume) {
+        const size_t o = (size_t)k * p + i0 + i;
+        hi = (T)tk.st_u[2 * o];
+        lo = (T)tk.st_u[2 * o + 1];
+        b0 = (T)tk.st_beta[o];
+      } else {
+        const double cv = cb[i0 + i];
+        hi = (T)cv;
+        lo = (T)(cv - (double)hi);
+      }
+      if (kF32) { if (pen.w32) wt = (T)pen.w32[i0 + i]; }
+      else { if (pen.w64) wt = (T)pen.w64[i0 + i]; }
+      if (pen.kind >= OEM_GROUP_LASSO) {
+        const int g = pen.grp[i0 + i];
+        cgv = (T)pen.cg[g];
+        if (i == 0 || pen.grp[i0 + i - 1] != g) {
+          int len = 1;
+          while (i + len < R && pen.grp[i0 + i + len] == g) ++len;
+          gl = len;
+        }
+      }
+    }
+    uhi[e] = hi; ulo[e] = lo; bet[e] = b0; wv[e] = wt; cgr[e] = cgv; glen[e] = gl; gn[e] = T(0);
+  }
+  for (int e = tid; e < 2 * ldgs * M; e += NT) Dbuf[e] = T(0);
+  for (int e = tid; e < 3 * M * 2; e += NT) red[e] = 0u;
+  if (kAsync && tid == 0) {
+    xs_init(xbar0);
+    xs_init(xbar0 + 8);
+    *xfail = 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int e = tid; e < smem_rows * ldgs; e += NT) {
+    const int i = e / ldgs, j = e % ldgs;
+    Gs[e] = (i < R && j < p) ? Gglob[(size_t)(i0 + i) * ldgg + j] : T(0);
+  }
+  if constexpr (kGrid) {
+    if (!group_barrier(tk.xbar, (unsigned)C, bar_gen, wait_lim)) {
+      if (tid == 0) atomicOr(P.dstatus, kStatTimeout);
+      return;
+    }
+  } else {
+    cluster.sync();  // every CTA initialised before any DSMEM access
+  }
+
+  // Lane roles in the row-group mat-vec: a group is RG rows (V = RG M sums);
+  // after the reduce-scatter lane l holds the sum of value v = l / S,
+  // S = 32 / V, i.e. row rsub = v / M of the group and instance kq = v % M
+  // (the first lane of each group of S acts).
+  constexpr int V = RG * M, S = 32 / V;
+  static_assert(V == 4 || V == 8 || V == 16, "row group");
+  const int vq = lane / S, rsub = vq / M, kq = vq % M;
+  const bool even = (lane % S) == 0;
+  int my_kind = OEM_LASSO;
+  T my_alpha = T(1), my_gamma = T(3), my_d = T(1), my_lam = T(0);
+  int my_done = 1;
+#pragma unroll
+  for (int k = 0; k < M; ++k)
+    if (k == kq) {
+      my_kind = kind[k]; my_alpha = alpha[k]; my_gamma = gamma[k]; my_d = dk[k];
+      my_lam = lamv[k]; my_done = done[k];
+    }
+  const bool my_inst = kq < m;
+
+  const T tol = (T)P.tol;
+  // Float32 with one row group per warp and p <= 512: the warp's G rows live
+  // in registers (lane l holds columns 4l .. 4l+3 + 128 s of each row), so the
+  // mat-vec reads only dbeta from shared memory. Same products in the same
+  // order as from shared memory.
+  constexpr int kGS = 4;                          // column steps of 128
+  constexpr bool kGregT = kF32 && RG <= 4;        // register budget: RG * kGS float4
+  const bool greg_on = kGregT && (whi - wlo) <= RG && p <= 128 * kGS;
+  float4 greg[kGregT ? RG : 1][kGregT ? kGS : 1];
+  // With one row group per warp and scalar penalties, the lane that owns row
+  // wlo + rsub of instance kq keeps u (hi, lo), beta, w and its last dbeta
+  // in registers for the whole launch (beta is still stored for the outputs,
+  // u written back at the end); the same values as in shared memory.
+  const bool regst = kF32 && greg_on && !has_group;
+  const int i_own = wlo + rsub;
+  const bool own = even && i_own < whi;
+  T r_uhi = T(0), r_ulo = T(0), r_bet = T(0), r_w = T(1), r_dn = T(0);
+  if (regst && own) {
+    const int idx = kq * maxR + i_own;
+    r_uhi = uhi[idx];
+    r_ulo = ulo[idx];
+    r_bet = bet[idx];
+    r_w = wv[idx];
+  }
+  if constexpr (kGregT) {
+#pragma unroll
+    for (int r = 0; r < RG; ++r)
+#pragma unroll
+      for (int sx = 0; sx < kGS; ++sx) {
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int j4 = lane * 4 + 128 * sx;
+        if (greg_on && r < whi - wlo && j4 < p) {
+          const int ib = wlo + r;
+          const float* rowp = reinterpret_cast<const float*>(
+              ib < smem_rows ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg);
+          g = *reinterpret_cast<const float4*>(rowp + j4);
+        }
+        greg[r][sx] = g;
+      }
+  }
+  int skip_mv = 1;      // dbeta of the previous iteration is all zero
+  int all_done = 1;
+  for (int k = 0; k < m; ++k) all_done &= done[k];
+  int64_t loops = 0;
+  int t = 0;
+  while (!all_done) {
+    const int cur = t & 1, nxt = cur ^ 1;
+    const T* Dc = Dbuf + (size_t)cur * ldgs * M;
+    const int nr = whi - wlo;
+    if constexpr (kGrid) {
+      // the whole dbeta of the last iteration, from L2 (not L1: other SMs
+      // wrote it)
+      if (!skip_mv) {
+        const float4* src = reinterpret_cast<const float4*>(xD + (size_t)cur * ldgs * M);
+        float4* dst = reinterpret_cast<float4*>(Dbuf + (size_t)cur * ldgs * M);
+        const int nv4 = (int)((size_t)ldgs * M * sizeof(T) / 16);
+        for (int e = tid; e < nv4; e += NT) dst[e] = __ldcg(src + e);
+      }
+      __syncthreads();
+    }
+    T lmd = T(0), lmb = T(0);  // this lane's running max |dbeta|, |beta| (instance kq)
+    // ---- 1. per group of RG rows: y = G dbeta for all instances (one pass
+    // over dbeta for the group), u update and, without groups, the threshold
+    for (int gb = wlo; gb < whi; gb += RG) {
+      const int nv = min(RG, whi - gb);
+      T y = T(0);
+      if (!skip_mv) {
+        T acc[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) acc[q] = T(0);
+        const T* gr[RG];
+#pragma unroll
+        for (int r = 0; r < RG; ++r) {
+          const int ib = gb + min(r, nv - 1);
+          gr[r] = ib < smem_rows ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
+        }
+        if constexpr (kF32) {
+          // lane l takes columns 4l .. 4l+3, then + 128: one float4 of each
+          // G row and M float4 units of dbeta per step (rows are zero-padded
+          // to ldgs, a multiple of 4). Rows resident in shared memory are
+          // addressed from Gs (shared loads), the others through gr.
+          const float* g0 = Gs + (size_t)gb * ldgs;
+          auto matvec = [&](auto row) {
+            for (int j4 = lane * 4; j4 < p; j4 += 128) {
+              float dv[4][M];
+#pragma unroll
+              for (int q = 0; q < M; ++q) {
+                const int u = (j4 * M >> 2) + q;
+                const float4 t = *reinterpret_cast<const float4*>(Dc + ((u ^ ((u >> 3) & (M - 1))) << 2));
+                const float tv[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) dv[(q * 4 + e) / M][(q * 4 + e) % M] = tv[e];
+              }
+#pragma unroll
+              for (int r = 0; r < RG; ++r) {
+                float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (r < nv) g4 = *reinterpret_cast<const float4*>(row(r) + j4);
+                const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                  for (int k = 0; k < M; ++k) acc[r * M + k] = fma(gv[c], dv[c][k], acc[r * M + k]);
+              }
+            }
+          };
+          if (kGregT && greg_on) {
+#pragma unroll
+            for (int sx = 0; sx < kGS; ++sx) {
+              const int j4 = lane * 4 + 128 * sx;
+              if (j4 < p) {
+                float dv[4][M];
+#pragma unroll
+                for (int q = 0; q < M; ++q) {
+                  const int u = (j4 * M >> 2) + q;
+                  const float4 t = *reinterpret_cast<const float4*>(Dc + ((u ^ ((u >> 3) & (M - 1))) << 2));
+                  const float tv[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                  for (int e = 0; e < 4; ++e) dv[(q * 4 + e) / M][(q * 4 + e) % M] = tv[e];
+                }
+#pragma unroll
+                for (int r = 0; r < RG; ++r) {
+                  const float4 g4 = greg[kGregT ? r : 0][kGregT ? sx : 0];
+                  const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+                  for (int c = 0; c < 4; ++c)
+#pragma unroll
+                    for (int k = 0; k < M; ++k) acc[r * M + k] = fma(gv[c], dv[c][k], acc[r * M + k]);
+                }
+              }
+            }
+          } else if (gb + nv <= smem_rows) {
+            matvec([&](int r) { return g0 + (size_t)r * ldgs; });
+          } else {
+            matvec([&](int r) { return gr[r]; });
+          }
+        } else {
+#pragma unroll 4
+          for (int j = lane; j < p; j += 32) {
+            T dv[M];
+            load_col<T, M>(Dc, j, dv);
+#pragma unroll
+            for (int r = 0; r < RG; ++r) {
+              const T g = r < nv ? gr[r][j] : T(0);
+#pragma unroll
+              for (int k = 0; k < M; ++k) acc[r * M + k] = fma(g, dv[k], acc[r * M + k]);
+            }
+          }
+        }
+        y = reduce_scatter<V>(acc, lane);
+      }
+      const int i = gb + rsub;  // this lane's row (local index)
+      if (regst) {
+        if (own) {
+          if (my_inst && !skip_mv) {
+            const T incr = fma(my_d, r_dn, -y);
+            if (incr != T(0)) {
+              const T h = r_uhi;
+              const T s1 = h + incr, bb = s1 - h;
+              const T e = (h - (s1 - bb)) + (incr - bb);
+              const T lo = r_ulo + e;
+              const T hi2 = s1 + lo;
+              r_ulo = lo - (hi2 - s1);
+              r_uhi = hi2;
+            }
+          }
+          T dn = T(0);
+          if (my_inst) {
+            if (!my_done) {
+              const T bn = thr_scalar<T>(my_kind, r_uhi, r_w * my_lam, my_alpha, my_gamma, my_d);
+              dn = bn - r_bet;
+              r_bet = bn;
+              bet[kq * maxR + i] = bn;
+              lmd = fmax(lmd, fabs(dn));
+              lmb = fmax(lmb, fabs(bn));
+            } else {
+              lmb = fmax(lmb, fabs(r_bet));
+            }
+          }
+          st[(size_t)i * M + kq] = dn;
+          r_dn = dn;
+        }
+      } else if (even && i < whi) {
+        const int idx = kq * maxR + i;
+        if (my_inst && !skip_mv) {
+          const T incr = fma(my_d, Dc[dpos<T, M>(i0 + i, kq)], -y);
+          // an instance whose dbeta was zero (y == 0 exactly) keeps its u
+          // bit for bit, however the instances are grouped into tasks
+          if (incr == T(0)) {
+          } else if (kF32) {
+            const T h = uhi[idx];
+            const T s1 = h + incr, bb = s1 - h;
+            const T e = (h - (s1 - bb)) + (incr - bb);
+            const T lo = ulo[idx] + e;
+            const T hi2 = s1 + lo;
+            ulo[idx] = lo - (hi2 - s1);
+            uhi[idx] = hi2;
+          } else {
+            uhi[idx] += incr;
+          }
+        }
+        if (!has_group) {
+          T dn = T(0);
+          if (my_inst) {
+            if (!my_done) {
+              const T bn = thr_scalar<T>(my_kind, uhi[idx], wv[idx] * my_lam, my_alpha, my_gamma, my_d);
+              dn = bn - bet[idx];
+              bet[idx] = bn;
+              lmd = fmax(lmd, fabs(dn));
+              lmb = fmax(lmb, fabs(bn));
+            } else {
+              lmb = fmax(lmb, fabs(bet[idx]));
+            }
+          }
+          st[(size_t)i * M + kq] = dn;
+        }
+      }
+    }
+    __syncwarp();
+    if (has_group) {
+      // ---- 2a. group norms over the warp's rows: ||u_g||, or for the
+      // sparse group lasso ||v_g|| with v = S(u, w lambda tau) / d
+      for (int e = lane; e < M * nr; e += 32) {
+        const int k = e / nr, i = wlo + e % nr;
+        const int idx = k * maxR + i;
+        const int len = glen[idx];
+        if (len > 0) {
+          int kd = OEM_LASSO;
+          T lt = T(0), dd = T(1);
+#pragma unroll
+          for (int kk = 0; kk < M; ++kk)
+            if (kk == k) { kd = kind[kk]; lt = lamv[kk] * alpha[kk]; dd = dk[kk]; }
+          T s2 = T(0);
+          if (kd == OEM_SPARSE_GROUP_LASSO) {
+            for (int q = 0; q < len; ++q) {
+              const T v = fmax(fabs(uhi[idx + q]) - wv[idx + q] * lt, T(0)) / dd;
+              s2 = fma(v, v, s2);
+            }
+          } else {
+            for (int q = 0; q < len; ++q) s2 = fma(uhi[idx + q], uhi[idx + q], s2);
+          }
+          s2 = sqrt(s2);
+          for (int q = 0; q < len; ++q) gn[idx + q] = s2;
+        }
+      }
+      __syncwarp();
+      // ---- 2b. thresholds and the new dbeta (rows of this warp)
+      T mx_d[M], mx_b[M];
+#pragma unroll
+      for (int k = 0; k < M; ++k) { mx_d[k] = T(0); mx_b[k] = T(0); }
+      for (int e = lane; e < M * nr; e += 32) {
+        const int k = e / nr, i = wlo + e % nr;
+        const int idx = k * maxR + i;
+        T dn = T(0);
+#pragma unroll
+        for (int kk = 0; kk < M; ++kk) {
+          if (kk == k && kk < m) {
+            if (!done[kk]) {
+              const T u = uhi[idx];
+              T bn;
+              if (kind[kk] == OEM_GROUP_LASSO) {
+                const T nrm = gn[idx];
+                const T f = nrm > T(0) ? T(1) - cgr[idx] * lamv[kk] / nrm : T(0);
+                bn = f > T(0) ? u / dk[kk] * f : T(0);
+              } else if (kind[kk] == OEM_GROUP_MCP || kind[kk] == OEM_GROUP_SCAD) {
+                // Eqs. gmcp / gscad: the scalar rule on the norm, u's direction
+                const T nrm = gn[idx];
+                const T bnorm = nrm > T(0) ? thr_scalar<T>(kind[kk] == OEM_GROUP_MCP ? OEM_MCP : OEM_SCAD, nrm,
+                                                           cgr[idx] * lamv[kk], alpha[kk], gamma[kk], dk[kk])
+                                           : T(0);
+                bn = nrm > T(0) ? u * (bnorm / nrm) : T(0);
+              } else if (kind[kk] == OEM_SPARSE_GROUP_LASSO) {
+                // Eq. sglasso (reading: the group step shrinks v by
+                // c_k lambda (1 - tau) / d)
+                const T nrm = gn[idx];
+                const T v = copysign(fmax(fabs(u) - wv[idx] * lamv[kk] * alpha[kk], T(0)) / dk[kk], u);
+                const T f = nrm > T(0) ? T(1) - cgr[idx] * lamv[kk] * (T(1) - alpha[kk]) / (dk[kk] * nrm) : T(0);
+                bn = f > T(0) ? v * f : T(0);
+              } else {
+                bn = thr_scalar<T>(kind[kk], u, wv[idx] * lamv[kk], alpha[kk], gamma[kk], dk[kk]);
+              }
+              dn = bn - bet[idx];
+              bet[idx] = bn;
+              mx_d[kk] = fmax(mx_d[kk], fabs(dn));
+              mx_b[kk] = fmax(mx_b[kk], fabs(bn));
+            } else {
+              mx_b[kk] = fmax(mx_b[kk], fabs(bet[idx]));
+            }
+          }
+        }
+        st[(size_t)i * M + k] = dn;
+      }
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        const T a1 = warp_max(mx_d[k]), a2 = warp_max(mx_b[k]);
+        if (k == kq) { lmd = a1; lmb = a2; }
+      }
+      __syncwarp();
+    }
+    // ---- 3. DSMEM: dbeta rows to every CTA, maxima into every CTA's slot
+    {
+      if constexpr (kF32) {
+        // by 16-byte units of the buffer: a unit inside the warp's rows goes
+        // as one float4 store, a unit shared with a neighbour warp element by
+        // element (i0 is a multiple of 4, so st is unit-aligned)
+        const int f0 = (i0 + wlo) * M, f1 = (i0 + whi) * M;
+        const int u0 = f0 >> 2, nu = ((f1 + 3) >> 2) - u0;
+        T* Dn = (kGrid ? xD : Dbuf) + (size_t)nxt * ldgs * M;
+        const int CC = kGrid ? 1 : C;
+        if constexpr (kAsync) {
+          const uint32_t bar = xbar0 + 8 * nxt;
+          for (int e = lane; e < nu * C; e += 32) {
+            const int u = u0 + e / C, r = e % C;
+            float* dl = Dn + ((u ^ ((u >> 3) & (M - 1))) << 2);
+            const float* src = st + (4 * u - i0 * M);
+            const bool whole = 4 * u >= f0 && 4 * u + 4 <= f1;
+            if (r == rank) {
+              if (whole) {
+                *reinterpret_cast<float4*>(dl) = *reinterpret_cast<const float4*>(src);
+              } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                  if (4 * u + q >= f0 && 4 * u + q < f1) dl[q] = src[q];
+              }
+            } else {
+              const uint32_t ra = xs_map(xs_u32(dl), r), rb = xs_map(bar, r);
+              if (whole) {
+                xs_st4(ra, *reinterpret_cast<const float4*>(src), rb);
+              } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                  if (4 * u + q >= f0 && 4 * u + q < f1) xs_st1(ra + 4 * q, __float_as_uint(src[q]), rb);
+              }
+            }
+          }
+        } else {
+          for (int e = lane; e < nu * CC; e += 32) {
+            const int u = u0 + e / CC, r = e % CC;
+            float* dst = (kGrid ? Dn : cluster.map_shared_rank(Dn, r)) + ((u ^ ((u >> 3) & (M - 1))) << 2);
+            const float* src = st + (4 * u - i0 * M);
+            if (4 * u >= f0 && 4 * u + 4 <= f1) {
+              *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(src);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                if (4 * u + q >= f0 && 4 * u + q < f1) dst[q] = src[q];
+            }
+          }
+        }
+      } else if constexpr (kGrid) {
+        T* Dn = xD + (size_t)nxt * ldgs * M;
+        for (int i = wlo + lane; i < whi; i += 32) store_row<T, M>(Dn, i0 + i, st + (size_t)i * M);
+      } else {
+        T* Dn = Dbuf + (size_t)nxt * ldgs * M;
+        for (int e = lane; e < nr * C; e += 32) {
+          const int i = wlo + e / C, r = e % C;
+          store_row<T, M>(cluster.map_shared_rank(Dn, r), i0 + i, st + (size_t)i * M);
+        }
+      }
+      // instance kq's warp maxima end in lane S kq (lanes of one instance
+      // differ in the row bits 32 / RG .. 16 of the lane index)
+#pragma unroll
+      for (int o = 32 / RG; o < 32; o <<= 1) {
+        lmd = fmax(lmd, __shfl_xor_sync(0xffffffffu, lmd, o));
+        lmb = fmax(lmb, __shfl_xor_sync(0xffffffffu, lmb, o));
+      }
+      if (even && rsub == 0) {
+        lred[(warp * M + kq) * 2] = to_red(lmd);
+        lred[(warp * M + kq) * 2 + 1] = to_red(lmb);
+      }
+    }
+    __syncthreads();
+    // ---- 3b. warp 0: the block's maxima into slot t % 3 of every CTA (the
+    // slot is zeroed after its decisions, two iterations before its reuse)
+    if (warp == 0) {
+      constexpr int E = 2 * M;  // values per slot
+      float v = 0.f;
+      if (lane < E)
+        for (int w = 0; w < NW; ++w) v = fmax(v, lred[w * E + lane]);
+      if constexpr (kAsync) {
+        // this CTA's maxima into entry [nxt][rank] of every CTA; then the
+        // wait for every peer's dbeta rows and maxima (bounded), and the
+        // maxima over the C entries into xred
+        const uint32_t bar = xbar0 + 8 * nxt;
+        unsigned int* sl = xslot + (size_t)nxt * 16 * E;
+        for (int base = 0; base < C * E; base += 32) {
+          const int e = base + lane, q = e % E, r = e / E;
+          const float val = __shfl_sync(0xffffffffu, v, q);
+          if (e < C * E) {
+            if (r == rank) sl[rank * E + q] = __float_as_uint(val);
+            else xs_st1(xs_map(xs_u32(sl + rank * E + q), r), __float_as_uint(val), xs_map(bar, r));
+          }
+        }
+        if (lane == 0) xs_arm(bar, (uint32_t)(((p - R) * M + (C - 1) * E) * 4));
+        const uint32_t par = (uint32_t)((t >> 1) & 1);
+        bool ok = xs_try(bar, par);
+        if (!ok) {
+          const long long t0 = clock64();
+          while (!(ok = xs_try(bar, par)))
+            if (clock64() - t0 > wait_lim) break;
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        unsigned int mx = 0u;
+        for (int e = lane; e < C * E; e += 32) mx = max(mx, sl[e]);
+        for (int o = E; o < 32; o <<= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane < E) xred[lane] = mx;
+        if (lane == 0 && !ok) *xfail = 1u;
+      } else if constexpr (kGrid) {
+        if (lane < E && v > 0.f) atomicMax(tk.xslot + (size_t)(t % 3) * E + lane, __float_as_uint(v));
+      } else {
+        unsigned int* slot = red + (size_t)(t % 3) * E;
+        for (int base = 0; base < C * E; base += 32) {
+          const int e = base + lane, q = e % E;
+          const float val = __shfl_sync(0xffffffffu, v, q);
+          if (e < C * E && val > 0.f)
+            atomicMax(cluster.map_shared_rank(slot + q, e / E), __float_as_uint(val));
+        }
+      }
+    }
+    if constexpr (kGrid) {
+      if (!group_barrier(tk.xbar, (unsigned)C, bar_gen, wait_lim)) {
+        if (tid == 0) atomicOr(P.dstatus, kStatTimeout);
+        break;
+      }
+      // the slot into this CTA's table (read below like the cluster slot)
+      if (tid < 2 * M) red[(size_t)(t % 3) * M * 2 + tid] = ld_relaxed_gpu(tk.xslot + (size_t)(t % 3) * M * 2 + tid);
+      __syncthreads();
+    } else if constexpr (kAsync) {
+      __syncthreads();
+      if (*xfail) {
+        if (tid == 0) atomicOr(P.dstatus, kStatTimeout);
+        break;
+      }
+    } else {
+      cluster.sync();
+    }
+    // ---- 4. decisions (every thread, same data, same result)
+    {
+      const unsigned int* slot = kAsync ? xred : red + (size_t)(t % 3) * M * 2;
+      int anyd = 0;
+      all_done = 1;
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        if (k >= m || done[k]) continue;
+        const T md = (T)from_red(slot[2 * k]), mb = (T)from_red(slot[2 * k + 1]);
+        if (md > T(0)) anyd = 1;
+        const int it = ++its[k];
+        const bool conv = md <= tol * fmax(T(1), mb);
+        if (conv || it >= P.max_iter) {
+          const int l = lidx[k];
+          if (rank == 0 && tid == 0) {
+            const size_t o = (size_t)k * L + l;
+            tk.iters[o] = it;
+            tk.conv[o] = conv ? 1 : 0;
+            if (!conv) atomicOr(P.dstatus, kStatNotConv);
+          }
+          double* out = tk.beta + ((size_t)k * L + l) * p + i0;
+          for (int i = wlo + lane; i < whi; i += 32) out[i] = (double)bet[k * maxR + i];
+          its[k] = 0;
+          lidx[k] = l + 1;
+          if (l + 1 >= L) done[k] = 1;
+          else lamv[k] = (T)tk.lam[(size_t)k * L + l + 1];
+        }
+        all_done &= done[k];
+      }
+      skip_mv = !anyd;
+#pragma unroll
+      for (int k = 0; k < M; ++k)
+        if (k == kq) { my_lam = lamv[k]; my_done = done[k]; }
+      if (tid < M * 2) {
+        red[(size_t)((t + 2) % 3) * M * 2 + tid] = 0u;
+        if (kGrid && rank == 0) tk.xslot[(size_t)((t + 2) % 3) * M * 2 + tid] = 0u;
+      }
+    }
+    ++t;
+    ++loops;
+    if (P.max_loops > 0 && loops >= P.max_loops) break;
+  }
+  if (regst && own) {
+    uhi[kq * maxR + i_own] = r_uhi;
+    ulo[kq * maxR + i_own] = r_ulo;
+  }
+  __syncwarp();
+  // ---- save the state for a later launch (serving): apply the pending dbeta
+  if (tk.st_u) {
+    if (!all_done && !skip_mv) {
+      const T* Dc = Dbuf + (size_t)(t & 1) * ldgs * M;
+      for (int ib = wlo; ib < whi; ++ib) {
+        const T* g0 = (ib < smem_rows) ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
+        T acc[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) acc[k] = T(0);
+        // same column order and lane tree as the loop's mat-vec, so a resumed
+        // path is the same as an uninterrupted one
+        if constexpr (kF32) {
+          for (int j4 = lane * 4; j4 < p; j4 += 128) {
+            const float4 g4 = *reinterpret_cast<const float4*>(g0 + j4);
+            const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int k = 0; k < M; ++k) acc[k] = fma(gv[c], Dc[dpos<T, M>(j4 + c, k)], acc[k]);
+          }
+        } else {
+          for (int j = lane; j < p; j += 32) {
+            T dv[M];
+            load_col<T, M>(Dc, j, dv);
+            const T g = g0[j];
+#pragma unroll
+            for (int k = 0; k < M; ++k) acc[k] = fma(g, dv[k], acc[k]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < M; ++k) acc[k] = warp_sum(acc[k]);
+        if (lane == 0) {
+#pragma unroll
+          for (int k = 0; k < M; ++k) {
+            if (k >= m) continue;
+            const int idx = k * maxR + ib;
+            const T incr = fma(dk[k], Dc[dpos<T, M>(i0 + ib, k)], -acc[k]);
+            if (incr == T(0)) {
+            } else if (kF32) {
+              const T h = uhi[idx];
+              const T s = h + incr, bb = s - h;
+              const T e = (h - (s - bb)) + (incr - bb);
+              const T lo = ulo[idx] + e;
+              const T hi2 = s + lo;
+              ulo[idx] = lo - (hi2 - s);
+              uhi[idx] = hi2;
+            } else {
+              uhi[idx] += incr;
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+    for (int e = lane; e < m * (whi - wlo); e += 32) {
+      const int k = e / (whi - wlo), i = wlo + e % (whi - wlo);
+      const size_t o = (size_t)k * p + i0 + i;
+      tk.st_u[2 * o] = (double)uhi[k * maxR + i];
+      tk.st_u[2 * o + 1] = (double)ulo[k * maxR + i];
+      tk.st_beta[o] = (double)bet[k * maxR + i];
+    }
+    if (rank == 0 && tid == 0) {
+      for (int k = 0; k < m; ++k) {
+        tk.st_ctl[k * 4 + 0] = lidx[k];
+        tk.st_ctl[k * 4 + 1] = its[k];
+        tk.st_ctl[k * 4 + 2] = done[k];
+      }
+      int fin = 1;
+      for (int k = 0; k < m; ++k) fin &= done[k];
+      tk.st_ctl[32] = fin;
+    }
+  }
+  if (tk.fin_out && rank == 0 && tid == 0) *tk.fin_out = all_done;
+  if constexpr (!kGrid)
+    cluster.sync();  // no CTA leaves while a peer could still address its shared memory
+}
+
+size_t oem_iter_rows_smem_fixed(int p, int npen, int max_rows, int precision) {
+  const int M = oem_iter_mpad(npen);
+  const int tsz = precision == OEM_ITER_F64 ? 8 : 4;
+  return iter_smem_layout(p, M, max_rows, tsz, 0).total;
+}
+
+size_t oem_iter_rows_smem_per_row(int p, int precision) {
+  const int tsz = precision == OEM_ITER_F64 ? 8 : 4;
+  return (size_t)((p + 3) & ~3) * tsz;
+}
+
+template <typename T, int M, bool kGrid, int RG>
+static cudaError_t launch_t(const IterLaunch& P, cudaStream_t s, bool query, int* out) {
+  constexpr int NT = iter_threads<T, M>();
+  auto kfn = oem_iter_rows_kernel<T, M, NT, kGrid, RG>;
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(P.ntasks * P.C));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = P.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  if constexpr (kGrid) {
+    if (query) {
+      int n = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kfn, NT, P.smem);
+      *out = (e == cudaSuccess) ? n : 0;
+      return e;
+    }
+    attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs resident, or no launch
+    attr[0].val.cooperative = 1;
+  } else {
+    e = cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = P.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (query) {
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, kfn, &cfg);
+    *out = (e == cudaSuccess) ? n : 0;
+    return e;
+  }
+  return cudaLaunchKernelEx(&cfg, kfn, P);
+}
+
+// Row group: 16 / M rows, or 4 when no warp owns more than 4 rows (the
+// instances then fill fewer sums per lane and no load is wasted).
+template <typename T, int M, int RG>
+static cudaError_t dispatch_r(const IterLaunch& P, cudaStream_t s, bool q, int* out) {
+  return P.grid ? launch_t<T, M, true, RG>(P, s, q, out) : launch_t<T, M, false, RG>(P, s, q, out);
+}
+template <typename T, int M>
+static cudaError_t dispatch_g(const IterLaunch& P, cudaStream_t s, bool q, int* out) {
+  constexpr int RGF = 16 / M;
+  if constexpr (RGF > 4) {
+    constexpr int NW = iter_threads<T, M>() / 32;
+    if ((P.max_rows + NW - 1) / NW <= 4) return dispatch_r<T, M, 4>(P, s, q, out);
+  }
+  return dispatch_r<T, M, RGF>(P, s, q, out);
+}
+
+template <typename T>
+static cudaError_t dispatch_m(const IterLaunch& P, cudaStream_t s, bool q, int* out) {
+  switch (P.M) {
+    case 1: return dispatch_g<T, 1>(P, s, q, out);
+    case 2: return dispatch_g<T, 2>(P, s, q, out);
+    case 4: return dispatch_g<T, 4>(P, s, q, out);
+    default: return dispatch_g<T, 8>(P, s, q, out);
+  }
+}
+
+int oem_iter_rows_max_cluster(const IterLaunch& P0) {
+  IterLaunch P = P0;
+  int n = 0;
+  cudaError_t e = (P.precision == OEM_ITER_F64) ? dispatch_m<double>(P, 0, true, &n)
+                                                : dispatch_m<float>(P, 0, true, &n);
+  if (e != cudaSuccess) { cudaGetLastError(); return 0; }
+  return n;
+}
+
+cudaError_t launch_oem_iter_rows(const IterLaunch& P, cudaStream_t s) {
+  if (P.precision == OEM_ITER_F64) return dispatch_m<double>(P, s, false, nullptr);
+  return dispatch_m<float>(P, s, false, nullptr);
+}
+
+}  // namespace oem

@@ -341,20 +341,18 @@ void fail_job(oem_server* S, SrvJob* J, int code) {
   J->state = OEM_JOB_FAILED;
 }
 
-// One batched round over every job whose preparation is complete.
-int run_round(oem_server* S, std::vector<SrvJob*>& ready) {
+// One launch of the iteration kernel over the tasks [t0, t0 + T) of the
+// round: the jobs in `jobs`, all served by the same kernel (replicated
+// row-owned, replicated column-segment, or row-owned for very large p), so
+// that a job's arithmetic does not depend on the jobs it shares a round with.
+static int launch_class(oem_server* S, const std::vector<SrvJob*>& jobs, int t0, cudaStream_t s) {
   oem_ctx* ctx = S->ctx;
-  cudaStream_t s = S->iter_stream;
   int T = 0;
   int64_t pmax = 1;
-  for (SrvJob* J : ready) { T += J->B; pmax = std::max(pmax, J->p); }
-  if (T > S->tasks_cap) {
-    if (S->d_tasks) { cudaFree(S->d_tasks); cudaFree(S->d_fin); cudaFreeHost(S->h_fin); }
-    S->tasks_cap = std::max(T, 2 * S->tasks_cap);
-    CU(cudaMalloc(&S->d_tasks, sizeof(IterTask) * S->tasks_cap));
-    CU(cudaMalloc(&S->d_fin, sizeof(int32_t) * S->tasks_cap));
-    CU(cudaMallocHost(&S->h_fin, sizeof(int32_t) * S->tasks_cap));
-  }
+  bool groups = false;
+  for (SrvJob* J : jobs) { T += J->B; pmax = std::max(pmax, J->p); groups = groups || J->groups; }
+  const bool rows = iter_rows_kernel(pmax);
+  const bool wide = !rows && pmax > kIterWideP;
   // cluster size: all clusters resident at once, about 32 rows per CTA
   int C = 1;
   const int byT = std::max(1, ctx->num_sms / std::max(1, T));
@@ -365,15 +363,18 @@ int run_round(oem_server* S, std::vector<SrvJob*>& ready) {
   for (;; C /= 2) {
     size_t smem = 0;
     int t = 0;
-    for (SrvJob* J : ready) {
+    for (SrvJob* J : jobs) {
       for (int b = 0; b < J->B; ++b, ++t) {
         IterTask& k = tasks[t];
         k = IterTask{};
-        make_slices(J->p, C, J->P.allowed, k.slice, &k.max_rows);
+        if (rows) make_slices(J->p, C, J->P.allowed, k.slice, &k.max_rows);
+        else make_slices_even(J->p, C, 4, k.slice, &k.max_rows);
         for (int r = C + 1; r <= kMaxCluster; ++r) k.slice[r] = (int32_t)J->p;
-        fixed[t] = oem_iter_smem_fixed((int)J->p, 1, k.max_rows, OEM_ITER_F32);
-        smem = std::max(smem, std::min(kIterSmemCap, fixed[t] + (size_t)k.max_rows *
-                                                          oem_iter_smem_per_row((int)J->p, OEM_ITER_F32)));
+        fixed[t] = rows ? oem_iter_rows_smem_fixed((int)J->p, 1, k.max_rows, OEM_ITER_F32)
+                        : oem_iter_smem_fixed((int)J->p, 1, k.max_rows, OEM_ITER_F32, false, groups);
+        const size_t per = rows ? oem_iter_rows_smem_per_row((int)J->p, OEM_ITER_F32)
+                                : oem_iter_smem_per_row((int)J->p, OEM_ITER_F32);
+        smem = std::max(smem, std::min(kIterSmemCap, fixed[t] + (size_t)k.max_rows * per));
       }
     }
     smem = std::max<size_t>(smem, 1024);
@@ -381,14 +382,15 @@ int run_round(oem_server* S, std::vector<SrvJob*>& ready) {
     for (int u = 0; u < T; ++u) max_rows = std::max(max_rows, tasks[u].max_rows);
     IterLaunch probe{};
     probe.ntasks = T; probe.C = C; probe.M = 1; probe.precision = OEM_ITER_F32; probe.smem = smem;
-    probe.max_rows = max_rows;
-    if (oem_iter_max_cluster(probe) >= 1 || C == 1) {
+    probe.max_rows = max_rows; probe.groups = groups ? 1 : 0; probe.wide = wide ? 1 : 0;
+    if (iter_smem_probe(probe, rows) >= 1 || C == 1) {
       t = 0;
-      for (SrvJob* J : ready) {
+      for (SrvJob* J : jobs) {
         const int L = J->spec.nlambda;
         for (int b = 0; b < J->B; ++b, ++t) {
           IterTask& k = tasks[t];
-          const size_t per = oem_iter_smem_per_row((int)J->p, OEM_ITER_F32);
+          const size_t per = rows ? oem_iter_rows_smem_per_row((int)J->p, OEM_ITER_F32)
+                                  : oem_iter_smem_per_row((int)J->p, OEM_ITER_F32);
           k.p = (int)J->p; k.npen = 1; k.L = L; k.ldg = J->ldg;
           k.smem_rows = smem > fixed[t] ? (int)std::min<size_t>(k.max_rows, (smem - fixed[t]) / per) : 0;
           k.resume = J->rounds > 0 ? 1 : 0;
@@ -404,22 +406,53 @@ int run_round(oem_server* S, std::vector<SrvJob*>& ready) {
           k.st_u = J->st_u + (size_t)b * J->p * 2;
           k.st_beta = J->st_beta + (size_t)b * J->p;
           k.st_ctl = J->st_ctl + (size_t)b * 40;
-          k.fin_out = S->d_fin + t;
+          k.fin_out = S->d_fin + t0 + t;
         }
       }
-      CU(cudaMemcpyAsync(S->d_tasks, tasks.data(), sizeof(IterTask) * T, cudaMemcpyHostToDevice, s));
+      CU(cudaMemcpyAsync(S->d_tasks + t0, tasks.data(), sizeof(IterTask) * T, cudaMemcpyHostToDevice, s));
       IterLaunch Lc{};
-      Lc.tasks = S->d_tasks; Lc.ntasks = T; Lc.C = C; Lc.M = 1; Lc.precision = OEM_ITER_F32;
-      Lc.tol = ready[0]->spec.tol;  // per-job tolerance: jobs of one round share it (see submit)
-      Lc.max_iter = ready[0]->spec.max_iter;
+      Lc.tasks = S->d_tasks + t0; Lc.ntasks = T; Lc.C = C; Lc.M = 1; Lc.precision = OEM_ITER_F32;
+      Lc.tol = jobs[0]->spec.tol;  // per-job tolerance: jobs of one round share it (see submit)
+      Lc.max_iter = jobs[0]->spec.max_iter;
       Lc.max_loops = S->iters_per_round;
       Lc.dstatus = ctx->dstatus;
       Lc.smem = smem;
       Lc.max_rows = max_rows;
-      LAUNCH(OEM_PROF_ITER, launch_oem_iter(Lc, s));
-      break;
+      Lc.groups = groups ? 1 : 0;
+      Lc.wide = wide ? 1 : 0;
+      Lc.wait_cycles = iter_wait_cycles();
+      if (rows) LAUNCH(OEM_PROF_ITER, launch_oem_iter_rows(Lc, s));
+      else LAUNCH(OEM_PROF_ITER, launch_oem_iter(Lc, s));
+      return OEM_OK;
     }
   }
+}
+
+// One batched round over every job whose preparation is complete.
+int run_round(oem_server* S, std::vector<SrvJob*>& ready) {
+  oem_ctx* ctx = S->ctx;
+  cudaStream_t s = S->iter_stream;
+  int T = 0;
+  for (SrvJob* J : ready) T += J->B;
+  if (T > S->tasks_cap) {
+    if (S->d_tasks) { cudaFree(S->d_tasks); cudaFree(S->d_fin); cudaFreeHost(S->h_fin); }
+    S->tasks_cap = std::max(T, 2 * S->tasks_cap);
+    CU(cudaMalloc(&S->d_tasks, sizeof(IterTask) * S->tasks_cap));
+    CU(cudaMalloc(&S->d_fin, sizeof(int32_t) * S->tasks_cap));
+    CU(cudaMallocHost(&S->h_fin, sizeof(int32_t) * S->tasks_cap));
+  }
+  // the round's jobs by kernel class, in their order within `ready`
+  std::vector<SrvJob*> cls[3];
+  for (SrvJob* J : ready) cls[iter_rows_kernel(J->p) ? 2 : J->p > kIterWideP ? 1 : 0].push_back(J);
+  std::vector<SrvJob*> order;
+  int t0 = 0;
+  for (auto& c : cls) {
+    if (c.empty()) continue;
+    int r = launch_class(S, c, t0, s);
+    if (r) return r;
+    for (SrvJob* J : c) { order.push_back(J); t0 += J->B; }
+  }
+  ready = order;
   CU(cudaMemcpyAsync(S->h_fin, S->d_fin, sizeof(int32_t) * T, cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   S->rounds += 1;
