@@ -91,10 +91,13 @@ enum { OEM_F64 = 0, OEM_F32 = 1, OEM_BF16 = 2 };
  *   BF16       : tcgen05 kind::f16 with bfloat16 operands (X bfloat16: exact
  *                products; the float32 y is carried exactly as three bfloat16
  *                columns hi + mid + lo).
- *   SPLIT_BF16 : tcgen05 kind::f16, X float32 split as hi + lo bfloat16,
- *                products hi*hi + hi*lo + lo*hi, plus lo*lo on the diagonal
- *                128 x 128 tiles (where lo_i^2 would otherwise bias G_ii)
- *                (X float32).
+ *   SPLIT_BF16 : tcgen05 kind::f16, X float32 split as hi + lo bfloat16
+ *                (X float32). The TMA-fed path (the default whenever the
+ *                packed copy fits the budget) forms hi*hi + hi*lo + lo*hi,
+ *                plus lo*lo on the diagonal 128 x 128 tiles (where lo_i^2
+ *                would otherwise bias G_ii); the converting kernel (small
+ *                budgets and oem_gram_noalloc) forms all four products on
+ *                every tile. Both hold the same error bound.
  *   AUTO       : SPLIT_BF16 for float32, BF16 for bfloat16, FP64 for float64. */
 enum {
   OEM_GRAM_FP64 = 0,
@@ -194,6 +197,16 @@ int oem_sync(oem_ctx* ctx, void* stream);
 /* Number of kernels this context has launched so far (for accounting). */
 int64_t oem_kernel_launches(const oem_ctx* ctx);
 
+/* OEM iterations of the last oem_fit_path / oem_fit / oem_cv call on ctx
+ * (Section 2.1 Step 2: one iteration = one update u, beta of one instance).
+ * Waits for `stream`, then reads that call's per-lambda iteration counts:
+ * *iterations = their sum over every instance (penalty, and fold Gram for
+ * oem_cv) and lambda; *loop_trips = the largest sum of one instance, i.e.
+ * the loop trips of the persistent launch that runs all instances side by
+ * side. Valid until the next call on ctx (the counts live in its
+ * workspace). Returns OEM_OK, OEM_EINVAL (no fit yet) or OEM_ECUDA. */
+int oem_iter_stats(oem_ctx* ctx, void* stream, int64_t* iterations, int64_t* loop_trips);
+
 /* Per-kernel device timing. While enabled, every launch of this context is
  * bracketed by CUDA events on its stream; oem_profile_get() waits for the
  * pending events and returns the accumulated device milliseconds and launch
@@ -234,9 +247,14 @@ int oem_gram(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p,
  * that device current); make that first call before any stream capture.
  * Every call shares the one array and leaves its contents behind: calls whose
  * work overlaps on the GPU (other streams, other host threads) race and must
- * not be issued. Non-finite values in X or y are not reported (they show up
- * in G, c, yty). Returns OEM_OK, OEM_EINVAL, OEM_EBUDGET or OEM_ECUDA; work is
- * enqueued on `stream` and the call does not wait. */
+ * not be issued. X, y, G, c and yty must be device memory (or managed memory) of the
+ * current device: host memory, pinned or not, and memory of another device
+ * give OEM_EINVAL (this entry point has no streamed host path). A bounded
+ * device wait of the Gram pass that expires (about 2 s: a device that stopped
+ * making progress) leaves NaN in every element of G, c and yty, since no
+ * status word is read back. Non-finite values in X or y are not reported
+ * (they show up in G, c, yty). Returns OEM_OK, OEM_EINVAL, OEM_EBUDGET or
+ * OEM_ECUDA; work is enqueued on `stream` and the call does not wait. */
 int oem_gram_noalloc(const void* X, int32_t xtype, int64_t n, int64_t p, int64_t ldx,
                      const void* y, int32_t mode, double* G, double* c, double* yty,
                      void* stream);

@@ -42,7 +42,7 @@ MODE = {"fp64": OEM_GRAM_FP64, "fp32": OEM_GRAM_FP32, "tf32": OEM_GRAM_TF32,
         "bf16": OEM_GRAM_BF16, "split_bf16": OEM_GRAM_SPLIT_BF16, "auto": OEM_GRAM_AUTO}
 
 EXPORTED = ["oem_options_default", "oem_create", "oem_destroy", "oem_last_error", "oem_sync",
-            "oem_kernel_launches", "oem_profile_enable", "oem_profile_get", "oem_profile_name",
+            "oem_kernel_launches", "oem_iter_stats", "oem_profile_enable", "oem_profile_get", "oem_profile_name",
             "oem_gram", "oem_gram_noalloc", "oem_fold_grams", "oem_spectral_d", "oem_fit_path",
             "oem_fit", "oem_cv", "oem_fit_logistic", "oem_server_create", "oem_server_submit", "oem_server_poll",
             "oem_server_result", "oem_server_stats", "oem_server_destroy"]
@@ -82,6 +82,7 @@ _sigs = {
     "oem_last_error": (C.c_char_p, [_vp]),
     "oem_sync": (C.c_int, [_vp, _vp]),
     "oem_kernel_launches": (C.c_int64, [_vp]),
+    "oem_iter_stats": (C.c_int, [_vp, _vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "oem_profile_enable": (C.c_int, [_vp, C.c_int]),
     "oem_profile_get": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "oem_profile_name": (C.c_char_p, [C.c_int]),
@@ -238,6 +239,12 @@ class Context:
     def launches(self) -> int:
         return int(lib.oem_kernel_launches(self.h))
 
+    def iter_stats(self, stream=None):
+        """(iterations, loop trips) of the last fit / cross validation."""
+        it, tr = C.c_int64(), C.c_int64()
+        self.check(lib.oem_iter_stats(self.h, _stream(stream), C.byref(it), C.byref(tr)))
+        return int(it.value), int(tr.value)
+
     def profile(self, enable: bool = True):
         self.check(lib.oem_profile_enable(self.h, 1 if enable else 0))
 
@@ -292,16 +299,23 @@ def oem_gram(ctx: Context, X, y, mode="auto", G=None, c=None, yty=None, stream=N
 
 
 def oem_gram_noalloc(X, y, mode="auto", G=None, c=None, yty=None, stream=None):
-    """oem_gram without device allocation or context (see include/oem.h)."""
+    """oem_gram without device allocation or context (see include/oem.h).
+    X, y and the outputs must be CUDA tensors of one device; the call runs
+    with that device current."""
     import torch
+    if not (X.is_cuda and y.is_cuda):
+        raise TypeError("oem_gram_noalloc takes X and y in device memory (CUDA tensors)")
     n, p = X.shape
     dev = X.device
     G = torch.empty((p, p), dtype=torch.float64, device=dev) if G is None else G
     c = torch.empty(p, dtype=torch.float64, device=dev) if c is None else c
     yty = torch.empty(1, dtype=torch.float64, device=dev) if yty is None else yty
-    rc = lib.oem_gram_noalloc(_ptr(X), _xtype(X), n, p, X.stride(0), _ptr(y),
-                              MODE[mode] if isinstance(mode, str) else int(mode),
-                              _ptr(G), _ptr(c), _ptr(yty), _stream(stream))
+    if any(t.device != dev for t in (y, G, c, yty)):
+        raise ValueError("oem_gram_noalloc: X, y, G, c, yty must be on one device")
+    with torch.cuda.device(dev):
+        rc = lib.oem_gram_noalloc(_ptr(X), _xtype(X), n, p, X.stride(0), _ptr(y),
+                                  MODE[mode] if isinstance(mode, str) else int(mode),
+                                  _ptr(G), _ptr(c), _ptr(yty), _stream(stream))
     if rc < 0:
         raise OemError(rc, "oem_gram_noalloc rejected the call")
     return G, c, yty
@@ -373,26 +387,32 @@ def oem_fit(ctx: Context, X, y, pens: Sequence[Penalty], stream=None, out=None, 
     return beta, lam, its, conv, d
 
 
-def oem_cv(ctx: Context, X, y, fold, K, pens: Sequence[Penalty], stream=None, **opts):
+def cv_outputs(npen, L, p, dev):
+    """Output buffers of oem_cv (a dict of device tensors)."""
     import torch
+    return {"beta": torch.empty((npen, L, p), dtype=torch.float64, device=dev),
+            "beta0": torch.empty((npen, L), dtype=torch.float64, device=dev),
+            "lambdas": torch.empty((npen, L), dtype=torch.float64, device=dev),
+            "cvm": torch.empty((npen, L), dtype=torch.float64, device=dev),
+            "cvsd": torch.empty((npen, L), dtype=torch.float64, device=dev),
+            "idx_min": torch.empty(npen, dtype=torch.int32, device=dev),
+            "idx_1se": torch.empty(npen, dtype=torch.int32, device=dev),
+            "best_penalty": torch.empty(1, dtype=torch.int32, device=dev)}
+
+
+def oem_cv(ctx: Context, X, y, fold, K, pens: Sequence[Penalty], stream=None, out=None, **opts):
     n, p = X.shape
     o = make_options(**opts)
     P = _PenArray(pens)
     L = o.nlambda
     dev = _out_device(ctx, X)
-    beta = torch.empty((P.n, L, p), dtype=torch.float64, device=dev)
-    lam = torch.empty((P.n, L), dtype=torch.float64, device=dev)
-    cvm = torch.empty((P.n, L), dtype=torch.float64, device=dev)
-    cvsd = torch.empty((P.n, L), dtype=torch.float64, device=dev)
-    imin = torch.empty(P.n, dtype=torch.int32, device=dev)
-    i1se = torch.empty(P.n, dtype=torch.int32, device=dev)
-    best = torch.empty(1, dtype=torch.int32, device=dev)
-    beta0 = torch.empty((P.n, L), dtype=torch.float64, device=dev)
+    r = cv_outputs(P.n, L, p, dev) if out is None else out
+    beta, lam, cvm, cvsd = r["beta"], r["lambdas"], r["cvm"], r["cvsd"]
+    imin, i1se, best, beta0 = r["idx_min"], r["idx_1se"], r["best_penalty"], r["beta0"]
     ctx.check(lib.oem_cv(ctx.h, _ptr(X), _xtype(X), n, p, X.stride(0), _ptr(y), _ptr(fold), int(K),
                          P.arr, P.n, C.byref(o), _ptr(beta), _ptr(lam), _ptr(cvm), _ptr(cvsd),
                          _ptr(imin), _ptr(i1se), _ptr(best), _ptr(beta0), _stream(stream)))
-    return {"beta": beta, "beta0": beta0, "lambdas": lam, "cvm": cvm, "cvsd": cvsd,
-            "idx_min": imin, "idx_1se": i1se, "best_penalty": best}
+    return r
 
 
 def oem_fit_logistic(ctx: Context, X, y, pens: Sequence[Penalty], stream=None, **opts):

@@ -125,6 +125,26 @@ const char* oem_profile_name(int kernel) {
   return (kernel >= 0 && kernel < OEM_PROF_NKERNELS) ? names[kernel] : "unknown";
 }
 
+int oem_iter_stats(oem_ctx* ctx, void* stream, int64_t* iterations, int64_t* loop_trips) {
+  if (!ctx) return OEM_EINVAL;
+  if (!ctx->last_iters) return fail(ctx, OEM_EINVAL, "no path has been fitted on this context");
+  CU(cudaSetDevice(ctx->device));
+  CU(cudaStreamSynchronize((cudaStream_t)stream));
+  const size_t inst = (size_t)ctx->last_B * ctx->last_npen, L = (size_t)ctx->last_L;
+  std::vector<int32_t> h(inst * L);
+  CU(cudaMemcpy(h.data(), ctx->last_iters, sizeof(int32_t) * h.size(), cudaMemcpyDeviceToHost));
+  int64_t tot = 0, trips = 0;
+  for (size_t i = 0; i < inst; ++i) {
+    int64_t s = 0;
+    for (size_t l = 0; l < L; ++l) s += h[i * L + l];
+    tot += s;
+    trips = std::max(trips, s);
+  }
+  if (iterations) *iterations = tot;
+  if (loop_trips) *loop_trips = trips;
+  return OEM_OK;
+}
+
 int oem_sync(oem_ctx* ctx, void* stream) {
   if (!ctx) return OEM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
@@ -248,6 +268,10 @@ static int fit_tail(oem_ctx* ctx, int64_t p, int B, const double* G64, const flo
   } else {
     LAUNCH(OEM_PROF_LAMBDA, launch_lambda_grid(c, (int)p, P.dpens, P.npen, o->nlambda, o->lambda_min_ratio, lam, s));
   }
+  ctx->last_iters = iters;
+  ctx->last_B = B;
+  ctx->last_npen = P.npen;
+  ctx->last_L = o->nlambda;
   return run_iter(ctx, p, B, G32, ldg32, G64, c, d, lam, P, o, I, beta, iters, conv, s);
 }
 

@@ -56,7 +56,8 @@ def test_single_rank_needs_no_process_group():
 def test_reference_arm_under_torchrun_prints_once():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py",
-           "--impl", "reference", "--steps", "1", "--warmup", "3", "--cpu-sample-rows", "20000"]
+           "--impl", "reference", "--steps", "1", "--warmup", "3", "--cpu-sample-rows", "20000",
+           "--workload", "four_penalties_f32_n1e6_p500"]
     p = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert p.returncode == 0, p.stderr[-2000:]
     lines = [l for l in p.stdout.splitlines() if l.startswith("{")]
