@@ -193,7 +193,7 @@ int oem_gram(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, i
   StreamBufs sb;
   int64_t rows;
   if ((r = plan_residence(ctx, X, y, nullptr, n, ldx, xtype, sb, &rows, s))) return r;
-  GramPlan g = plan_gram(ctx, rows, p, 1, m, false);
+  GramPlan g = plan_gram(ctx, rows, p, 1, m, false, 0, direct_x_ok(X, xtype, sb));
   GramBufs b;
   Arena A;
   gram_request(A, g, rows, b);
@@ -347,7 +347,8 @@ int oem_fit(oem_ctx* ctx, const void* X, int32_t xtype, int64_t n, int64_t p, in
   StreamBufs sb;
   int64_t rows;
   if ((r = plan_residence(ctx, X, y, nullptr, n, ldx, xtype, sb, &rows, s))) return r;
-  GramPlan g = plan_gram(ctx, rows, p, 1, m, false, opt->intercept ? kOnesShifted : 0);
+  GramPlan g = plan_gram(ctx, rows, p, 1, m, false, opt->intercept ? kOnesShifted : 0,
+                         direct_x_ok(X, xtype, sb));
   GramBufs b;
   double *G64 = nullptr, *c = nullptr, *N = nullptr, *cnt = nullptr, *dd = nullptr, *cen = nullptr;
   float* G32 = nullptr;

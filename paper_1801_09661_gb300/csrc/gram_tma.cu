@@ -79,6 +79,9 @@ __device__ __forceinline__ bool mbar_wait_drain(uint32_t bar, uint32_t parity) {
 
 struct TmaGramArgs {
   int32_t split;   // 1: four products from (hi, lo); 0: hi only
+  int32_t nbx;     // bfloat16 mode: 64-column boxes below 64 nbx come from the
+                   // first map (X itself in direct mode), the others from the
+                   // second (the packed tail) at column c - 64 nbx
   int32_t ntile1, ntiles;
   ChunkTable pc;   // chunks of packed rows (row0, row1 multiples of kGramPackRows)
   double* partial; // [chunks][ntiles][128][128]
@@ -162,15 +165,20 @@ __global__ void __launch_bounds__(kTThreads, 1)
           if ((s >> 1) == 0) last0 = u; else if ((s >> 1) == 1) last1 = u; else last2 = u;
           const uint32_t pb = stage0 + s * kTStageBytes;
           const int row = row0 + st * kRS;
-          tma_load_2d(pb, &zhi, ci, row, bar);
-          tma_load_2d(pb + kAtom, &zhi, ci + 64, row, bar);
+          // one 64-column box of hi (bfloat16 mode: from X or from the tail)
+          auto hi_box = [&](uint32_t dst, int c) {
+            if (split || c < 64 * a.nbx) tma_load_2d(dst, &zhi, c, row, bar);
+            else tma_load_2d(dst, &zlo, c - 64 * a.nbx, row, bar);
+          };
+          hi_box(pb, ci);
+          hi_box(pb + kAtom, ci + 64);
           if (split) {
             tma_load_2d(pb + kPanel, &zlo, ci, row, bar);
             tma_load_2d(pb + kPanel + kAtom, &zlo, ci + 64, row, bar);
           }
           if (!diag) {
-            tma_load_2d(pb + 16384, &zhi, cj, row, bar);
-            tma_load_2d(pb + 16384 + kAtom, &zhi, cj + 64, row, bar);
+            hi_box(pb + 16384, cj);
+            hi_box(pb + 16384 + kAtom, cj + 64);
             if (split) {
               tma_load_2d(pb + 16384 + kPanel, &zlo, cj, row, bar);
               tma_load_2d(pb + 16384 + kPanel + kAtom, &zlo, cj + 64, row, bar);
@@ -470,7 +478,11 @@ __global__ void __launch_bounds__(256) zpack_kernel(ZPackArgs a) {
 
 size_t gram_tma_smem_bytes() { return (size_t)tc::kTNS * tc::kTStageBytes + sizeof(tc::TBars) + 1024; }
 
-static cudaError_t encode_z_map(CUtensorMap* m, void* base, int64_t rows, int qp, int box_rows) {
+// 2-D bfloat16 tensor map: cols x rows, row stride ld elements, boxes of 64
+// columns x box_rows rows, 128-byte swizzle; reads outside the extents give
+// zeros.
+static cudaError_t encode_bf16_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols,
+                                   int64_t ld, int box_rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -480,14 +492,64 @@ static cudaError_t encode_z_map(CUtensorMap* m, void* base, int64_t rows, int qp
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  const cuuint64_t dims[2] = {(cuuint64_t)qp, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)qp * 2};
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
   const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+static cudaError_t encode_z_map(CUtensorMap* m, void* base, int64_t rows, int qp, int box_rows) {
+  return encode_bf16_map(m, base, rows, qp, qp, box_rows);
+}
+
+// Direct mode: the tail of Z for bfloat16 X -- X's columns [64 nbx, p), the
+// three bfloat16 pieces of y (exact: y = y0 + y1 + y2), zeros up to
+// tail_cols -- one 8-column unit per thread.
+__global__ void tail_pack_kernel(const __nv_bfloat16* __restrict__ X, int64_t ldx, int64_t n, int64_t p,
+                                 const float* __restrict__ y, int nbx, int tail_cols,
+                                 __nv_bfloat16* __restrict__ tail) {
+  const int units = tail_cols / 8;
+  const int64_t total = n * units;
+  const int64_t x0 = 64 * (int64_t)nbx;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / units;
+    const int u = (int)(e % units);
+    const float yv = y[r];
+    const float y0 = tc::bf16_round(yv);
+    const float y1 = tc::bf16_round(yv - y0);
+    const float yp[3] = {y0, y1, (yv - y0) - y1};
+    uint16_t w[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t c = x0 + 8 * u + q;
+      uint16_t b = 0;
+      if (c < p) b = __bfloat16_as_ushort(X[r * ldx + c]);
+      else if (c - p < 3) b = __bfloat16_as_ushort(__float2bfloat16_rn(yp[c - p]));
+      w[q] = b;
+    }
+    uint4 v;
+    v.x = (uint32_t)w[0] | ((uint32_t)w[1] << 16);
+    v.y = (uint32_t)w[2] | ((uint32_t)w[3] << 16);
+    v.z = (uint32_t)w[4] | ((uint32_t)w[5] << 16);
+    v.w = (uint32_t)w[6] | ((uint32_t)w[7] << 16);
+    *reinterpret_cast<uint4*>(tail + r * tail_cols + 8 * u) = v;
+  }
+}
+
+cudaError_t launch_tail_pack(const GramArgs& a, const TmaBufs& t, cudaStream_t s) {
+  packed_chunks_kernel<<<1, 1, 0, s>>>(a.ct.fold_off, 1, t.chunk_rows, t.pc, t.max_chunks, a.dstatus);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = kNumSMsHint;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  tail_pack_kernel<<<sms * 4, 256, 0, s>>>((const __nv_bfloat16*)a.X, a.ldx, a.n, a.p, (const float*)a.y, t.nbx,
+                                           t.tail_cols, (__nv_bfloat16*)t.zhi);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_zpack(const GramArgs& a, int K, const TmaBufs& t, cudaStream_t s) {
@@ -516,9 +578,18 @@ cudaError_t launch_gram_tma(const GramArgs& a, const TmaBufs& t, int flush_rows,
   int flush_stages = 1;
   while (flush_stages * 2 * rs <= flush_rows && flush_stages * 2 <= tc::kTCrossStages) flush_stages *= 2;
   CUtensorMap mhi, mlo;
-  cudaError_t e = encode_z_map(&mhi, t.zhi, t.rows_cap, t.qp, rs);
-  if (e != cudaSuccess) return e;
-  e = encode_z_map(&mlo, split ? t.zlo : t.zhi, t.rows_cap, t.qp, rs);
+  cudaError_t e;
+  if (t.direct) {
+    // X itself (boxes below 64 nbx: inside its p columns) and the tail; rows
+    // past n read as zeros
+    e = encode_bf16_map(&mhi, a.X, a.n, a.p, a.ldx, rs);
+    if (e != cudaSuccess) return e;
+    e = encode_bf16_map(&mlo, t.zhi, a.n, t.tail_cols, t.tail_cols, rs);
+  } else {
+    e = encode_z_map(&mhi, t.zhi, t.rows_cap, t.qp, rs);
+    if (e != cudaSuccess) return e;
+    e = encode_z_map(&mlo, split ? t.zlo : t.zhi, t.rows_cap, t.qp, rs);
+  }
   if (e != cudaSuccess) return e;
   const size_t smem = gram_tma_smem_bytes();
   auto kern = split ? tc::gram_tma_kernel<true> : tc::gram_tma_kernel<false>;
@@ -529,6 +600,7 @@ cudaError_t launch_gram_tma(const GramArgs& a, const TmaBufs& t, int flush_rows,
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   tc::TmaGramArgs g{};
   g.split = split ? 1 : 0;
+  g.nbx = t.direct ? t.nbx : (1 << 24);
   g.ntile1 = a.ntile1;
   g.ntiles = a.ntiles;
   g.pc = t.pc;

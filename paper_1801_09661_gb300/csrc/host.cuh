@@ -270,6 +270,9 @@ struct GramPlan {
   int32_t qp = 0;
   int64_t rows_cap = 0;
   int pmax_chunks = 0;
+  // direct TMA from X (bfloat16, one fold, no ones): only the tail is packed
+  bool direct = false;
+  int32_t nbx = 0, tail_cols = 0;
 };
 
 // ones: 0 = Z = [X | y]; kOnesShifted = Z = [X | y | 1] on X and y shifted
@@ -277,8 +280,10 @@ struct GramPlan {
 // bfloat16 request then runs in split mode, since the shifted X is not
 // bfloat16); kOnes = Z = [X | y | 1] unshifted (logistic regression).
 constexpr int kOnesShifted = 1, kOnes = 2;
+// x_direct: X is bfloat16 device memory at a 16-byte aligned address (the
+// TMA may read it in place).
 inline GramPlan plan_gram(oem_ctx* ctx, int64_t n, int64_t p, int K, int32_t mode, bool sorted,
-                          int ones = 0) {
+                          int ones = 0, bool x_direct = false) {
   GramPlan g;
   const bool centre = ones == kOnesShifted;
   if (centre && mode == OEM_GRAM_BF16) mode = OEM_GRAM_SPLIT_BF16;
@@ -316,9 +321,16 @@ inline GramPlan plan_gram(oem_ctx* ctx, int64_t n, int64_t p, int K, int32_t mod
     int64_t tcr = (g.rows_cap + want - 1) / want;
     tcr = std::max<int64_t>(1024, (tcr + 127) / 128 * 128);
     g.pmax_chunks = (int)((g.rows_cap + tcr - 1) / tcr + K);
-    const size_t bytes = (size_t)g.rows_cap * g.qp * 2 * (mode == OEM_GRAM_SPLIT_BF16 ? 2 : 1);
+    g.direct = x_direct && mode == OEM_GRAM_BF16 && !sorted && ones == 0 && K == 1;
+    if (g.direct) {
+      g.nbx = (int32_t)(p / 64);
+      g.tail_cols = (g.q - 64 * g.nbx + 63) / 64 * 64;
+    }
+    const size_t bytes = g.direct ? (size_t)g.rows_cap * g.tail_cols * 2
+                                  : (size_t)g.rows_cap * g.qp * 2 * (mode == OEM_GRAM_SPLIT_BF16 ? 2 : 1);
     const size_t partial = (size_t)g.pmax_chunks * g.ntiles * g.T * g.T * sizeof(double);
     g.tma = bytes + partial <= ctx->budget / 2;
+    if (!g.tma) g.direct = false;
     if (g.tma) {
       g.chunk_rows = tcr;
       g.max_chunks = (int)((n + tcr - 1) / tcr + K);
@@ -353,7 +365,7 @@ inline void gram_request(Arena& A, const GramPlan& g, int64_t n, GramBufs& b) {
   A.add(&b.Zg, (size_t)g.K * g.q * g.q);
   if (g.centre) A.add(&b.shift, (size_t)(g.q - g.ycols - g.ocols) + 1);
   if (g.tma) {
-    A.add(&b.zhi, (size_t)g.rows_cap * g.qp);
+    A.add(&b.zhi, (size_t)g.rows_cap * (g.direct ? g.tail_cols : g.qp));
     if (g.mode == OEM_GRAM_SPLIT_BF16) A.add(&b.zlo, (size_t)g.rows_cap * g.qp);
     A.add(&b.t.pc.row0, (size_t)g.pmax_chunks);
     A.add(&b.t.pc.row1, (size_t)g.pmax_chunks);
@@ -393,11 +405,15 @@ inline int run_gram(oem_ctx* ctx, const GramPlan& g, GramBufs& b, const void* X,
     b.t.rows_cap = g.rows_cap;
     b.t.max_chunks = g.pmax_chunks;
     b.t.chunk_rows = g.chunk_rows;
+    b.t.direct = g.direct ? 1 : 0;
+    b.t.nbx = g.nbx;
+    b.t.tail_cols = g.tail_cols;
     // The hi.hi product is summed over 128 rows (split mode) or 256 rows
     // (bfloat16) in float32 tensor memory before it is added to the
     // compensated sum; the cross terms, 2^-8 smaller, over 1,024 rows.
     const int flush = g.mode == OEM_GRAM_SPLIT_BF16 ? 128 : 256;
-    LAUNCH(OEM_PROF_GRAM_TC, launch_zpack(a, g.K, b.t, s));
+    if (g.direct) LAUNCH(OEM_PROF_GRAM_TC, launch_tail_pack(a, b.t, s));
+    else LAUNCH(OEM_PROF_GRAM_TC, launch_zpack(a, g.K, b.t, s));
     LAUNCH(OEM_PROF_GRAM_TC, launch_gram_tma(a, b.t, flush, s));
     GramArgs r = a;
     r.ct.fold_c0 = b.t.pc.fold_c0;
@@ -451,6 +467,12 @@ struct StreamBufs {
   int64_t* cnt = nullptr;   // [K]
   int64_t* off = nullptr;   // [K+1]
 };
+// The Gram pass may read bfloat16 X in place by TMA (direct mode): device X
+// at a 16-byte aligned address, or X streamed through the (aligned) staging
+// buffers.
+inline bool direct_x_ok(const void* X, int32_t xtype, const StreamBufs& sb) {
+  return xtype == OEM_BF16 && (sb.on || ((uintptr_t)X & 15) == 0);
+}
 
 // Rows per block: about 256 MB of X, a multiple of 64, at most n
 // (OEM_STREAM_ROWS overrides, for experiments).
@@ -750,6 +772,14 @@ inline int64_t iter_wait_cycles() {
   return 4000000000LL;
 }
 
+// Tests of the timeout path only: OEM_DEVICE_WAIT_TEST=1 makes the first
+// exchange of every replicated-kernel launch wait for data that nobody
+// sends, so that its bounded wait expires.
+inline int iter_test_stall() {
+  const char* v = std::getenv("OEM_DEVICE_WAIT_TEST");
+  return (v && v[0] == '1') ? 1 : 0;
+}
+
 inline int iter_smem_probe(const IterLaunch& P, bool rows) {
   return rows ? oem_iter_rows_max_cluster(P) : oem_iter_max_cluster(P);
 }
@@ -779,12 +809,13 @@ struct IterPlan {
 };
 
 // Grid-mode exchange space of one task, the larger of the two kernels'
-// needs (row-owned: dbeta buffers, maxima slots, barrier words; replicated:
-// tagged words of G dbeta).
+// needs (row-owned: tagged words of dbeta and of every CTA's maxima, barrier
+// words; replicated: tagged words of G dbeta). At most kMaxGridCtas CTAs
+// per task.
+constexpr int kMaxGridCtas = 256;
 inline size_t grid_xbuf_task_bytes(int64_t p) {
-  const size_t ldgs = (size_t)((p + 3) & ~3LL);
-  const size_t rows = ((2 * ldgs * 8 * sizeof(double) + 3 * 16 * 4 + 2 * 4) + 255) & ~(size_t)255;
-  return std::max(rows, oem_iter_xbuf_bytes((int)p, 8, OEM_ITER_F64));
+  return std::max(oem_iter_rows_xbuf_bytes((int)p, 8, OEM_ITER_F64, kMaxGridCtas),
+                  oem_iter_xbuf_bytes((int)p, 8, OEM_ITER_F64));
 }
 
 // Cluster size C and Mg instances per task for B Grams of npen instances;
@@ -799,7 +830,6 @@ inline int layout_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, int pre
   I.rows = iter_rows_kernel(p);
   const int ntasks = B * ((P.npen + Mg - 1) / Mg);
   const bool rows = I.rows;
-  const bool wide = !rows && p > kIterWideP;
   auto fixed_of = [&](int max_rows) {
     return rows ? oem_iter_rows_smem_fixed((int)p, Mg, max_rows, prec)
                 : oem_iter_smem_fixed((int)p, Mg, max_rows, prec, grid, I.groups);
@@ -808,11 +838,13 @@ inline int layout_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, int pre
     IterLaunch probe{};
     probe.ntasks = ntasks; probe.C = CC; probe.M = I.M; probe.precision = prec;
     probe.smem = I.smem; probe.max_rows = I.max_rows; probe.grid = grid ? 1 : 0;
-    probe.groups = I.groups ? 1 : 0; probe.wide = wide ? 1 : 0;
+    probe.groups = I.groups ? 1 : 0;
+    probe.wide = (!rows && prec == OEM_ITER_F32 && p > kIterWideP && I.max_rows <= 16 && I.M <= 2) ? 1 : 0;
     return iter_smem_probe(probe, rows);
   };
   if (grid) {
     C = std::min<int>(C, ctx->num_sms / std::max(1, ntasks));
+    C = std::min(C, kMaxGridCtas);
     C = (int)std::min<int64_t>(C, rows ? (p + 3) / 4 : p);
     if (C < 2) return fail(ctx, OEM_EUNSUPPORTED, "grid mode needs at least 2 CTAs per task");
     I.gslice.assign((size_t)C + 1, 0);
@@ -973,8 +1005,10 @@ inline int launch_iter_layout(oem_ctx* ctx, int64_t p, int B, const float* G32, 
   Lc.grid = I.grid ? 1 : 0;
   Lc.max_rows = I.max_rows;
   Lc.groups = I.groups ? 1 : 0;
-  Lc.wide = (!I.rows && p > kIterWideP) ? 1 : 0;
+  Lc.wide = (!I.rows && o->iter_precision == OEM_ITER_F32 && p > kIterWideP && I.max_rows <= 16 &&
+             I.M <= 2) ? 1 : 0;
   Lc.wait_cycles = iter_wait_cycles();
+  Lc.test_stall = I.rows ? 0 : iter_test_stall();
   if (I.rows) LAUNCH(OEM_PROF_ITER, launch_oem_iter_rows(Lc, s));
   else LAUNCH(OEM_PROF_ITER, launch_oem_iter(Lc, s));
   return OEM_OK;

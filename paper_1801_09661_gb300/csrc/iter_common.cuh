@@ -49,6 +49,23 @@ __device__ __forceinline__ T reduce_scatter(const T (&a)[V], int lane) {
   return b[0];
 }
 
+// The same for V = 1 or 2 (one or two full butterfly sums; every lane holds
+// them): lane l returns the sum of value l / (32 / V).
+template <int V, typename T>
+__device__ __forceinline__ T reduce_scatter_any(const T (&a)[V], int lane) {
+  if constexpr (V >= 4) {
+    return reduce_scatter<V>(a, lane);
+  } else {
+    T r = T(0);
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      const T sq = warp_sum(a[q]);
+      if (lane / (32 / V) == q) r = sq;
+    }
+    return r;
+  }
+}
+
 // Load the M entries of row j of a [rows][M] buffer.
 template <typename T, int M>
 __device__ __forceinline__ void load_col(const T* __restrict__ D, int j, T (&v)[M]) {

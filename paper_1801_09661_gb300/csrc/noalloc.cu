@@ -40,7 +40,33 @@ cudaError_t scratch_address(void** out) {
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Whether ptr is device (or managed) memory that the current device `dev`
+// can use as this entry point's operand: host memory, pinned or not, and
+// memory of another device are refused.
+bool on_device(const void* ptr, int dev) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
 }  // namespace
+
+// A device wait of the Gram pass that expired leaves its bit in the status
+// word of the scratch array, which nobody reads back; this kernel turns it
+// into NaN in every output so that the caller sees it.
+__global__ void noalloc_flag_kernel(const unsigned* st, double* G, double* c, double* yty, int64_t p) {
+  if ((*st & kStatTimeout) == 0) return;
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
+  const int64_t n = p * p;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    G[i] = nan;
+    if (i < p) c[i] = nan;
+    if (i == 0) yty[0] = nan;
+  }
+}
 }  // namespace oem
 
 using namespace oem;
@@ -64,6 +90,13 @@ extern "C" int oem_gram_noalloc(const void* X, int32_t xtype, int64_t n, int64_t
   if (mode == OEM_GRAM_BF16 && xtype != OEM_BF16) return OEM_EINVAL;
   if (mode < OEM_GRAM_FP64 || mode > OEM_GRAM_SPLIT_BF16) return OEM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return OEM_ECUDA; }
+    if (!on_device(X, dev) || !on_device(y, dev) || !on_device(G, dev) || !on_device(c, dev) ||
+        !on_device(yty, dev))
+      return OEM_EINVAL;
+  }
 
   void* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) { cudaGetLastError(); return OEM_ECUDA; }
@@ -116,6 +149,11 @@ extern "C" int oem_gram_noalloc(const void* X, int32_t xtype, int64_t n, int64_t
   if (e == cudaSuccess) e = launch_gram_reduce(a, 1, Zg, s);
   if (e == cudaSuccess)
     e = launch_extract_folds(Zg, 1, a.q, (int)p, a.ycols, G, c, yty, nk, a.ct.fold_off, s);
+  if (e == cudaSuccess) {
+    noalloc_flag_kernel<<<std::max<int>(1, (int)std::min<int64_t>(sms, (p * p + 255) / 256)), 256, 0, s>>>(
+        a.dstatus, G, c, yty, p);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) { cudaGetLastError(); return OEM_ECUDA; }
   return OEM_OK;
 }

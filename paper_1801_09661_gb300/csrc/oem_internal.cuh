@@ -62,13 +62,17 @@ struct GramArgs {
 // bfloat16 modes): every fold's rows padded with zero rows to a multiple of
 // 32, qp = round_up(q, 128) columns.
 struct TmaBufs {
-  void* zhi;            // [rows_cap][qp] bfloat16
+  void* zhi;            // [rows_cap][qp] bfloat16 (direct: [rows_cap][tail_cols], the tail)
   void* zlo;            // [rows_cap][qp] bfloat16 (split mode) or NULL
   int32_t qp;
   int64_t rows_cap;     // n + kGramPackRows K
   ChunkTable pc;        // chunks of packed rows; pc.fold_off = packed fold offsets
   int32_t max_chunks;
   int64_t chunk_rows;
+  // direct mode (bfloat16 X, one fold, no column of ones): the first nbx
+  // 64-column boxes of Z are read by TMA from X itself; only the tail --
+  // X's columns [64 nbx, p), the y columns, zeros up to tail_cols -- is packed
+  int32_t direct, nbx, tail_cols;
 };
 
 // tile index -> (ti, tj), ti <= tj, row-major over the upper triangle
@@ -100,6 +104,8 @@ cudaError_t launch_check_finite(const void* X, int32_t xtype, int64_t n, int64_t
 size_t gram_tma_smem_bytes();
 // packed chunk table + the packing pass (fold order, zero-padded folds)
 cudaError_t launch_zpack(const GramArgs& a, int K, const TmaBufs& t, cudaStream_t s);
+// direct mode: packed chunk table and the tail of Z (bfloat16 X, one fold)
+cudaError_t launch_tail_pack(const GramArgs& a, const TmaBufs& t, cudaStream_t s);
 cudaError_t launch_gram_tma(const GramArgs& a, const TmaBufs& t, int flush_rows, cudaStream_t s);
 cudaError_t launch_gram_reduce(const GramArgs& a, int K, double* Zg, cudaStream_t s);
 
@@ -339,11 +345,13 @@ struct IterLaunch {
   int32_t grid;          // 1: cooperative launch, C CTAs per task, global-memory exchange
   int32_t max_rows;      // longest CTA slice of the launch (picks the row group)
   int32_t groups;        // some task has a group penalty (group arrays in shared memory)
-  int32_t wide;          // column-segment mat-vec (p > kIterWideP; replicated kernel)
+  int32_t wide;          // long rows: 512 threads, one G row per warp (replicated kernel, float32)
   double tol;
   int64_t max_iter;      // per lambda
   int64_t max_loops;     // per launch (<= 0: run to completion)
   int64_t wait_cycles;   // bound of every device wait (clock64 cycles)
+  int32_t test_stall;    // tests only: the first exchange waits for data nobody sends,
+                         // so its bounded wait runs out (replicated kernel)
   unsigned* dstatus;
   size_t smem;
 };
@@ -353,8 +361,10 @@ int oem_iter_mpad(int npen);
 // Replicated-update kernel (oem_iter.cu), used for p <= kIterRepMaxP: every
 // CTA of a task keeps u, beta and dbeta of all p rows and applies the
 // thresholds to all of them; only the mat-vec rows are split between CTAs.
-constexpr int kIterRepMaxP = 4096;
-constexpr int kIterWideP = 1024;   // above: column-segment mat-vec, 512 threads
+// Above it the replicated threshold work outweighs the exchange it saves and
+// the row-owned kernel serves.
+constexpr int kIterRepMaxP = 1024;
+constexpr int kIterWideP = 512;    // above, with at most 16 rows per CTA: the long-row variant
 // Shared memory besides the resident Gram rows, and per resident row.
 size_t oem_iter_smem_fixed(int p, int M, int max_rows, int precision, bool grid, bool groups);
 size_t oem_iter_smem_per_row(int p, int precision);
@@ -366,7 +376,9 @@ cudaError_t launch_oem_iter(const IterLaunch& P, cudaStream_t s);
 size_t oem_iter_xbuf_bytes(int p, int M, int precision);
 
 // Row-owned kernel (oem_iter_rows.cu), used for p > kIterRepMaxP: CTA r owns
-// rows of u and beta and exchanges dbeta and the maxima.
+// rows of u and beta and exchanges dbeta and the maxima (grid mode: tagged
+// words in the exchange buffer, which needs oem_iter_rows_xbuf_bytes).
+size_t oem_iter_rows_xbuf_bytes(int p, int M, int precision, int C);
 size_t oem_iter_rows_smem_fixed(int p, int npen, int max_rows, int precision);
 size_t oem_iter_rows_smem_per_row(int p, int precision);
 int oem_iter_rows_max_cluster(const IterLaunch& P);

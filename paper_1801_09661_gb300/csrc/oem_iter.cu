@@ -46,31 +46,35 @@ namespace oem {
 
 int oem_iter_mpad(int npen) { return npen <= 1 ? 1 : npen <= 2 ? 2 : npen <= 4 ? 4 : 8; }
 
-constexpr int kWideRows = 16;  // wide mat-vec: G rows per CTA held in registers
 
-__host__ __device__ constexpr int rep_threads(bool wide) { return wide ? 512 : 256; }
-__host__ __device__ inline int rep_nseg(int p) { return (p + 127) / 128; }
+// 512 threads: one G row per warp held in registers (long rows); else 256.
+__host__ __device__ constexpr int rep_threads(bool longrow) { return longrow ? 512 : 256; }
+constexpr int kRepMaxWarps = 16;
 
 // Shared-memory carve-up (byte offsets, 16-byte aligned).
 struct RepSmem {
-  size_t db, yb, uh, ul, be, gn, cg, gl, part, lred, xbar, gs, total;
+  size_t db, yb, uh, ul, be, gn, cg, gl, sl, sn, lred, xbar, gs, total;
 };
-__host__ __device__ inline RepSmem rep_smem_layout(int p, int M, int tsz, bool wide, bool grid,
-                                                   bool groups, int maxR, int smem_rows) {
+// Group slots per instance: whole groups packed into 32-lane slots (groups
+// of at most 32 rows; at least half a slot is used, so p / 16 + 2 slots).
+__host__ __device__ inline int rep_gslots(int p) { return p / 16 + 2; }
+__host__ __device__ inline RepSmem rep_smem_layout(int p, int M, int tsz, bool grid, bool groups,
+                                                   int smem_rows) {
   const int ldgs = (p + 3) & ~3;
-  const int NW = rep_threads(wide) / 32;
+  const int NW = kRepMaxWarps;
   const size_t pm = (size_t)p * M;
   RepSmem L;
   size_t o = 0;
   L.db = o;   o = al16(o + 2 * (size_t)ldgs * M * tsz);           // dbeta, two parities
-  L.yb = o;   o = al16(o + (grid ? 0 : 2 * (size_t)ldgs * M * tsz));  // G dbeta received, two parities
+  L.yb = o;   o = al16(o + 2 * (size_t)ldgs * M * tsz);           // G dbeta received, two parities
   L.uh = o;   o = al16(o + pm * tsz);
   L.ul = o;   o = al16(o + pm * tsz);
   L.be = o;   o = al16(o + pm * tsz);
   L.gn = o;   o = al16(o + (groups ? pm * tsz : 0));              // group norm per element
   L.cg = o;   o = al16(o + (groups ? pm * tsz : 0));              // group weight per element
   L.gl = o;   o = al16(o + (groups ? pm * 4 : 0));                // group length at group starts
-  L.part = o; o = al16(o + (wide ? (size_t)rep_nseg(p) * maxR * M * tsz : 0));
+  L.sl = o;   o = al16(o + (groups ? (size_t)M * rep_gslots(p) * 32 * 4 : 0));  // group slots
+  L.sn = o;   o = al16(o + (groups ? (size_t)(M + 1) * 4 : 0));   // slots per instance, long-group flag
   L.lred = o; o = al16(o + (size_t)2 * NW * 2 * M * 4);
   L.xbar = o; o = al16(o + 32);                                   // two mbarriers, timeout flag
   L.gs = o;   o = al16(o + (size_t)smem_rows * ldgs * tsz);
@@ -78,7 +82,7 @@ __host__ __device__ inline RepSmem rep_smem_layout(int p, int M, int tsz, bool w
   return L;
 }
 
-template <typename T, int M, int NT, bool kGrid, int RG, bool kWide>
+template <typename T, int M, int NT, bool kGrid, int RG, bool kLong>
 __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   constexpr int NW = NT / 32;
   constexpr bool kF32 = sizeof(T) == 4;
@@ -86,22 +90,21 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   static_assert(NT % M == 0 && 32 % M == 0, "instances per lane layout");
   // elements per thread whose state lives in registers (the wide mat-vec's
   // G rows take most of the 128 registers a thread has at 512 threads)
-  constexpr int kRepJR = kWide ? 2 : 4;
+  constexpr int kRepJR = kLong ? 2 : 4;
   cg::cluster_group cluster = cg::this_cluster();
   const int C = P.C;
   const int rank = kGrid ? (int)(blockIdx.x % C) : (int)cluster.block_rank();
   const IterTask& tk = P.tasks[blockIdx.x / C];
-  const int p = tk.p, L = tk.L, m = tk.npen, maxR = tk.max_rows;
+  const int p = tk.p, L = tk.L, m = tk.npen;
   const int i0 = kGrid ? tk.gslice[rank] : tk.slice[rank];
   const int R = (kGrid ? tk.gslice[rank + 1] : tk.slice[rank + 1]) - i0;
   const int ldgs = (p + 3) & ~3, smem_rows = tk.smem_rows;
   const int PM = p * M;
-  const int nseg = kWide ? rep_nseg(p) : 0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long wait_lim = P.wait_cycles > 0 ? P.wait_cycles : 4000000000LL;
 
   extern __shared__ __align__(16) unsigned char smem[];
-  const RepSmem Ls = rep_smem_layout(p, M, (int)sizeof(T), kWide, kGrid, P.groups != 0, maxR, smem_rows);
+  const RepSmem Ls = rep_smem_layout(p, M, (int)sizeof(T), kGrid, P.groups != 0, smem_rows);
   T* const Dbuf = reinterpret_cast<T*>(smem + Ls.db);
   T* const Ybuf = reinterpret_cast<T*>(smem + Ls.yb);   // [2][ldgs][M]
   T* const uhs = reinterpret_cast<T*>(smem + Ls.uh);
@@ -110,8 +113,11 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
   T* const gns = reinterpret_cast<T*>(smem + Ls.gn);
   T* const cgs = reinterpret_cast<T*>(smem + Ls.cg);
   int* const gls = reinterpret_cast<int*>(smem + Ls.gl);
-  T* const part = reinterpret_cast<T*>(smem + Ls.part);
-  float* const lred = reinterpret_cast<float*>(smem + Ls.lred);  // [2][NW][2M]
+  uint32_t* const gsl = reinterpret_cast<uint32_t*>(smem + Ls.sl);  // [M][gsm][32]: row | start << 16 | end << 21
+  int* const gsn = reinterpret_cast<int*>(smem + Ls.sn);            // [M] slots, [M] any group > 32 rows
+  volatile int* const long_grp = gsn + M;
+  const int gsm = rep_gslots(p);
+  float* const lred = reinterpret_cast<float*>(smem + Ls.lred);  // [2][NW][2M] (room for 16 warps)
   const uint32_t xbar0 = xs_u32(smem + Ls.xbar);                 // mbarriers of Ybuf parities 0 / 1
   T* const Gs = reinterpret_cast<T*>(smem + Ls.gs);
   unsigned long long* const xw = reinterpret_cast<unsigned long long*>(tk.xD);  // grid: [2][PM][W]
@@ -208,6 +214,30 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
       }
       cgs[e2] = cgv; gls[e2] = gl; gns[e2] = T(0);
     }
+    for (int e3 = tid; e3 < M * gsm * 32; e3 += NT) gsl[e3] = 0xFFFFFFFFu;
+    if (tid == 0) *long_grp = 0;
+    __syncthreads();
+    // pack each group instance's groups, in order, into 32-lane slots
+    if (lane == 0 && warp < M) {
+      const int k = warp;
+      int sl = 0, used = 0, lng = 0;
+      if (k < m && tk.pens[k].kind >= OEM_GROUP_LASSO) {
+        for (int i = 0; i < p;) {
+          const int len = max(1, gls[k * p + i]);
+          if (len > 32) { lng = 1; break; }
+          if (used + len > 32) { ++sl; used = 0; }
+          if (sl >= gsm) { lng = 1; break; }  // cannot happen for groups <= 32 rows
+          for (int q = 0; q < len; ++q)
+            gsl[((size_t)k * gsm + sl) * 32 + used + q] =
+                (uint32_t)(i + q) | ((uint32_t)used << 16) | ((uint32_t)(used + len - 1) << 21);
+          used += len;
+          i += len;
+        }
+        if (used) ++sl;
+      }
+      gsn[k] = sl;
+      if (lng) atomicOr((int*)long_grp, 1);
+    }
   }
   for (int e = tid; e < 2 * ldgs * M; e += NT) Dbuf[e] = T(0);
   if (kAsync && tid == 0) {
@@ -220,33 +250,30 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
     Gs[e] = (i < R && j < p) ? Gglob[(size_t)(i0 + i) * ldgg + j] : T(0);
   }
 
-  // ---- mat-vec roles
-  // row-owned (p <= 1024): warp w owns rows [wlo, whi) of the CTA's slice;
-  // a row group is RG rows (V = RG M sums); after the reduce-scatter lane l
-  // holds the sum of value v = l / S, S = 32 / V: row rsub = v / M of the
-  // group and instance kv = v % M (the first lane of each group of S acts).
+  // ---- mat-vec roles: warp w owns rows [wlo, whi) of the CTA's slice; a
+  // row group is RG rows (V = RG M sums); after the reduction lane l holds
+  // the sum of value v = l / S, S = 32 / V: row rsub = v / M of the group and
+  // instance kv = v % M (the first lane of each group of S acts). Lane l runs
+  // over columns 4l .. 4l+3, + 128, ... and the lanes' sums meet in one
+  // butterfly, for every p and every layout.
   constexpr int V = RG * M, S = 32 / V;
-  static_assert(V == 4 || V == 8 || V == 16, "row group");
+  static_assert(V == 1 || V == 2 || V == 4 || V == 8 || V == 16, "row group");
   const int vq = lane / S, rsub = vq / M, kv = vq % M;
   const bool even = (lane % S) == 0;
   int wlo = 0, whi = 0;
-  if constexpr (!kWide) {
+  {
     const int per = (R + NW - 1) / NW;
     wlo = min(R, warp * per);
     whi = min(R, wlo + per);
   }
-  // Float32 G rows in registers: row-owned with one row group per warp and
-  // p <= 512 (lane l holds columns 4l .. 4l+3 + 128 s of each row); wide with
-  // at most kWideRows rows per CTA and one segment per warp (lane l holds
-  // columns 128 w + 4l .. 4l+3 of every row). Same products in the same order
-  // as from shared memory.
-  constexpr int kGS = 4;
-  constexpr bool kGregT = kF32 && !kWide && RG <= 4;
+  // Float32 G rows in registers when a warp holds one row group: lane l
+  // holds columns 4l .. 4l+3 + 128 s of each row, s < kGS (p <= 512 with
+  // 256 threads; one row per warp and p <= 2048 with 512). Same products in
+  // the same order as from shared memory.
+  constexpr int kGS = kLong ? 16 : 4;
+  constexpr bool kGregT = kF32 && RG <= 4;
   const bool greg_on = kGregT && (whi - wlo) <= RG && p <= 128 * kGS;
   float4 greg[kGregT ? RG : 1][kGregT ? kGS : 1];
-  constexpr bool kWregT = kF32 && kWide;
-  const bool wreg_on = kWregT && R <= kWideRows && nseg <= NW;
-  float4 wreg[kWregT ? kWideRows : 1];
   auto grow = [&](int ib) -> const T* {  // local row ib of this CTA's slice
     return ib < smem_rows ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
   };
@@ -261,15 +288,6 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
         if (greg_on && r < whi - wlo && j4 < p) g = *reinterpret_cast<const float4*>(grow(wlo + r) + j4);
         greg[r][sx] = g;
       }
-  }
-  if constexpr (kWregT) {
-#pragma unroll
-    for (int r = 0; r < kWideRows; ++r) {
-      float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-      const int j4 = 128 * warp + lane * 4;
-      if (wreg_on && r < R && j4 < p) g = *reinterpret_cast<const float4*>(grow(r) + j4);
-      wreg[r] = g;
-    }
   }
   if constexpr (!kGrid) cluster.sync();  // every CTA initialised before any DSMEM access
 
@@ -288,6 +306,8 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
     const bool got_y = !skip_mv;
     const unsigned b = xc & 1;
     const unsigned tag = xc + 1;
+    // the tag a reader waits for (test_stall: one that is never written)
+    const unsigned want_tag = tag + ((P.test_stall && xc == 0) ? 1u : 0u);
     T* Yb = Ybuf + (size_t)b * ldgs * M;  // parities 16-byte aligned
     if (got_y) {
       // ---- A. y = G dbeta for this CTA's rows, delivered to every CTA
@@ -307,7 +327,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
           for (int r = 0; r < C; ++r) cluster.map_shared_rank(Yb, r)[e] = y;
         }
       };
-      if constexpr (!kWide) {
+      {
         for (int gb = wlo; gb < whi; gb += RG) {
           const int nv = min(RG, whi - gb);
           T acc[V];
@@ -365,7 +385,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
               }
             }
           }
-          const T y = reduce_scatter<V>(acc, lane);
+          const T y = reduce_scatter_any<V>(acc, lane);
           if (even && gb + rsub < whi) deliver(gb + rsub, kv, y);
         }
         if constexpr (kAsync) {
@@ -391,114 +411,14 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
             }
           }
         }
-      } else {
-        // column segments: warp w takes segments w, w + NW, ...; per segment
-        // and group of 16 / M rows one reduce-scatter of the lanes' partial
-        // sums into part[segment][row][instance]
-        constexpr int RGW = 16 / M;
-        for (int s = warp; s < nseg; s += NW) {
-          const int j4 = 128 * s + lane * 4;
-          float dv[4][M];
-          if constexpr (kF32) {
-#pragma unroll
-            for (int q = 0; q < M; ++q) {
-              float4 tq = make_float4(0.f, 0.f, 0.f, 0.f);
-              if (j4 < p) {
-                const int u = (j4 * M >> 2) + q;
-                tq = *reinterpret_cast<const float4*>(Dp + ((u ^ ((u >> 3) & (M - 1))) << 2));
-              }
-              const float tv[4] = {tq.x, tq.y, tq.z, tq.w};
-#pragma unroll
-              for (int e = 0; e < 4; ++e) dv[(q * 4 + e) / M][(q * 4 + e) % M] = tv[e];
-            }
-          }
-          for (int rg = 0; rg < R; rg += RGW) {
-            T acc[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) acc[q] = T(0);
-            if constexpr (kF32) {
-              if (j4 < p) {
-#pragma unroll
-                for (int r = 0; r < RGW; ++r) {
-                  float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                  if (rg + r < R) {
-                    if (kWregT && wreg_on) {
-#pragma unroll
-                      for (int q = 0; q < kWideRows; ++q)
-                        if (q == rg + r) g4 = wreg[kWregT ? q : 0];
-                    } else {
-                      g4 = *reinterpret_cast<const float4*>(grow(rg + r) + j4);
-                    }
-                  }
-                  const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
-#pragma unroll
-                  for (int c = 0; c < 4; ++c)
-#pragma unroll
-                    for (int k = 0; k < M; ++k) acc[r * M + k] = fma(gv[c], dv[c][k], acc[r * M + k]);
-                }
-              }
-            } else {
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                const int j = j4 + c;
-                if (j < p) {
-                  T dd[M];
-                  load_col<T, M>(Dp, j, dd);
-#pragma unroll
-                  for (int r = 0; r < RGW; ++r) {
-                    const T g = rg + r < R ? grow(rg + r)[j] : T(0);
-#pragma unroll
-                    for (int k = 0; k < M; ++k) acc[r * M + k] = fma(g, dd[k], acc[r * M + k]);
-                  }
-                }
-              }
-            }
-            const T y = reduce_scatter<16>(acc, lane);
-            const int row = rg + (lane >> 1) / M, k = (lane >> 1) % M;
-            if ((lane & 1) == 0 && row < R) part[((size_t)s * maxR + row) * M + k] = y;
-          }
-        }
-        __syncthreads();
-        // segment sums in segment order, 4 consecutive words per thread
-        const int nw = R * M;
-        for (int u = tid; 4 * u < nw; u += NT) {
-          T yv4[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int wd = 4 * u + q;
-            T y = T(0);
-            if (wd < nw)
-              for (int s = 0; s < nseg; ++s) y += part[((size_t)s * maxR + wd / M) * M + wd % M];
-            yv4[q] = y;
-          }
-          if constexpr (kAsync) {
-            float* dst = Yb + i0 * M + 4 * u;
-            const uint32_t bar = xbar0 + 8 * b;
-            if (4 * u + 4 <= nw) {
-              const float4 v4 = make_float4(yv4[0], yv4[1], yv4[2], yv4[3]);
-              *reinterpret_cast<float4*>(dst) = v4;
-              for (int r = 0; r < C; ++r)
-                if (r != rank) xs_st4(xs_map(xs_u32(dst), r), v4, xs_map(bar, r));
-            } else {
-              for (int q = 0; 4 * u + q < nw; ++q) {
-                dst[q] = yv4[q];
-                for (int r = 0; r < C; ++r)
-                  if (r != rank) xs_st1(xs_map(xs_u32(dst + q), r), __float_as_uint(yv4[q]), xs_map(bar, r));
-              }
-            }
-          } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              if (4 * u + q < nw) deliver((4 * u + q) / M, (4 * u + q) % M, yv4[q]);
-          }
-        }
       }
       // ---- wait for every CTA's y
       if constexpr (kAsync) {
         __syncwarp();
         const uint32_t bar = xbar0 + 8 * b;
         if (lane == 0) {
-          if (warp == 0) xs_arm(bar, (uint32_t)((p - R) * M * 4));
+          // test_stall: four bytes more than the peers send
+          if (warp == 0) xs_arm(bar, (uint32_t)((p - R) * M * 4) + ((P.test_stall && xc == 0) ? 4u : 0u));
           else xs_arrive(bar);
         }
         const uint32_t par = (xc >> 1) & 1u;
@@ -517,57 +437,62 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
 
     // ---- B, C. u update, thresholds, dbeta and maxima for this thread's elements
     // y of element e (grid mode: polled until its tag is this exchange's)
-    auto poll = [&](int e) -> T {
-      if constexpr (kGrid) {
-        if (fail) return T(0);  // a wait of this iteration expired already
-        const unsigned want = tag;
-        long long t0 = 0;
-        for (int tries = 0;; ++tries) {
-          if constexpr (kF32) {
-            const unsigned long long w = ld_tag1(xw + (size_t)b * PM + e);
-            if ((unsigned)(w >> 32) == want) return __uint_as_float((uint32_t)w);
-          } else {
-            unsigned long long w0, w1;
-            ld_tag2(xw + ((size_t)b * PM + e) * 2, w0, w1);
-            if ((unsigned)(w0 >> 32) == want && (unsigned)(w1 >> 32) == want)
-              return __longlong_as_double((long long)(((w1 & 0xffffffffull) << 32) | (w0 & 0xffffffffull)));
-          }
-          if (tries == 0) t0 = clock64();
-          else if (clock64() - t0 > wait_lim) { fail = true; return T(0); }
-        }
-      } else {
-        return Yb[e];
-      }
-    };
+    // grid mode: y of this thread's elements from global memory -- the loads
+    // of a batch of elements in flight at once, the stale ones again (after a
+    // short pause, to spare L2 the spinning) until their tag is this
+    // exchange's; register elements' values go to yr, the others to this
+    // thread's own slots of Yb (cluster mode: already in Yb)
     T yr[kRepJR];
 #pragma unroll
     for (int j = 0; j < kRepJR; ++j) yr[j] = T(0);
     if (got_y) {
       if constexpr (kGrid) {
-        // first the loads of every register element, then the checks
-        unsigned long long wv[kRepJR][2];
+        constexpr int kB = kLong ? 4 : 8;
+        long long t0 = 0;
+        bool started = false;
+        for (int j0 = 0; j0 < nJ && !fail; j0 += kB) {
+          unsigned long long w0[kB], w1[kB];
+          unsigned pend = 0;
 #pragma unroll
-        for (int j = 0; j < kRepJR; ++j) {
-          const int e = tid + NT * j;
-          wv[j][0] = wv[j][1] = 0ull;
-          if (e < PM) {
-            if constexpr (kF32) wv[j][0] = ld_tag1(xw + (size_t)b * PM + e);
-            else ld_tag2(xw + ((size_t)b * PM + e) * 2, wv[j][0], wv[j][1]);
-          }
-        }
+          for (int q = 0; q < kB; ++q)
+            if (j0 + q < nJ && tid + NT * (j0 + q) < PM) pend |= 1u << q;
+          while (pend) {
 #pragma unroll
-        for (int j = 0; j < kRepJR; ++j) {
-          const int e = tid + NT * j;
-          if (e < PM) {
-            bool hit;
-            if constexpr (kF32) hit = (unsigned)(wv[j][0] >> 32) == tag;
-            else hit = (unsigned)(wv[j][0] >> 32) == tag && (unsigned)(wv[j][1] >> 32) == tag;
-            if (hit) {
-              if constexpr (kF32) yr[j] = __uint_as_float((uint32_t)wv[j][0]);
-              else yr[j] = __longlong_as_double((long long)(((wv[j][1] & 0xffffffffull) << 32) | (wv[j][0] & 0xffffffffull)));
-            } else {
-              yr[j] = poll(e);
+            for (int q = 0; q < kB; ++q) {
+              const size_t e = (size_t)tid + (size_t)NT * (j0 + q);
+              if ((pend >> q) & 1u) {
+                if constexpr (kF32) w0[q] = ld_tag1(xw + (size_t)b * PM + e);
+                else ld_tag2(xw + ((size_t)b * PM + e) * 2, w0[q], w1[q]);
+              }
             }
+#pragma unroll
+            for (int q = 0; q < kB; ++q) {
+              if (!((pend >> q) & 1u)) continue;
+              const int e = tid + NT * (j0 + q);
+              bool hit;
+              T v;
+              if constexpr (kF32) {
+                hit = (unsigned)(w0[q] >> 32) == want_tag;
+                v = __uint_as_float((uint32_t)w0[q]);
+              } else {
+                hit = (unsigned)(w0[q] >> 32) == want_tag && (unsigned)(w1[q] >> 32) == want_tag;
+                v = __longlong_as_double((long long)(((w1[q] & 0xffffffffull) << 32) | (w0[q] & 0xffffffffull)));
+              }
+              if (hit) {
+                if (j0 == 0 && q < kRepJR) yr[q < kRepJR ? q : 0] = v;
+                else Yb[e] = v;
+                pend &= ~(1u << q);
+              }
+            }
+            if (!pend) break;
+            if (!started) {
+              t0 = clock64();
+              started = true;
+            } else if (clock64() - t0 > wait_lim) {
+              fail = true;
+              break;
+            }
+            __nanosleep(64);
           }
         }
       } else {
@@ -599,18 +524,30 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
       }
     };
     T lmd = T(0), lmb = T(0);  // this thread's running max |dbeta|, |beta| (instance kq)
+    T gmd[M], gmb[M];          // group tasks: per instance
+#pragma unroll
+    for (int k = 0; k < M; ++k) { gmd[k] = T(0); gmb[k] = T(0); }
+    auto gmax = [&](int k, T dn, T bn) {
+#pragma unroll
+      for (int kk = 0; kk < M; ++kk)
+        if (kk == k) { gmd[kk] = fmax(gmd[kk], fabs(dn)); gmb[kk] = fmax(gmb[kk], fabs(bn)); }
+    };
     if (final_pass) {
       // the pending dbeta applied to u, for a resumed launch to continue from
 #pragma unroll
       for (int j = 0; j < kRepJR; ++j) {
         const int e = tid + NT * j;
-        if (e < PM) { u_update(r_uh[j], r_ul[j], r_dn[j], yr[j]); uhs[e] = r_uh[j]; uls[e] = r_ul[j]; }
+        if (e < PM) {
+          u_update(r_uh[j], r_ul[j], has_group ? Dp[dpos<T, M>(e / M, kq)] : r_dn[j], yr[j]);
+          uhs[e] = r_uh[j];
+          uls[e] = r_ul[j];
+        }
       }
       for (int j = kRepJR; j < nJ; ++j) {
         const int e = tid + NT * j;
         if (e >= PM) break;
         T uh = uhs[e], ul = uls[e];
-        u_update(uh, ul, Dp[dpos<T, M>(e / M, kq)], got_y ? poll(e) : T(0));
+        u_update(uh, ul, Dp[dpos<T, M>(e / M, kq)], got_y ? Yb[e] : T(0));
         uhs[e] = uh; uls[e] = ul;
       }
       break;
@@ -646,115 +583,190 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
         if (e >= PM) break;
         const int i = e / M;
         T uh = uhs[e], ul = uls[e], bv = bes[e];
-        const T dn = scalar_step(uh, ul, bv, weight(i), Dp[dpos<T, M>(i, kq)], got_y ? poll(e) : T(0));
+        const T dn = scalar_step(uh, ul, bv, weight(i), Dp[dpos<T, M>(i, kq)], got_y ? Yb[e] : T(0));
         uhs[e] = uh; uls[e] = ul; bes[e] = bv;
         Dn[dpos<T, M>(i, kq)] = dn;
       }
     } else {
-      // ---- C1. u update of every element (kept in shared memory for the norms)
+      // Group tasks keep beta and dbeta in shared memory (the group step
+      // writes them by group, not by thread); u stays in this thread's
+      // registers and its shared copy feeds the norms.
+      // ---- C1. u update of every element; scalar instances of the task are
+      // thresholded here too
+      auto c1 = [&](T& uh, T& ul, int e, T y) {
+        const int i = e / M;
+        u_update(uh, ul, Dp[dpos<T, M>(i, kq)], y);
+        uhs[e] = uh;
+        if (my_inst && my_kind < OEM_GROUP_LASSO) {
+          const T bv = bes[e];
+          T dn = T(0);
+          if (!my_done) {
+            const T bn = thr_scalar<T>(my_kind, uh, weight(i) * my_lam, my_alpha, my_gamma, my_d);
+            dn = bn - bv;
+            bes[e] = bn;
+            gmax(kq, dn, bn);
+          } else {
+            gmax(kq, T(0), bv);
+          }
+          Dn[dpos<T, M>(i, kq)] = dn;
+        }
+      };
 #pragma unroll
       for (int j = 0; j < kRepJR; ++j) {
         const int e = tid + NT * j;
-        if (e < PM) { u_update(r_uh[j], r_ul[j], r_dn[j], yr[j]); uhs[e] = r_uh[j]; }
+        if (e < PM) c1(r_uh[j], r_ul[j], e, yr[j]);
       }
       for (int j = kRepJR; j < nJ; ++j) {
         const int e = tid + NT * j;
         if (e >= PM) break;
         T uh = uhs[e], ul = uls[e];
-        u_update(uh, ul, Dp[dpos<T, M>(e / M, kq)], got_y ? poll(e) : T(0));
-        uhs[e] = uh; uls[e] = ul;
+        c1(uh, ul, e, got_y ? Yb[e] : T(0));
+        uls[e] = ul;
       }
       __syncthreads();
-      // ---- C2. group norms ||u_g|| (sparse group lasso: ||v_g||, v = S(u, w lambda tau) / d)
-      for (int e2 = tid; e2 < PM; e2 += NT) {
-        const int len = gls[e2];
-        if (len == 0) continue;
-        const int k = e2 / p, i = e2 % p;
-        int kd = OEM_LASSO;
-        T lt = T(0), dd = T(1);
-        const float* gw32 = nullptr;
-        const double* gw64 = nullptr;
+      if (!*long_grp) {
+        // ---- C2. one warp per slot of whole groups (Section 2.2: Eqs.
+        // glasso, gmcp, gscad, sglasso need ||u_g||, or ||v_g|| with
+        // v = S(u, w lambda tau) / d): the squares summed by a segmented
+        // warp scan over each group's lanes, then every lane's update
+        for (int k = 0; k < M; ++k) {
+          if (k >= m) break;
+          int kd = OEM_LASSO;
+          T lamk = T(0), alk = T(1), gak = T(3), dkk = T(1);
+          int dnk = 1;
 #pragma unroll
-        for (int kk = 0; kk < M; ++kk)
-          if (kk == k) { kd = kind[kk]; lt = lamv[kk] * alpha[kk]; dd = dk[kk]; }
-        if (kd == OEM_SPARSE_GROUP_LASSO) { gw32 = tk.pens[k].w32; gw64 = tk.pens[k].w64; }
-        T s2 = T(0);
-        for (int q = 0; q < len; ++q) {
-          const T u = uhs[(i + q) * M + k];
-          if (kd == OEM_SPARSE_GROUP_LASSO) {
-            T wq = T(1);
-            if constexpr (kF32) { if (gw32) wq = (T)gw32[i + q]; }
-            else { if (gw64) wq = (T)gw64[i + q]; }
-            const T v = fmax(fabs(u) - wq * lt, T(0)) / dd;
-            s2 = fma(v, v, s2);
-          } else {
-            s2 = fma(u, u, s2);
-          }
-        }
-        s2 = sqrt(s2);
-        for (int q = 0; q < len; ++q) gns[e2 + q] = s2;
-      }
-      __syncthreads();
-      // ---- C3. thresholds (Eqs. glasso, gmcp, gscad, sglasso; scalar ones for
-      // scalar instances of the task)
-      auto group_step = [&](T uh, T& bv, T wt, int i) -> T {
-        T dn = T(0);
-        if (my_inst) {
-          if (!my_done) {
-            const T u = uh;
-            const int g2 = kq * p + i;
+          for (int kk = 0; kk < M; ++kk)
+            if (kk == k) { kd = kind[kk]; lamk = lamv[kk]; alk = alpha[kk]; gak = gamma[kk]; dkk = dk[kk]; dnk = done[kk]; }
+          if (kd < OEM_GROUP_LASSO) continue;
+          const float* w32k = tk.pens[k].w32;
+          const double* w64k = tk.pens[k].w64;
+          for (int sl = warp; sl < gsn[k]; sl += NW) {
+            const uint32_t info = gsl[((size_t)k * gsm + sl) * 32 + lane];
+            const bool valid = info != 0xFFFFFFFFu;
+            const int i = (int)(info & 0xFFFFu);
+            const int st = valid ? (int)((info >> 16) & 31u) : lane;
+            const int en = valid ? (int)((info >> 21) & 31u) : lane;
+            const int e = i * M + k;
+            const T u = valid ? uhs[e] : T(0);
+            T wt = T(1);
+            if constexpr (kF32) { if (valid && w32k) wt = (T)w32k[i]; }
+            else { if (valid && w64k) wt = (T)w64k[i]; }
+            T v = u;
+            if (kd == OEM_SPARSE_GROUP_LASSO) v = fmax(fabs(u) - wt * lamk * alk, T(0)) / dkk;
+            T sc = v * v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const T tq = __shfl_up_sync(0xffffffffu, sc, o);
+              if (lane - o >= st) sc += tq;
+            }
+            const T nrm = sqrt(__shfl_sync(0xffffffffu, sc, en));
+            if (!valid) continue;
+            const T bv = bes[e];
+            if (dnk) {
+              Dn[dpos<T, M>(i, k)] = T(0);
+              gmax(k, T(0), bv);
+              continue;
+            }
+            const T cgv = cgs[(size_t)k * p + i];
             T bn;
-            if (my_kind == OEM_GROUP_LASSO) {
-              const T nrm = gns[g2];
-              const T f = nrm > T(0) ? T(1) - cgs[g2] * my_lam / nrm : T(0);
-              bn = f > T(0) ? u / my_d * f : T(0);
-            } else if (my_kind == OEM_GROUP_MCP || my_kind == OEM_GROUP_SCAD) {
-              const T nrm = gns[g2];
-              const T bnorm = nrm > T(0) ? thr_scalar<T>(my_kind == OEM_GROUP_MCP ? OEM_MCP : OEM_SCAD, nrm,
-                                                         cgs[g2] * my_lam, my_alpha, my_gamma, my_d)
+            if (kd == OEM_GROUP_LASSO) {
+              const T f = nrm > T(0) ? T(1) - cgv * lamk / nrm : T(0);
+              bn = f > T(0) ? u / dkk * f : T(0);
+            } else if (kd == OEM_GROUP_MCP || kd == OEM_GROUP_SCAD) {
+              // Eqs. gmcp / gscad: the scalar rule on the norm, u's direction
+              const T bnorm = nrm > T(0) ? thr_scalar<T>(kd == OEM_GROUP_MCP ? OEM_MCP : OEM_SCAD, nrm,
+                                                         cgv * lamk, alk, gak, dkk)
                                          : T(0);
               bn = nrm > T(0) ? u * (bnorm / nrm) : T(0);
-            } else if (my_kind == OEM_SPARSE_GROUP_LASSO) {
-              // reading of Eq. sglasso: the group step shrinks v by c_k lambda (1 - tau) / d
-              const T nrm = gns[g2];
-              const T v = copysign(fmax(fabs(u) - wt * my_lam * my_alpha, T(0)) / my_d, u);
-              const T f = nrm > T(0) ? T(1) - cgs[g2] * my_lam * (T(1) - my_alpha) / (my_d * nrm) : T(0);
-              bn = f > T(0) ? v * f : T(0);
             } else {
-              bn = thr_scalar<T>(my_kind, u, wt * my_lam, my_alpha, my_gamma, my_d);
+              // reading of Eq. sglasso: the group step shrinks v by c_k lambda (1 - tau) / d
+              const T vv = copysign(v, u);
+              const T f = nrm > T(0) ? T(1) - cgv * lamk * (T(1) - alk) / (dkk * nrm) : T(0);
+              bn = f > T(0) ? vv * f : T(0);
             }
-            dn = bn - bv;
-            bv = bn;
-            lmd = fmax(lmd, fabs(dn));
-            lmb = fmax(lmb, fabs(bn));
-          } else {
-            lmb = fmax(lmb, fabs(bv));
+            const T dn = bn - bv;
+            bes[e] = bn;
+            Dn[dpos<T, M>(i, k)] = dn;
+            gmax(k, dn, bn);
           }
         }
-        return dn;
-      };
+      } else {
+        // ---- groups longer than a warp: norms by one thread per group,
+        // then every element's update
+        for (int e2 = tid; e2 < PM; e2 += NT) {
+          const int len = gls[e2];
+          if (len == 0) continue;
+          const int k = e2 / p, i = e2 % p;
+          int kd = OEM_LASSO;
+          T lt = T(0), dd = T(1);
 #pragma unroll
-      for (int j = 0; j < kRepJR; ++j) {
-        const int e = tid + NT * j;
-        if (e < PM) {
-          const T dn = group_step(r_uh[j], r_b[j], r_w[j], e / M);
-          r_dn[j] = dn;
-          Dn[dpos<T, M>(e / M, kq)] = dn;
+          for (int kk = 0; kk < M; ++kk)
+            if (kk == k) { kd = kind[kk]; lt = lamv[kk] * alpha[kk]; dd = dk[kk]; }
+          const float* gw32 = kd == OEM_SPARSE_GROUP_LASSO ? tk.pens[k].w32 : nullptr;
+          const double* gw64 = kd == OEM_SPARSE_GROUP_LASSO ? tk.pens[k].w64 : nullptr;
+          T s2 = T(0);
+          for (int q = 0; q < len; ++q) {
+            const T u = uhs[(i + q) * M + k];
+            if (kd == OEM_SPARSE_GROUP_LASSO) {
+              T wq = T(1);
+              if constexpr (kF32) { if (gw32) wq = (T)gw32[i + q]; }
+              else { if (gw64) wq = (T)gw64[i + q]; }
+              const T v = fmax(fabs(u) - wq * lt, T(0)) / dd;
+              s2 = fma(v, v, s2);
+            } else {
+              s2 = fma(u, u, s2);
+            }
+          }
+          s2 = sqrt(s2);
+          for (int q = 0; q < len; ++q) gns[e2 + q] = s2;
         }
-      }
-      for (int j = kRepJR; j < nJ; ++j) {
-        const int e = tid + NT * j;
-        if (e >= PM) break;
-        const int i = e / M;
-        T bv = bes[e];
-        const T dn = group_step(uhs[e], bv, weight(i), i);
-        bes[e] = bv;
-        Dn[dpos<T, M>(i, kq)] = dn;
+        __syncthreads();
+        for (int j = 0; j < nJ; ++j) {
+          const int e = tid + NT * j;
+          if (e >= PM) break;
+          if (!my_inst || my_kind < OEM_GROUP_LASSO) continue;
+          const int i = e / M, g2 = kq * p + i;
+          const T bv = bes[e];
+          if (my_done) {
+            Dn[dpos<T, M>(i, kq)] = T(0);
+            gmax(kq, T(0), bv);
+            continue;
+          }
+          const T u = uhs[e], nrm = gns[g2], cgv = cgs[g2];
+          T bn;
+          if (my_kind == OEM_GROUP_LASSO) {
+            const T f = nrm > T(0) ? T(1) - cgv * my_lam / nrm : T(0);
+            bn = f > T(0) ? u / my_d * f : T(0);
+          } else if (my_kind == OEM_GROUP_MCP || my_kind == OEM_GROUP_SCAD) {
+            const T bnorm = nrm > T(0) ? thr_scalar<T>(my_kind == OEM_GROUP_MCP ? OEM_MCP : OEM_SCAD, nrm,
+                                                       cgv * my_lam, my_alpha, my_gamma, my_d)
+                                       : T(0);
+            bn = nrm > T(0) ? u * (bnorm / nrm) : T(0);
+          } else {
+            const T v = copysign(fmax(fabs(u) - weight(i) * my_lam * my_alpha, T(0)) / my_d, u);
+            const T f = nrm > T(0) ? T(1) - cgv * my_lam * (T(1) - my_alpha) / (my_d * nrm) : T(0);
+            bn = f > T(0) ? v * f : T(0);
+          }
+          const T dn = bn - bv;
+          bes[e] = bn;
+          Dn[dpos<T, M>(i, kq)] = dn;
+          gmax(kq, dn, bn);
+        }
       }
     }
     // ---- D. block maxima per instance: every CTA holds all rows, so these
     // are the task's maxima
-    {
+    if (has_group) {
+      float* lr = lred + (size_t)(t & 1) * NW * 2 * M;
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        const T a1 = warp_max(gmd[k]), a2 = warp_max(gmb[k]);
+        if (lane == 0) {
+          lr[(warp * M + k) * 2] = to_red(a1);
+          lr[(warp * M + k) * 2 + 1] = to_red(a2);
+        }
+      }
+    } else {
 #pragma unroll
       for (int o = M; o < 32; o <<= 1) {
         lmd = fmax(lmd, __shfl_xor_sync(0xffffffffu, lmd, o));
@@ -804,7 +816,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
 #pragma unroll
           for (int j = 0; j < kRepJR; ++j) {
             const int e = tid + NT * j, i = e / M;
-            if (e < PM && i >= i0 && i < i0 + R) out[i] = (double)r_b[j];
+            if (e < PM && i >= i0 && i < i0 + R) out[i] = (double)(has_group ? bes[e] : r_b[j]);
           }
           for (int j = kRepJR; j < nJ; ++j) {
             const int e = tid + NT * j, i = e / M;
@@ -836,7 +848,11 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
 #pragma unroll
     for (int j = 0; j < kRepJR; ++j) {
       const int e = tid + NT * j, i = e / M;
-      if (e < PM) { uhs[e] = r_uh[j]; uls[e] = r_ul[j]; bes[e] = r_b[j]; }
+      if (e < PM) {
+        uhs[e] = r_uh[j];
+        uls[e] = r_ul[j];
+        if (!has_group) bes[e] = r_b[j];
+      }
       (void)i;
     }
     for (int j = 0; j < nJ; ++j) {
@@ -867,7 +883,8 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_kernel(IterLaunch P) {
 
 size_t oem_iter_smem_fixed(int p, int M, int max_rows, int precision, bool grid, bool groups) {
   const int tsz = precision == OEM_ITER_F64 ? 8 : 4;
-  return rep_smem_layout(p, oem_iter_mpad(M), tsz, p > kIterWideP, grid, groups, max_rows, 0).total;
+  (void)max_rows;
+  return rep_smem_layout(p, oem_iter_mpad(M), tsz, grid, groups, 0).total;
 }
 
 size_t oem_iter_smem_per_row(int p, int precision) {
@@ -880,10 +897,10 @@ size_t oem_iter_xbuf_bytes(int p, int M, int precision) {
   return (2 * (size_t)p * oem_iter_mpad(M) * W * 8 + 255) & ~(size_t)255;
 }
 
-template <typename T, int M, bool kGrid, int RG, bool kWide>
+template <typename T, int M, bool kGrid, int RG, bool kLong>
 static cudaError_t launch_t(const IterLaunch& P, cudaStream_t s, bool query, int* out) {
-  constexpr int NT = rep_threads(kWide);
-  auto kfn = oem_iter_kernel<T, M, NT, kGrid, RG, kWide>;
+  constexpr int NT = rep_threads(kLong);
+  auto kfn = oem_iter_kernel<T, M, NT, kGrid, RG, kLong>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -920,12 +937,15 @@ static cudaError_t launch_t(const IterLaunch& P, cudaStream_t s, bool query, int
   return cudaLaunchKernelEx(&cfg, kfn, P);
 }
 
-// Row group of the row-owned mat-vec: 16 / M rows, or 4 when no warp owns
-// more than 4 rows (the instances then fill fewer sums per lane and no load
-// is wasted); the wide mat-vec always takes 16 / M.
+// Row group: 16 / M rows, or 4 when no warp owns more than 4 rows (the
+// instances then fill fewer sums per lane and no load is wasted); long rows
+// (IterLaunch::wide, float32, at most 2 instances per task): 512 threads,
+// one row per warp.
 template <typename T, int M, bool kGrid>
 static cudaError_t dispatch_w(const IterLaunch& P, cudaStream_t s, bool q, int* out) {
-  if (P.wide) return launch_t<T, M, kGrid, 16 / M, true>(P, s, q, out);
+  if constexpr (sizeof(T) == 4 && M <= 2) {
+    if (P.wide) return launch_t<T, M, kGrid, 1, true>(P, s, q, out);
+  }
   constexpr int RGF = 16 / M;
   if constexpr (RGF > 4) {
     constexpr int NW = rep_threads(false) / 32;

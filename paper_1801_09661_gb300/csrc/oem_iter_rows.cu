@@ -101,7 +101,13 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
   const int p = tk.p, L = tk.L, m = tk.npen, maxR = tk.max_rows;
   const int i0 = kGrid ? tk.gslice[rank] : tk.slice[rank];
   const int R = (kGrid ? tk.gslice[rank + 1] : tk.slice[rank + 1]) - i0;
-  T* const xD = reinterpret_cast<T*>(tk.xD);  // grid mode
+  // grid mode exchange buffer (zeroed before the launch): [2][p M W] tagged
+  // words of dbeta, [2][C][2M] tagged words of the CTAs' maxima, then the
+  // two words of the start barrier
+  constexpr int W = sizeof(T) / 4;
+  unsigned long long* const xw = reinterpret_cast<unsigned long long*>(tk.xD);
+  unsigned long long* const xm = xw + (size_t)2 * tk.p * M * W;
+  unsigned* const xbarg = reinterpret_cast<unsigned*>(xm + (size_t)2 * P.C * 2 * M);
   unsigned bar_gen = 0;
   const long long wait_lim = P.wait_cycles > 0 ? P.wait_cycles : 4000000000LL;
   const int ldgs = (p + 3) & ~3, smem_rows = tk.smem_rows;
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
     Gs[e] = (i < R && j < p) ? Gglob[(size_t)(i0 + i) * ldgg + j] : T(0);
   }
   if constexpr (kGrid) {
-    if (!group_barrier(tk.xbar, (unsigned)C, bar_gen, wait_lim)) {
+    if (!group_barrier(xbarg, (unsigned)C, bar_gen, wait_lim)) {
       if (tid == 0) atomicOr(P.dstatus, kStatTimeout);
       return;
     }
@@ -296,17 +302,6 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
     const int cur = t & 1, nxt = cur ^ 1;
     const T* Dc = Dbuf + (size_t)cur * ldgs * M;
     const int nr = whi - wlo;
-    if constexpr (kGrid) {
-      // the whole dbeta of the last iteration, from L2 (not L1: other SMs
-      // wrote it)
-      if (!skip_mv) {
-        const float4* src = reinterpret_cast<const float4*>(xD + (size_t)cur * ldgs * M);
-        float4* dst = reinterpret_cast<float4*>(Dbuf + (size_t)cur * ldgs * M);
-        const int nv4 = (int)((size_t)ldgs * M * sizeof(T) / 16);
-        for (int e = tid; e < nv4; e += NT) dst[e] = __ldcg(src + e);
-      }
-      __syncthreads();
-    }
     T lmd = T(0), lmb = T(0);  // this lane's running max |dbeta|, |beta| (instance kq)
     // ---- 1. per group of RG rows: y = G dbeta for all instances (one pass
     // over dbeta for the group), u update and, without groups, the threshold
@@ -553,9 +548,13 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
         // element (i0 is a multiple of 4, so st is unit-aligned)
         const int f0 = (i0 + wlo) * M, f1 = (i0 + whi) * M;
         const int u0 = f0 >> 2, nu = ((f1 + 3) >> 2) - u0;
-        T* Dn = (kGrid ? xD : Dbuf) + (size_t)nxt * ldgs * M;
-        const int CC = kGrid ? 1 : C;
-        if constexpr (kAsync) {
+        T* Dn = Dbuf + (size_t)nxt * ldgs * M;
+        const int CC = C;
+        if constexpr (kGrid) {
+          // this warp's dbeta words, tagged with the iteration number
+          for (int e = f0 + lane; e < f1; e += 32)
+            st_tag1(xw + (size_t)nxt * p * M + e, tag_word(__float_as_uint(st[e - i0 * M]), (uint32_t)t + 1u));
+        } else if constexpr (kAsync) {
           const uint32_t bar = xbar0 + 8 * nxt;
           for (int e = lane; e < nu * C; e += 32) {
             const int u = u0 + e / C, r = e % C;
@@ -584,7 +583,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
         } else {
           for (int e = lane; e < nu * CC; e += 32) {
             const int u = u0 + e / CC, r = e % CC;
-            float* dst = (kGrid ? Dn : cluster.map_shared_rank(Dn, r)) + ((u ^ ((u >> 3) & (M - 1))) << 2);
+            float* dst = cluster.map_shared_rank(Dn, r) + ((u ^ ((u >> 3) & (M - 1))) << 2);
             const float* src = st + (4 * u - i0 * M);
             if (4 * u >= f0 && 4 * u + 4 <= f1) {
               *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(src);
@@ -596,8 +595,11 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
           }
         }
       } else if constexpr (kGrid) {
-        T* Dn = xD + (size_t)nxt * ldgs * M;
-        for (int i = wlo + lane; i < whi; i += 32) store_row<T, M>(Dn, i0 + i, st + (size_t)i * M);
+        for (int e = (i0 + wlo) * M + lane; e < (i0 + whi) * M; e += 32) {
+          const unsigned long long bits = (unsigned long long)__double_as_longlong((double)st[e - i0 * M]);
+          st_tag2(xw + ((size_t)nxt * p * M + e) * 2, tag_word((uint32_t)bits, (uint32_t)t + 1u),
+                  tag_word((uint32_t)(bits >> 32), (uint32_t)t + 1u));
+        }
       } else {
         T* Dn = Dbuf + (size_t)nxt * ldgs * M;
         for (int e = lane; e < nr * C; e += 32) {
@@ -654,7 +656,8 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
         if (lane < E) xred[lane] = mx;
         if (lane == 0 && !ok) *xfail = 1u;
       } else if constexpr (kGrid) {
-        if (lane < E && v > 0.f) atomicMax(tk.xslot + (size_t)(t % 3) * E + lane, __float_as_uint(v));
+        if (lane < E)
+          st_tag1(xm + ((size_t)nxt * C + rank) * E + lane, tag_word(__float_as_uint(v), (uint32_t)t + 1u));
       } else {
         unsigned int* slot = red + (size_t)(t % 3) * E;
         for (int base = 0; base < C * E; base += 32) {
@@ -666,13 +669,67 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
       }
     }
     if constexpr (kGrid) {
-      if (!group_barrier(tk.xbar, (unsigned)C, bar_gen, wait_lim)) {
+      // every CTA's dbeta words into this CTA's next buffer, and every CTA's
+      // maxima into slot t % 3: loads of a batch in flight at once, the stale
+      // ones again after a short pause until their tag is this iteration's
+      const uint32_t want = (uint32_t)t + 1u;
+      T* Dn = Dbuf + (size_t)nxt * ldgs * M;
+      const int nw = p * M, nm = C * 2 * M;
+      bool bad = false;
+      long long w0c = 0;
+      bool started = false;
+      constexpr int kB = 8;
+      for (int base = tid; base < nw + nm && !bad; base += NT * kB) {
+        unsigned long long a0[kB], a1[kB];
+        unsigned pend = 0;
+#pragma unroll
+        for (int q = 0; q < kB; ++q)
+          if (base + q * NT < nw + nm) pend |= 1u << q;
+        while (pend) {
+#pragma unroll
+          for (int q = 0; q < kB; ++q) {
+            if (!((pend >> q) & 1u)) continue;
+            const int e = base + q * NT;
+            if (e < nw) {
+              if constexpr (sizeof(T) == 4) a0[q] = ld_tag1(xw + (size_t)nxt * nw + e);
+              else ld_tag2(xw + ((size_t)nxt * nw + e) * 2, a0[q], a1[q]);
+            } else {
+              a0[q] = ld_tag1(xm + (size_t)nxt * nm + (e - nw));
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < kB; ++q) {
+            if (!((pend >> q) & 1u)) continue;
+            const int e = base + q * NT;
+            bool hit = (uint32_t)(a0[q] >> 32) == want;
+            if constexpr (sizeof(T) == 8) { if (e < nw) hit = hit && (uint32_t)(a1[q] >> 32) == want; }
+            if (!hit) continue;
+            if (e < nw) {
+              T v;
+              if constexpr (sizeof(T) == 4) v = __uint_as_float((uint32_t)a0[q]);
+              else v = __longlong_as_double((long long)(((a1[q] & 0xffffffffull) << 32) | (a0[q] & 0xffffffffull)));
+              Dn[dpos<T, M>(e / M, e % M)] = v;
+            } else {
+              const uint32_t bits = (uint32_t)a0[q];
+              if (bits) atomicMax(red + (size_t)(t % 3) * M * 2 + (e - nw) % (2 * M), bits);
+            }
+            pend &= ~(1u << q);
+          }
+          if (!pend) break;
+          if (!started) {
+            w0c = clock64();
+            started = true;
+          } else if (clock64() - w0c > wait_lim) {
+            bad = true;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      if (__syncthreads_or(bad ? 1 : 0)) {
         if (tid == 0) atomicOr(P.dstatus, kStatTimeout);
         break;
       }
-      // the slot into this CTA's table (read below like the cluster slot)
-      if (tid < 2 * M) red[(size_t)(t % 3) * M * 2 + tid] = ld_relaxed_gpu(tk.xslot + (size_t)(t % 3) * M * 2 + tid);
-      __syncthreads();
     } else if constexpr (kAsync) {
       __syncthreads();
       if (*xfail) {
@@ -717,7 +774,6 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
         if (k == kq) { my_lam = lamv[k]; my_done = done[k]; }
       if (tid < M * 2) {
         red[(size_t)((t + 2) % 3) * M * 2 + tid] = 0u;
-        if (kGrid && rank == 0) tk.xslot[(size_t)((t + 2) % 3) * M * 2 + tid] = 0u;
       }
     }
     ++t;
@@ -810,6 +866,11 @@ size_t oem_iter_rows_smem_fixed(int p, int npen, int max_rows, int precision) {
   const int M = oem_iter_mpad(npen);
   const int tsz = precision == OEM_ITER_F64 ? 8 : 4;
   return iter_smem_layout(p, M, max_rows, tsz, 0).total;
+}
+
+size_t oem_iter_rows_xbuf_bytes(int p, int M, int precision, int C) {
+  const size_t W = precision == OEM_ITER_F64 ? 2 : 1, Mp = (size_t)oem_iter_mpad(M);
+  return ((2 * (size_t)p * Mp * W + 2 * (size_t)C * 2 * Mp) * 8 + 16 + 255) & ~(size_t)255;
 }
 
 size_t oem_iter_rows_smem_per_row(int p, int precision) {

@@ -352,7 +352,6 @@ static int launch_class(oem_server* S, const std::vector<SrvJob*>& jobs, int t0,
   bool groups = false;
   for (SrvJob* J : jobs) { T += J->B; pmax = std::max(pmax, J->p); groups = groups || J->groups; }
   const bool rows = iter_rows_kernel(pmax);
-  const bool wide = !rows && pmax > kIterWideP;
   // cluster size: all clusters resident at once, about 32 rows per CTA
   int C = 1;
   const int byT = std::max(1, ctx->num_sms / std::max(1, T));
@@ -382,7 +381,7 @@ static int launch_class(oem_server* S, const std::vector<SrvJob*>& jobs, int t0,
     for (int u = 0; u < T; ++u) max_rows = std::max(max_rows, tasks[u].max_rows);
     IterLaunch probe{};
     probe.ntasks = T; probe.C = C; probe.M = 1; probe.precision = OEM_ITER_F32; probe.smem = smem;
-    probe.max_rows = max_rows; probe.groups = groups ? 1 : 0; probe.wide = wide ? 1 : 0;
+    probe.max_rows = max_rows; probe.groups = groups ? 1 : 0; probe.wide = 0;
     if (iter_smem_probe(probe, rows) >= 1 || C == 1) {
       t = 0;
       for (SrvJob* J : jobs) {
@@ -419,7 +418,7 @@ static int launch_class(oem_server* S, const std::vector<SrvJob*>& jobs, int t0,
       Lc.smem = smem;
       Lc.max_rows = max_rows;
       Lc.groups = groups ? 1 : 0;
-      Lc.wide = wide ? 1 : 0;
+      Lc.wide = 0;
       Lc.wait_cycles = iter_wait_cycles();
       if (rows) LAUNCH(OEM_PROF_ITER, launch_oem_iter_rows(Lc, s));
       else LAUNCH(OEM_PROF_ITER, launch_oem_iter(Lc, s));
@@ -443,7 +442,7 @@ int run_round(oem_server* S, std::vector<SrvJob*>& ready) {
   }
   // the round's jobs by kernel class, in their order within `ready`
   std::vector<SrvJob*> cls[3];
-  for (SrvJob* J : ready) cls[iter_rows_kernel(J->p) ? 2 : J->p > kIterWideP ? 1 : 0].push_back(J);
+  for (SrvJob* J : ready) cls[iter_rows_kernel(J->p) ? 2 : 0].push_back(J);
   std::vector<SrvJob*> order;
   int t0 = 0;
   for (auto& c : cls) {
