@@ -181,6 +181,16 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
     wlo = bound(warp);
     whi = max(wlo, bound(warp + 1));
   }
+  // the mat-vec and u-update rows: the warp's block above without group
+  // penalties; with them an even split (group-aligned blocks would leave most
+  // warps idle), the group norms and thresholds then on [wlo, whi) after a
+  // block barrier
+  int mlo = wlo, mhi = whi;
+  if (has_group) {
+    const int per = (R + NW - 1) / NW;
+    mlo = min(R, warp * per);
+    mhi = min(R, mlo + per);
+  }
 
   // ---- initialise u, beta, weights, groups, the G rows kept in shared memory
   for (int e = tid; e < M * maxR; e += NT) {
@@ -260,7 +270,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
   // order as from shared memory.
   constexpr int kGS = 4;                          // column steps of 128
   constexpr bool kGregT = kF32 && RG <= 4;        // register budget: RG * kGS float4
-  const bool greg_on = kGregT && (whi - wlo) <= RG && p <= 128 * kGS;
+  const bool greg_on = kGregT && (mhi - mlo) <= RG && p <= 128 * kGS;
   float4 greg[kGregT ? RG : 1][kGregT ? kGS : 1];
   // With one row group per warp and scalar penalties, the lane that owns row
   // wlo + rsub of instance kq keeps u (hi, lo), beta, w and its last dbeta
@@ -284,8 +294,8 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
       for (int sx = 0; sx < kGS; ++sx) {
         float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
         const int j4 = lane * 4 + 128 * sx;
-        if (greg_on && r < whi - wlo && j4 < p) {
-          const int ib = wlo + r;
+        if (greg_on && r < mhi - mlo && j4 < p) {
+          const int ib = mlo + r;
           const float* rowp = reinterpret_cast<const float*>(
               ib < smem_rows ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg);
           g = *reinterpret_cast<const float4*>(rowp + j4);
@@ -305,8 +315,8 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
     T lmd = T(0), lmb = T(0);  // this lane's running max |dbeta|, |beta| (instance kq)
     // ---- 1. per group of RG rows: y = G dbeta for all instances (one pass
     // over dbeta for the group), u update and, without groups, the threshold
-    for (int gb = wlo; gb < whi; gb += RG) {
-      const int nv = min(RG, whi - gb);
+    for (int gb = mlo; gb < mhi; gb += RG) {
+      const int nv = min(RG, mhi - gb);
       T y = T(0);
       if (!skip_mv) {
         T acc[V];
@@ -423,7 +433,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
           st[(size_t)i * M + kq] = dn;
           r_dn = dn;
         }
-      } else if (even && i < whi) {
+      } else if (even && i < mhi) {
         const int idx = kq * maxR + i;
         if (my_inst && !skip_mv) {
           const T incr = fma(my_d, Dc[dpos<T, M>(i0 + i, kq)], -y);
@@ -459,7 +469,8 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
         }
       }
     }
-    __syncwarp();
+    if (has_group) __syncthreads();  // every row's u before the group norms
+    else __syncwarp();
     if (has_group) {
       // ---- 2a. group norms over the warp's rows: ||u_g||, or for the
       // sparse group lasso ||v_g|| with v = S(u, w lambda tau) / d
