@@ -790,6 +790,7 @@ constexpr size_t kIterSmemCap = 227 * 1024;
 // Grams of a cross validation): cluster size, slices, shared memory.
 struct IterPlan {
   int C = 1, M = 1, Mg = 1, max_rows = 0, smem_rows = 0;
+  int ucache = 0;         // row-owned kernel, float32: column-block cache slots
   size_t smem = 0;
   int32_t slice[kMaxCluster + 1] = {0};
   bool grid = false;      // cooperative grid mode (C CTAs per task, any C)
@@ -853,8 +854,17 @@ inline int layout_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, int pre
     const size_t fixed = fixed_of(I.max_rows);
     const size_t per = rows ? oem_iter_rows_smem_per_row((int)p, prec) : oem_iter_smem_per_row((int)p, prec);
     I.smem_rows = I.max_rows;
+    I.ucache = 0;
     I.smem = fixed + (size_t)I.max_rows * per;
     I.C = C;
+    if (rows && prec == OEM_ITER_F32) {
+      // float32 row-owned kernel: every column block of the slice cached
+      I.smem_rows = 0;
+      I.ucache = oem_iter_rows_ucache_slots((int)p, Mg, I.max_rows, prec, kIterSmemCap - 1024);
+      I.smem = oem_iter_rows_smem_ucache((int)p, Mg, I.max_rows, prec, I.ucache);
+      if (I.ucache < oem_iter_rows_blocks((int)p))
+        return fail(ctx, OEM_EUNSUPPORTED, "grid mode: %d rows per CTA do not fit", I.max_rows);
+    }
     if (I.smem + 1024 > kIterSmemCap)
       return fail(ctx, OEM_EUNSUPPORTED, "grid mode: %d rows per CTA do not fit", I.max_rows);
     if (probe_of(C) < 1) return fail(ctx, OEM_EUNSUPPORTED, "grid mode: no CTA fits on an SM");
@@ -873,6 +883,14 @@ inline int layout_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, int pre
     const size_t per = rows ? oem_iter_rows_smem_per_row((int)p, prec) : oem_iter_smem_per_row((int)p, prec);
     I.smem_rows = (int)std::min<size_t>((size_t)I.max_rows, (kIterSmemCap - fixed) / per);
     I.smem = fixed + (size_t)I.smem_rows * per;
+    I.ucache = 0;
+    if (rows && prec == OEM_ITER_F32) {
+      // float32 row-owned kernel: the 16-column blocks of G that nonzero
+      // dbeta entries touch, cached while slots last (the rest read from L2)
+      I.smem_rows = 0;
+      I.ucache = oem_iter_rows_ucache_slots((int)p, Mg, I.max_rows, prec, kIterSmemCap - 1024);
+      I.smem = oem_iter_rows_smem_ucache((int)p, Mg, I.max_rows, prec, I.ucache);
+    }
     I.C = C;
     if (probe_of(C) >= 1) return OEM_OK;
     if (C == 1) return fail(ctx, OEM_ECUDA, "no cluster configuration of the iteration kernel fits");
@@ -917,10 +935,12 @@ inline int plan_iter(oem_ctx* ctx, int64_t p, int B, const PenPlan& P, const oem
   I.gslice_cap = std::max(ctx->num_sms, o->cluster_ctas) + 1;
   if (grid) C = o->cluster_ctas;
   if (o->cluster_ctas <= 0) {
-    // grid mode when a cluster cannot keep all its Gram rows in shared
-    // memory but the whole device can
+    // grid mode when a cluster cannot keep all its Gram rows (float32
+    // row-owned kernel: all column blocks of its slices) in shared memory
+    // but the whole device can
     IterPlan J = I;
-    if (layout_iter(ctx, p, B, P, prec, C, Mg, false, J) == OEM_OK && J.smem_rows < J.max_rows) {
+    if (layout_iter(ctx, p, B, P, prec, C, Mg, false, J) == OEM_OK &&
+        (J.ucache > 0 ? J.ucache < oem_iter_rows_blocks((int)p) : J.smem_rows < J.max_rows)) {
       IterPlan K = I;
       if (layout_iter(ctx, p, B, P, prec, ctx->num_sms, Mg, true, K) == OEM_OK) {
         grid = true;
@@ -963,7 +983,7 @@ inline int launch_iter_layout(oem_ctx* ctx, int64_t p, int B, const float* G32, 
       IterTask& t = tasks[(size_t)b * S + q];
       const int k0 = q * Mg;
       t.p = (int)p; t.npen = std::min(Mg, npen - k0); t.L = L; t.ldg = ldg;
-      t.max_rows = I.max_rows; t.smem_rows = I.smem_rows; t.resume = 0;
+      t.max_rows = I.max_rows; t.smem_rows = I.smem_rows; t.ucache = I.ucache; t.resume = 0;
       for (int r = 0; r <= kMaxCluster; ++r) t.slice[r] = r <= I.C ? I.slice[r] : (int32_t)p;
       t.G32 = G32 ? G32 + (size_t)b * p * ldg : nullptr;
       t.G64 = G64 ? G64 + (size_t)b * p * p : nullptr;

@@ -313,6 +313,8 @@ struct IterTask {
   int32_t p, npen, L, ldg;
   int32_t max_rows;      // longest CTA slice
   int32_t smem_rows;     // leading rows of each slice kept in shared memory
+  int32_t ucache;        // row-owned kernel, float32: column-block cache slots
+                         // (resident rows unused: smem_rows = 0)
   int32_t resume;        // 1: start from st_* instead of beta = 0, u = c
   int32_t slice[kMaxCluster + 1];  // CTA r owns rows [slice[r], slice[r+1])
   const float* G32;      // [p][ldg] (float32 iteration)
@@ -380,6 +382,12 @@ size_t oem_iter_xbuf_bytes(int p, int M, int precision);
 // words in the exchange buffer, which needs oem_iter_rows_xbuf_bytes).
 size_t oem_iter_rows_xbuf_bytes(int p, int M, int precision, int C);
 size_t oem_iter_rows_smem_fixed(int p, int npen, int max_rows, int precision);
+// Column-block cache of the row-owned kernel (float32): the most slots
+// (16 columns of every row of a slice each) whose shared memory stays within
+// cap (0 when none fit).
+int oem_iter_rows_ucache_slots(int p, int npen, int max_rows, int precision, size_t cap);
+int oem_iter_rows_blocks(int p);  // 16-column blocks of order p (one cache slot each)
+size_t oem_iter_rows_smem_ucache(int p, int npen, int max_rows, int precision, int slots);
 size_t oem_iter_rows_smem_per_row(int p, int precision);
 int oem_iter_rows_max_cluster(const IterLaunch& P);
 cudaError_t launch_oem_iter_rows(const IterLaunch& P, cudaStream_t s);

@@ -63,21 +63,39 @@ template <typename T, int M>
 constexpr int iter_threads() { return 256; }
 
 // Shared-memory carve-up (byte offsets, 16-byte aligned). The dbeta buffers
-// have ldgs = round_up(p, 4) rows; rows p.. stay zero.
+// have ldd rows (iter_ldd); rows p.. stay zero. Float64: the Gram
+// region holds the first smem_rows rows of the CTA's slice of G. Float32:
+// it holds the column-block cache: ucache slots, each one block of 16
+// columns (four 16-byte units) of every row of the slice ([slot][unit][row]);
+// nzl[b] lists the column blocks of dbeta buffer b that hold a nonzero value
+// of some instance, in increasing order (entry: the block, and its slot's
+// offset in float4 | state << 30, state 0 cached, 1 to be filled by the
+// mat-vec that reads it, 2 without a slot), nzc[b] their count; cbit[s] has bit l set when block
+// 32 s + l has been given a slot (or refused one); smap[k] is block k's slot
+// (-1: none).
 struct IterSmem {
-  size_t dbuf, uhi, ulo, beta, w, gn, cgr, glen, st, lred, red, xbar, xslot, xred, gs, total;
+  size_t dbuf, uhi, ulo, beta, w, cgr, glen, st, lred, red, xbar, xslot, xred, nzc, nzl, cbit, smap, gs, total;
 };
 constexpr int kIterMaxWarps = 16;
-__host__ __device__ inline IterSmem iter_smem_layout(int p, int M, int maxR, int tsz, int smem_rows) {
-  const int ldgs = (p + 3) & ~3;
+__host__ __device__ inline int iter_units(int p) { return (p + 3) >> 2; }     // 4 columns
+__host__ __device__ inline int iter_blocks(int p) { return (p + 15) >> 4; }    // 16 columns
+__host__ __device__ inline int iter_block_words(int p) { return (iter_blocks(p) + 31) >> 5; }
+__host__ __device__ inline int iter_list_len(int p) { return (iter_blocks(p) + 3) & ~3; }
+constexpr int kMaxBlockSlots = 32767;  // slot + 1 takes 15 bits of a list entry
+// Rows of a dbeta buffer: float32 whole 16-column blocks, float64 4 rows.
+__host__ __device__ inline int iter_ldd(int p, int tsz) { return tsz == 4 ? (p + 15) & ~15 : (p + 3) & ~3; }
+__host__ __device__ inline IterSmem iter_smem_layout(int p, int M, int maxR, int tsz, int smem_rows,
+                                                     int ucache = 0) {
+  const int ldgs = (p + 3) & ~3, ldd = iter_ldd(p, tsz);
+  const int nbk = iter_blocks(p), nwd = iter_block_words(p);
+  const bool f32 = tsz == 4;
   IterSmem L;
   size_t o = 0;
-  L.dbuf = o;  o = al16(o + (size_t)2 * ldgs * M * tsz);
+  L.dbuf = o;  o = al16(o + (size_t)2 * ldd * M * tsz);
   L.uhi = o;   o = al16(o + (size_t)M * maxR * tsz);
   L.ulo = o;   o = al16(o + (size_t)M * maxR * tsz);
   L.beta = o;  o = al16(o + (size_t)M * maxR * tsz);
   L.w = o;     o = al16(o + (size_t)M * maxR * tsz);
-  L.gn = o;    o = al16(o + (size_t)M * maxR * tsz);
   L.cgr = o;   o = al16(o + (size_t)M * maxR * tsz);
   L.glen = o;  o = al16(o + (size_t)M * maxR * 4);
   L.st = o;    o = al16(o + (size_t)maxR * M * tsz);
@@ -86,7 +104,12 @@ __host__ __device__ inline IterSmem iter_smem_layout(int p, int M, int maxR, int
   L.xbar = o;  o = al16(o + 2 * 8);
   L.xslot = o; o = al16(o + (size_t)2 * 16 * M * 2 * 4);
   L.xred = o;  o = al16(o + (size_t)(M * 2 + 1) * 4);
-  L.gs = o;    o = al16(o + (size_t)smem_rows * ldgs * tsz);
+  L.nzc = o;   o = al16(o + (f32 ? (size_t)2 * 4 : 0));
+  L.nzl = o;   o = al16(o + (f32 ? (size_t)2 * iter_list_len(p) * 8 : 0));
+  L.cbit = o;  o = al16(o + (f32 ? (size_t)nwd * 4 : 0));
+  L.smap = o;  o = al16(o + (f32 ? (size_t)nbk * 2 : 0));
+  L.gs = o;
+  o = al16(o + (f32 ? (size_t)ucache * maxR * 64 : (size_t)smem_rows * ldgs * tsz));
   L.total = o;
   return L;
 }
@@ -111,23 +134,31 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
   unsigned bar_gen = 0;
   const long long wait_lim = P.wait_cycles > 0 ? P.wait_cycles : 4000000000LL;
   const int ldgs = (p + 3) & ~3, smem_rows = tk.smem_rows;
+  const int ldd = iter_ldd(p, (int)sizeof(T));  // rows of a dbeta buffer
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr bool kF32 = sizeof(T) == 4;
 
   extern __shared__ __align__(16) unsigned char smem[];
-  const IterSmem Ls = iter_smem_layout(p, M, maxR, (int)sizeof(T), tk.smem_rows);
+  const int ucs = kF32 ? tk.ucache : 0;  // column-unit cache slots
+  const IterSmem Ls = iter_smem_layout(p, M, maxR, (int)sizeof(T), tk.smem_rows, ucs);
   T* Dbuf = reinterpret_cast<T*>(smem + Ls.dbuf);
   T* uhi = reinterpret_cast<T*>(smem + Ls.uhi);
   T* ulo = reinterpret_cast<T*>(smem + Ls.ulo);
   T* bet = reinterpret_cast<T*>(smem + Ls.beta);
   T* wv = reinterpret_cast<T*>(smem + Ls.w);
-  T* gn = reinterpret_cast<T*>(smem + Ls.gn);
   T* cgr = reinterpret_cast<T*>(smem + Ls.cgr);
   int* glen = reinterpret_cast<int*>(smem + Ls.glen);
   T* st = reinterpret_cast<T*>(smem + Ls.st);
   float* lred = reinterpret_cast<float*>(smem + Ls.lred);  // [warp][2M] block table
   unsigned int* red = reinterpret_cast<unsigned int*>(smem + Ls.red);  // [3][2M] slots
   T* Gs = reinterpret_cast<T*>(smem + Ls.gs);
+  const int nwd = iter_block_words(p);  // words of the block bitmaps
+  const int nll = iter_list_len(p);
+  int* nzc = reinterpret_cast<int*>(smem + Ls.nzc);              // [2]
+  uint2* nzl = reinterpret_cast<uint2*>(smem + Ls.nzl);          // [2][nll]
+  unsigned* cbit = reinterpret_cast<unsigned*>(smem + Ls.cbit);  // [nwd]
+  short* smap = reinterpret_cast<short*>(smem + Ls.smap);        // [blocks]
+  float4* ucache = reinterpret_cast<float4*>(smem + Ls.gs);      // [ucs][4][maxR]
   constexpr bool kAsync = kF32 && !kGrid;
   const uint32_t xbar0 = xs_u32(smem + Ls.xbar);  // mbarriers of dbeta buffers 0 / 1
   unsigned int* xslot = reinterpret_cast<unsigned int*>(smem + Ls.xslot);  // [2][C][2M]
@@ -181,12 +212,12 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
     wlo = bound(warp);
     whi = max(wlo, bound(warp + 1));
   }
-  // the mat-vec and u-update rows: the warp's block above without group
-  // penalties; with them an even split (group-aligned blocks would leave most
-  // warps idle), the group norms and thresholds then on [wlo, whi) after a
-  // block barrier
+  // the mat-vec and u-update rows: float32 (one row per lane) and float64
+  // without group penalties the warp's block above; float64 with them an
+  // even split (group-aligned blocks would leave most warps idle), the group
+  // norms and thresholds then on [wlo, whi) after a block barrier
   int mlo = wlo, mhi = whi;
-  if (has_group) {
+  if (!kF32 && has_group) {
     const int per = (R + NW - 1) / NW;
     mlo = min(R, warp * per);
     mhi = min(R, mlo + per);
@@ -221,9 +252,10 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
         }
       }
     }
-    uhi[e] = hi; ulo[e] = lo; bet[e] = b0; wv[e] = wt; cgr[e] = cgv; glen[e] = gl; gn[e] = T(0);
+    uhi[e] = hi; ulo[e] = lo; bet[e] = b0; wv[e] = wt; cgr[e] = cgv; glen[e] = gl;
   }
-  for (int e = tid; e < 2 * ldgs * M; e += NT) Dbuf[e] = T(0);
+  for (int e = tid; e < 2 * ldd * M; e += NT) Dbuf[e] = T(0);
+  for (int e = tid; e < maxR * M; e += NT) st[e] = T(0);  // padded instances keep dbeta = 0
   for (int e = tid; e < 3 * M * 2; e += NT) red[e] = 0u;
   if (kAsync && tid == 0) {
     xs_init(xbar0);
@@ -231,9 +263,15 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
     *xfail = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int e = tid; e < smem_rows * ldgs; e += NT) {
-    const int i = e / ldgs, j = e % ldgs;
-    Gs[e] = (i < R && j < p) ? Gglob[(size_t)(i0 + i) * ldgg + j] : T(0);
+  if constexpr (kF32) {
+    for (int e = tid; e < iter_blocks(p); e += NT) smap[e] = -1;
+    for (int e = tid; e < nwd; e += NT) cbit[e] = 0u;
+    if (tid < 2) nzc[tid] = 0;
+  } else {
+    for (int e = tid; e < smem_rows * ldgs; e += NT) {
+      const int i = e / ldgs, j = e % ldgs;
+      Gs[e] = (i < R && j < p) ? Gglob[(size_t)(i0 + i) * ldgg + j] : T(0);
+    }
   }
   if constexpr (kGrid) {
     if (!group_barrier(xbarg, (unsigned)C, bar_gen, wait_lim)) {
@@ -264,45 +302,138 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
   const bool my_inst = kq < m;
 
   const T tol = (T)P.tol;
-  // Float32 with one row group per warp and p <= 512: the warp's G rows live
-  // in registers (lane l holds columns 4l .. 4l+3 + 128 s of each row), so the
-  // mat-vec reads only dbeta from shared memory. Same products in the same
-  // order as from shared memory.
-  constexpr int kGS = 4;                          // column steps of 128
-  constexpr bool kGregT = kF32 && RG <= 4;        // register budget: RG * kGS float4
-  const bool greg_on = kGregT && (mhi - mlo) <= RG && p <= 128 * kGS;
-  float4 greg[kGregT ? RG : 1][kGregT ? kGS : 1];
-  // With one row group per warp and scalar penalties, the lane that owns row
-  // wlo + rsub of instance kq keeps u (hi, lo), beta, w and its last dbeta
-  // in registers for the whole launch (beta is still stored for the outputs,
-  // u written back at the end); the same values as in shared memory.
-  const bool regst = kF32 && greg_on && !has_group;
-  const int i_own = wlo + rsub;
-  const bool own = even && i_own < whi;
-  T r_uhi = T(0), r_ulo = T(0), r_bet = T(0), r_w = T(1), r_dn = T(0);
-  if (regst && own) {
-    const int idx = kq * maxR + i_own;
-    r_uhi = uhi[idx];
-    r_ulo = ulo[idx];
-    r_bet = bet[idx];
-    r_w = wv[idx];
-  }
-  if constexpr (kGregT) {
+  // Float32 mat-vec of local rows [r0, r0 + 32) (lane = row i = r0 + lane,
+  // active when in): y_i = (G dbeta)_i for every instance over the 16-column
+  // blocks whose dbeta has a nonzero value (the list of buffer Db), in
+  // increasing column order, one accumulator per column within each 4-column
+  // unit; the caller adds (a0 + a1) + (a2 + a3). A zero unit adds exact
+  // zeros (fma(g, 0, a) = a for finite g), so the sums are those of every
+  // nonzero unit in increasing order, whatever the layout. G from the
+  // block's cache slot, filled from L2 by the first mat-vec that needs it;
+  // blocks without a slot are read from L2 each time.
+  const int nu_all = iter_units(p);
+  auto rows_matvec = [&](int r0, bool in, const T* Db, int b, float (&a)[M][4]) {
+    const int i = r0 + lane;
+    const int ii = in ? i : r0;  // a lane past the slice reads a valid row, unused
+    const float* grow = reinterpret_cast<const float*>(Gglob) + (size_t)(i0 + ii) * ldgg;
+    const float* Dbf = reinterpret_cast<const float*>(Db);
+    const uint2* lst = nzl + (size_t)b * nll;
+    const int cnt = nzc[b];
+    // dbeta of block kb: units 4 kb + j, instances q
+    auto load_dv = [&](int kb, float (&dv)[4][4][M]) {
 #pragma unroll
-    for (int r = 0; r < RG; ++r)
+      for (int j = 0; j < 4; ++j)
 #pragma unroll
-      for (int sx = 0; sx < kGS; ++sx) {
-        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int j4 = lane * 4 + 128 * sx;
-        if (greg_on && r < mhi - mlo && j4 < p) {
-          const int ib = mlo + r;
-          const float* rowp = reinterpret_cast<const float*>(
-              ib < smem_rows ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg);
-          g = *reinterpret_cast<const float4*>(rowp + j4);
+        for (int q = 0; q < M; ++q) {
+          const int uu = (4 * kb + j) * M + q;
+          const float4 tq = *reinterpret_cast<const float4*>(Dbf + ((uu ^ ((uu >> 3) & (M - 1))) << 2));
+          const float tv[4] = {tq.x, tq.y, tq.z, tq.w};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) dv[j][(q * 4 + c) / M][(q * 4 + c) % M] = tv[c];
         }
-        greg[r][sx] = g;
+    };
+    auto fma_block = [&](const float4 (&g)[4], const float (&dv)[4][4][M]) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float gv[4] = {g[j].x, g[j].y, g[j].z, g[j].w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int k = 0; k < M; ++k) a[k][c] = fma(gv[c], dv[j][c][k], a[k][c]);
       }
-  }
+    };
+    // any entry: cached, to be filled from L2 (units past p give zeros), or
+    // without a slot (read from L2)
+    auto block_any = [&](uint2 e) {
+      const int kb = (int)e.x;
+      const unsigned st2 = e.y >> 30, off = e.y & 0x3FFFFFFFu;
+      float dv[4][4][M];
+      load_dv(kb, dv);
+      float4 g[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int u = 4 * kb + j;
+        float4* cp = ucache + off + (size_t)j * maxR + ii;
+        if (st2 == 0u) {
+          g[j] = *cp;
+        } else {
+          g[j] = u < nu_all ? *reinterpret_cast<const float4*>(grow + 4 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+          if (st2 == 1u && in) *cp = g[j];
+        }
+      }
+      fma_block(g, dv);
+    };
+    constexpr int UB = M <= 2 ? 2 : 1;  // cached blocks whose loads are in flight together
+    int q = 0;
+    if constexpr (UB == 2) {
+      for (; q + 2 <= cnt; q += 2) {
+        const uint4 e2 = *reinterpret_cast<const uint4*>(lst + q);
+        if (((e2.y | e2.w) >> 30) == 0u) {
+          float dv[2][4][4][M];
+          float4 g[2][4];
+          load_dv((int)e2.x, dv[0]);
+          load_dv((int)e2.z, dv[1]);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            g[0][j] = ucache[e2.y + (size_t)j * maxR + ii];
+            g[1][j] = ucache[e2.w + (size_t)j * maxR + ii];
+          }
+          fma_block(g[0], dv[0]);
+          fma_block(g[1], dv[1]);
+        } else {
+          block_any(make_uint2(e2.x, e2.y));
+          block_any(make_uint2(e2.z, e2.w));
+        }
+      }
+    }
+    for (; q < cnt; ++q) block_any(lst[q]);
+  };
+  // Float32, warp 0: the list of 16-column blocks of dbeta buffer b with a
+  // nonzero value (every CTA's rows have arrived), giving a cache slot to
+  // each block that is nonzero for the first time (in block order, while
+  // slots last; its entry is marked to be filled by the mat-vec that reads
+  // it).
+  int nslot = 0;  // slots given (uniform in warp 0)
+  auto build_list = [&](int b) {
+    const float* Db = reinterpret_cast<const float*>(Dbuf) + (size_t)b * ldd * M;
+    const int nbk = iter_blocks(p);
+    uint2* lst = nzl + (size_t)b * nll;
+    int base = 0;
+    for (int sw = 0; sw < nwd; ++sw) {
+      const int kb = 32 * sw + lane;
+      uint32_t o = 0u;
+      int slv = -1;
+      if (kb < nbk) {
+        // whole blocks: buffer rows past p are zero
+#pragma unroll
+        for (int j = 0; j < 4 * M; ++j) {
+          const int uu = 4 * kb * M + j;
+          const float4 v = *reinterpret_cast<const float4*>(Db + ((uu ^ ((uu >> 3) & (M - 1))) << 2));
+          o |= __float_as_uint(v.x) | __float_as_uint(v.y) | __float_as_uint(v.z) | __float_as_uint(v.w);
+        }
+        slv = smap[kb];
+      }
+      const unsigned cb = cbit[sw];
+      const unsigned bits = __ballot_sync(0xffffffffu, (o & 0x7fffffffu) != 0u);
+      const unsigned nb = bits & ~cb;
+      unsigned state = slv >= 0 ? 0u : 2u;
+      if (nb) {  // blocks nonzero for the first time
+        const int sl = nslot + __popc(nb & ((1u << lane) - 1u));
+        if (((nb >> lane) & 1u) && sl < ucs) {
+          smap[kb] = (short)sl;
+          slv = sl;
+          state = 1u;
+        }
+        nslot = min(ucs, nslot + __popc(nb));
+        if (lane == 0) cbit[sw] = cb | nb;
+      }
+      if ((bits >> lane) & 1u)
+        lst[base + __popc(bits & ((1u << lane) - 1u))] =
+            make_uint2((unsigned)kb, (unsigned)(slv >= 0 ? slv * 4 * maxR : 0) | (state << 30));
+      base += __popc(bits);
+    }
+    if (lane == 0) nzc[b] = base;
+  };
   int skip_mv = 1;      // dbeta of the previous iteration is all zero
   int all_done = 1;
   for (int k = 0; k < m; ++k) all_done &= done[k];
@@ -310,84 +441,81 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
   int t = 0;
   while (!all_done) {
     const int cur = t & 1, nxt = cur ^ 1;
-    const T* Dc = Dbuf + (size_t)cur * ldgs * M;
+    const T* Dc = Dbuf + (size_t)cur * ldd * M;
     const int nr = whi - wlo;
-    T lmd = T(0), lmb = T(0);  // this lane's running max |dbeta|, |beta| (instance kq)
-    // ---- 1. per group of RG rows: y = G dbeta for all instances (one pass
-    // over dbeta for the group), u update and, without groups, the threshold
-    for (int gb = mlo; gb < mhi; gb += RG) {
-      const int nv = min(RG, mhi - gb);
-      T y = T(0);
-      if (!skip_mv) {
-        T acc[V];
+    T lmd = T(0), lmb = T(0);  // float64: this lane's running max |dbeta|, |beta| (instance kq)
+    T mx_d[M], mx_b[M];        // float32 (and group steps): per instance, this lane's rows
 #pragma unroll
-        for (int q = 0; q < V; ++q) acc[q] = T(0);
-        const T* gr[RG];
+    for (int k = 0; k < M; ++k) { mx_d[k] = T(0); mx_b[k] = T(0); }
+    if constexpr (kF32) {
+      // ---- 1. one row per lane, rows [wlo, whi) in chunks of 32: y = G dbeta
+      // for every instance, the u update and, without groups, the threshold
+      for (int r0 = wlo; r0 < whi; r0 += 32) {
+        const int i = r0 + lane;
+        const bool in = i < whi;
+        float a[M][4];
 #pragma unroll
-        for (int r = 0; r < RG; ++r) {
-          const int ib = gb + min(r, nv - 1);
-          gr[r] = ib < smem_rows ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
-        }
-        if constexpr (kF32) {
-          // lane l takes columns 4l .. 4l+3, then + 128: one float4 of each
-          // G row and M float4 units of dbeta per step (rows are zero-padded
-          // to ldgs, a multiple of 4). Rows resident in shared memory are
-          // addressed from Gs (shared loads), the others through gr.
-          const float* g0 = Gs + (size_t)gb * ldgs;
-          auto matvec = [&](auto row) {
-            for (int j4 = lane * 4; j4 < p; j4 += 128) {
-              float dv[4][M];
+        for (int k = 0; k < M; ++k)
 #pragma unroll
-              for (int q = 0; q < M; ++q) {
-                const int u = (j4 * M >> 2) + q;
-                const float4 t = *reinterpret_cast<const float4*>(Dc + ((u ^ ((u >> 3) & (M - 1))) << 2));
-                const float tv[4] = {t.x, t.y, t.z, t.w};
+          for (int c = 0; c < 4; ++c) a[k][c] = 0.f;
+        if (!skip_mv) rows_matvec(r0, in, Dc, cur, a);
+        if (in) {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) dv[(q * 4 + e) / M][(q * 4 + e) % M] = tv[e];
-              }
-#pragma unroll
-              for (int r = 0; r < RG; ++r) {
-                float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (r < nv) g4 = *reinterpret_cast<const float4*>(row(r) + j4);
-                const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-#pragma unroll
-                  for (int k = 0; k < M; ++k) acc[r * M + k] = fma(gv[c], dv[c][k], acc[r * M + k]);
+          for (int k = 0; k < M; ++k) {
+            if (k >= m) {
+              st[(size_t)i * M + k] = T(0);
+              continue;
+            }
+            const int idx = k * maxR + i;
+            if (!skip_mv) {
+              const T y = (a[k][0] + a[k][1]) + (a[k][2] + a[k][3]);
+              const T incr = fma(dk[k], Dc[dpos<T, M>(i0 + i, k)], -y);
+              // an instance whose dbeta was zero (y == 0 exactly) keeps its
+              // u bit for bit, however the instances are grouped into tasks
+              if (incr != T(0)) {
+                const T h = uhi[idx];
+                const T s1 = h + incr, bb = s1 - h;
+                const T e = (h - (s1 - bb)) + (incr - bb);
+                const T lo = ulo[idx] + e;
+                const T hi2 = s1 + lo;
+                ulo[idx] = lo - (hi2 - s1);
+                uhi[idx] = hi2;
               }
             }
-          };
-          if (kGregT && greg_on) {
-#pragma unroll
-            for (int sx = 0; sx < kGS; ++sx) {
-              const int j4 = lane * 4 + 128 * sx;
-              if (j4 < p) {
-                float dv[4][M];
-#pragma unroll
-                for (int q = 0; q < M; ++q) {
-                  const int u = (j4 * M >> 2) + q;
-                  const float4 t = *reinterpret_cast<const float4*>(Dc + ((u ^ ((u >> 3) & (M - 1))) << 2));
-                  const float tv[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-                  for (int e = 0; e < 4; ++e) dv[(q * 4 + e) / M][(q * 4 + e) % M] = tv[e];
-                }
-#pragma unroll
-                for (int r = 0; r < RG; ++r) {
-                  const float4 g4 = greg[kGregT ? r : 0][kGregT ? sx : 0];
-                  const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
-#pragma unroll
-                  for (int c = 0; c < 4; ++c)
-#pragma unroll
-                    for (int k = 0; k < M; ++k) acc[r * M + k] = fma(gv[c], dv[c][k], acc[r * M + k]);
-                }
+            if (!has_group) {
+              T dn = T(0);
+              if (!done[k]) {
+                const T bn = thr_scalar<T>(kind[k], uhi[idx], wv[idx] * lamv[k], alpha[k], gamma[k], dk[k]);
+                dn = bn - bet[idx];
+                bet[idx] = bn;
+                mx_d[k] = fmax(mx_d[k], fabs(dn));
+                mx_b[k] = fmax(mx_b[k], fabs(bn));
+              } else {
+                mx_b[k] = fmax(mx_b[k], fabs(bet[idx]));
               }
+              st[(size_t)i * M + k] = dn;
             }
-          } else if (gb + nv <= smem_rows) {
-            matvec([&](int r) { return g0 + (size_t)r * ldgs; });
-          } else {
-            matvec([&](int r) { return gr[r]; });
           }
-        } else {
+        }
+      }
+      __syncwarp();  // the group steps read u of the warp's own rows
+    } else {
+      // ---- 1. float64, per group of RG rows: y = G dbeta for all instances
+      // (one pass over dbeta for the group; lane l takes columns l, l + 32,
+      // ...; one reduce-scatter), u update and, without groups, the threshold
+      for (int gb = mlo; gb < mhi; gb += RG) {
+        const int nv = min(RG, mhi - gb);
+        T y = T(0);
+        if (!skip_mv) {
+          T acc[V];
+#pragma unroll
+          for (int q = 0; q < V; ++q) acc[q] = T(0);
+          const T* gr[RG];
+#pragma unroll
+          for (int r = 0; r < RG; ++r) {
+            const int ib = gb + min(r, nv - 1);
+            gr[r] = ib < smem_rows ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
+          }
 #pragma unroll 4
           for (int j = lane; j < p; j += 32) {
             T dv[M];
@@ -399,155 +527,142 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
               for (int k = 0; k < M; ++k) acc[r * M + k] = fma(g, dv[k], acc[r * M + k]);
             }
           }
+          y = reduce_scatter<V>(acc, lane);
         }
-        y = reduce_scatter<V>(acc, lane);
-      }
-      const int i = gb + rsub;  // this lane's row (local index)
-      if (regst) {
-        if (own) {
+        const int i = gb + rsub;  // this lane's row (local index)
+        if (even && i < mhi) {
+          const int idx = kq * maxR + i;
           if (my_inst && !skip_mv) {
-            const T incr = fma(my_d, r_dn, -y);
-            if (incr != T(0)) {
-              const T h = r_uhi;
-              const T s1 = h + incr, bb = s1 - h;
-              const T e = (h - (s1 - bb)) + (incr - bb);
-              const T lo = r_ulo + e;
-              const T hi2 = s1 + lo;
-              r_ulo = lo - (hi2 - s1);
-              r_uhi = hi2;
-            }
+            const T incr = fma(my_d, Dc[dpos<T, M>(i0 + i, kq)], -y);
+            if (incr != T(0)) uhi[idx] += incr;
           }
-          T dn = T(0);
-          if (my_inst) {
-            if (!my_done) {
-              const T bn = thr_scalar<T>(my_kind, r_uhi, r_w * my_lam, my_alpha, my_gamma, my_d);
-              dn = bn - r_bet;
-              r_bet = bn;
-              bet[kq * maxR + i] = bn;
-              lmd = fmax(lmd, fabs(dn));
-              lmb = fmax(lmb, fabs(bn));
-            } else {
-              lmb = fmax(lmb, fabs(r_bet));
-            }
-          }
-          st[(size_t)i * M + kq] = dn;
-          r_dn = dn;
-        }
-      } else if (even && i < mhi) {
-        const int idx = kq * maxR + i;
-        if (my_inst && !skip_mv) {
-          const T incr = fma(my_d, Dc[dpos<T, M>(i0 + i, kq)], -y);
-          // an instance whose dbeta was zero (y == 0 exactly) keeps its u
-          // bit for bit, however the instances are grouped into tasks
-          if (incr == T(0)) {
-          } else if (kF32) {
-            const T h = uhi[idx];
-            const T s1 = h + incr, bb = s1 - h;
-            const T e = (h - (s1 - bb)) + (incr - bb);
-            const T lo = ulo[idx] + e;
-            const T hi2 = s1 + lo;
-            ulo[idx] = lo - (hi2 - s1);
-            uhi[idx] = hi2;
-          } else {
-            uhi[idx] += incr;
-          }
-        }
-        if (!has_group) {
-          T dn = T(0);
-          if (my_inst) {
-            if (!my_done) {
-              const T bn = thr_scalar<T>(my_kind, uhi[idx], wv[idx] * my_lam, my_alpha, my_gamma, my_d);
-              dn = bn - bet[idx];
-              bet[idx] = bn;
-              lmd = fmax(lmd, fabs(dn));
-              lmb = fmax(lmb, fabs(bn));
-            } else {
-              lmb = fmax(lmb, fabs(bet[idx]));
-            }
-          }
-          st[(size_t)i * M + kq] = dn;
-        }
-      }
-    }
-    if (has_group) __syncthreads();  // every row's u before the group norms
-    else __syncwarp();
-    if (has_group) {
-      // ---- 2a. group norms over the warp's rows: ||u_g||, or for the
-      // sparse group lasso ||v_g|| with v = S(u, w lambda tau) / d
-      for (int e = lane; e < M * nr; e += 32) {
-        const int k = e / nr, i = wlo + e % nr;
-        const int idx = k * maxR + i;
-        const int len = glen[idx];
-        if (len > 0) {
-          int kd = OEM_LASSO;
-          T lt = T(0), dd = T(1);
-#pragma unroll
-          for (int kk = 0; kk < M; ++kk)
-            if (kk == k) { kd = kind[kk]; lt = lamv[kk] * alpha[kk]; dd = dk[kk]; }
-          T s2 = T(0);
-          if (kd == OEM_SPARSE_GROUP_LASSO) {
-            for (int q = 0; q < len; ++q) {
-              const T v = fmax(fabs(uhi[idx + q]) - wv[idx + q] * lt, T(0)) / dd;
-              s2 = fma(v, v, s2);
-            }
-          } else {
-            for (int q = 0; q < len; ++q) s2 = fma(uhi[idx + q], uhi[idx + q], s2);
-          }
-          s2 = sqrt(s2);
-          for (int q = 0; q < len; ++q) gn[idx + q] = s2;
-        }
-      }
-      __syncwarp();
-      // ---- 2b. thresholds and the new dbeta (rows of this warp)
-      T mx_d[M], mx_b[M];
-#pragma unroll
-      for (int k = 0; k < M; ++k) { mx_d[k] = T(0); mx_b[k] = T(0); }
-      for (int e = lane; e < M * nr; e += 32) {
-        const int k = e / nr, i = wlo + e % nr;
-        const int idx = k * maxR + i;
-        T dn = T(0);
-#pragma unroll
-        for (int kk = 0; kk < M; ++kk) {
-          if (kk == k && kk < m) {
-            if (!done[kk]) {
-              const T u = uhi[idx];
-              T bn;
-              if (kind[kk] == OEM_GROUP_LASSO) {
-                const T nrm = gn[idx];
-                const T f = nrm > T(0) ? T(1) - cgr[idx] * lamv[kk] / nrm : T(0);
-                bn = f > T(0) ? u / dk[kk] * f : T(0);
-              } else if (kind[kk] == OEM_GROUP_MCP || kind[kk] == OEM_GROUP_SCAD) {
-                // Eqs. gmcp / gscad: the scalar rule on the norm, u's direction
-                const T nrm = gn[idx];
-                const T bnorm = nrm > T(0) ? thr_scalar<T>(kind[kk] == OEM_GROUP_MCP ? OEM_MCP : OEM_SCAD, nrm,
-                                                           cgr[idx] * lamv[kk], alpha[kk], gamma[kk], dk[kk])
-                                           : T(0);
-                bn = nrm > T(0) ? u * (bnorm / nrm) : T(0);
-              } else if (kind[kk] == OEM_SPARSE_GROUP_LASSO) {
-                // Eq. sglasso (reading: the group step shrinks v by
-                // c_k lambda (1 - tau) / d)
-                const T nrm = gn[idx];
-                const T v = copysign(fmax(fabs(u) - wv[idx] * lamv[kk] * alpha[kk], T(0)) / dk[kk], u);
-                const T f = nrm > T(0) ? T(1) - cgr[idx] * lamv[kk] * (T(1) - alpha[kk]) / (dk[kk] * nrm) : T(0);
-                bn = f > T(0) ? v * f : T(0);
+          if (!has_group) {
+            T dn = T(0);
+            if (my_inst) {
+              if (!my_done) {
+                const T bn = thr_scalar<T>(my_kind, uhi[idx], wv[idx] * my_lam, my_alpha, my_gamma, my_d);
+                dn = bn - bet[idx];
+                bet[idx] = bn;
+                lmd = fmax(lmd, fabs(dn));
+                lmb = fmax(lmb, fabs(bn));
               } else {
-                bn = thr_scalar<T>(kind[kk], u, wv[idx] * lamv[kk], alpha[kk], gamma[kk], dk[kk]);
+                lmb = fmax(lmb, fabs(bet[idx]));
               }
-              dn = bn - bet[idx];
-              bet[idx] = bn;
-              mx_d[kk] = fmax(mx_d[kk], fabs(dn));
-              mx_b[kk] = fmax(mx_b[kk], fabs(bn));
-            } else {
-              mx_b[kk] = fmax(mx_b[kk], fabs(bet[idx]));
             }
+            st[(size_t)i * M + kq] = dn;
           }
         }
-        st[(size_t)i * M + k] = dn;
       }
+      if (has_group) __syncthreads();  // every row's u before the group norms
+      else __syncwarp();
+    }
+    if (has_group) {
+      // ---- 2. thresholds of the warp's rows [wlo, whi) (group-aligned):
+      // per group instance, windows of 32 rows that start at a group start
+      // and hold whole groups; ||u_g|| (or ||v_g||, v = S(u, w lambda tau) / d,
+      // for the sparse group lasso) by a segmented scan over each group's
+      // lanes, whose summation tree depends on the group's length only, so
+      // every layout gives the same bits. A group longer than 32 rows is
+      // summed in row order by one lane.
 #pragma unroll
       for (int k = 0; k < M; ++k) {
-        const T a1 = warp_max(mx_d[k]), a2 = warp_max(mx_b[k]);
-        if (k == kq) { lmd = a1; lmb = a2; }
+        if (k >= m) continue;
+        const int kd = kind[k], dnk = done[k];
+        const T lamk = lamv[k], alk = alpha[k], gak = gamma[k], dkk = dk[k];
+        auto record = [&](int idx, int i, T bn) {
+          const T dn = bn - bet[idx];
+          bet[idx] = bn;
+          mx_d[k] = fmax(mx_d[k], fabs(dn));
+          mx_b[k] = fmax(mx_b[k], fabs(bn));
+          st[(size_t)i * M + k] = dn;
+        };
+        auto keep = [&](int idx, int i) {
+          mx_b[k] = fmax(mx_b[k], fabs(bet[idx]));
+          st[(size_t)i * M + k] = T(0);
+        };
+        if (kd < OEM_GROUP_LASSO) {  // a scalar instance of a group task
+          for (int i = wlo + lane; i < whi; i += 32) {
+            const int idx = k * maxR + i;
+            if (dnk) keep(idx, i);
+            else record(idx, i, thr_scalar<T>(kd, uhi[idx], wv[idx] * lamk, alk, gak, dkk));
+          }
+          continue;
+        }
+        // Section 2.2, Eqs. glasso, gmcp, gscad, sglasso
+        auto group_step = [&](int idx, int i, T u, T nrm) {
+          if (dnk) { keep(idx, i); return; }
+          const T cgv = cgr[idx];
+          T bn;
+          if (kd == OEM_GROUP_LASSO) {
+            const T f = nrm > T(0) ? T(1) - cgv * lamk / nrm : T(0);
+            bn = f > T(0) ? u / dkk * f : T(0);
+          } else if (kd == OEM_GROUP_MCP || kd == OEM_GROUP_SCAD) {
+            // the scalar rule on the norm, u's direction
+            const T bnorm = nrm > T(0) ? thr_scalar<T>(kd == OEM_GROUP_MCP ? OEM_MCP : OEM_SCAD, nrm,
+                                                       cgv * lamk, alk, gak, dkk)
+                                       : T(0);
+            bn = nrm > T(0) ? u * (bnorm / nrm) : T(0);
+          } else {
+            // reading of Eq. sglasso: the group step shrinks v by
+            // c_k lambda (1 - tau) / d
+            const T v = copysign(fmax(fabs(u) - wv[idx] * lamk * alk, T(0)) / dkk, u);
+            const T f = nrm > T(0) ? T(1) - cgv * lamk * (T(1) - alk) / (dkk * nrm) : T(0);
+            bn = f > T(0) ? v * f : T(0);
+          }
+          record(idx, i, bn);
+        };
+        auto vterm = [&](int idx, T u) {
+          return kd == OEM_SPARSE_GROUP_LASSO ? fmax(fabs(u) - wv[idx] * lamk * alk, T(0)) / dkk : u;
+        };
+        int r0 = wlo;
+        while (r0 < whi) {
+          const int i = r0 + lane;
+          const bool in = i < whi;
+          const int idx = k * maxR + (in ? i : r0);
+          const int len = in ? glen[idx] : 0;
+          const unsigned starts = __ballot_sync(0xffffffffu, len > 0);  // lane 0 is a start
+          const int mys = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));
+          const int myend = mys + __shfl_sync(0xffffffffu, len, mys) - 1;
+          const bool fits = in && myend < 32;
+          const unsigned nf = __ballot_sync(0xffffffffu, in && !fits);
+          if (nf & 1u) {
+            // the window's first group is longer than 32 rows
+            const int len0 = __shfl_sync(0xffffffffu, len, 0);
+            T s2 = T(0);
+            if (lane == 0) {
+              for (int q = 0; q < len0; ++q) {
+                const T v = vterm(idx + q, uhi[idx + q]);
+                s2 = fma(v, v, s2);
+              }
+              s2 = sqrt(s2);
+            }
+            s2 = __shfl_sync(0xffffffffu, s2, 0);
+            for (int q = lane; q < len0; q += 32) {
+              const int i2 = r0 + q, id2 = k * maxR + i2;
+              group_step(id2, i2, uhi[id2], s2);
+            }
+            r0 += len0;
+            continue;
+          }
+          const T u = fits ? uhi[idx] : T(0);
+          const T v = fits ? vterm(idx, u) : T(0);
+          T sc = v * v;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const T tq = __shfl_up_sync(0xffffffffu, sc, o);
+            if (lane - o >= mys) sc += tq;
+          }
+          const T nrm = sqrt(__shfl_sync(0xffffffffu, sc, fits ? myend : lane));
+          if (fits) group_step(idx, i, u, nrm);
+          r0 += nf ? __ffs(nf) - 1 : 32;
+        }
+      }
+      if constexpr (!kF32) {
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          const T a1 = warp_max(mx_d[k]), a2 = warp_max(mx_b[k]);
+          if (k == kq) { lmd = a1; lmb = a2; }
+        }
       }
       __syncwarp();
     }
@@ -559,7 +674,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
         // element (i0 is a multiple of 4, so st is unit-aligned)
         const int f0 = (i0 + wlo) * M, f1 = (i0 + whi) * M;
         const int u0 = f0 >> 2, nu = ((f1 + 3) >> 2) - u0;
-        T* Dn = Dbuf + (size_t)nxt * ldgs * M;
+        T* Dn = Dbuf + (size_t)nxt * ldd * M;
         const int CC = C;
         if constexpr (kGrid) {
           // this warp's dbeta words, tagged with the iteration number
@@ -612,22 +727,34 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
                   tag_word((uint32_t)(bits >> 32), (uint32_t)t + 1u));
         }
       } else {
-        T* Dn = Dbuf + (size_t)nxt * ldgs * M;
+        T* Dn = Dbuf + (size_t)nxt * ldd * M;
         for (int e = lane; e < nr * C; e += 32) {
           const int i = wlo + e / C, r = e % C;
           store_row<T, M>(cluster.map_shared_rank(Dn, r), i0 + i, st + (size_t)i * M);
         }
       }
-      // instance kq's warp maxima end in lane S kq (lanes of one instance
-      // differ in the row bits 32 / RG .. 16 of the lane index)
+      if constexpr (kF32) {
+        // the warp's maxima per instance into the block table
 #pragma unroll
-      for (int o = 32 / RG; o < 32; o <<= 1) {
-        lmd = fmax(lmd, __shfl_xor_sync(0xffffffffu, lmd, o));
-        lmb = fmax(lmb, __shfl_xor_sync(0xffffffffu, lmb, o));
-      }
-      if (even && rsub == 0) {
-        lred[(warp * M + kq) * 2] = to_red(lmd);
-        lred[(warp * M + kq) * 2 + 1] = to_red(lmb);
+        for (int k = 0; k < M; ++k) {
+          const T a1 = warp_max(mx_d[k]), a2 = warp_max(mx_b[k]);
+          if (lane == 0) {
+            lred[(warp * M + k) * 2] = to_red(a1);
+            lred[(warp * M + k) * 2 + 1] = to_red(a2);
+          }
+        }
+      } else {
+        // instance kq's warp maxima end in lane S kq (lanes of one instance
+        // differ in the row bits 32 / RG .. 16 of the lane index)
+#pragma unroll
+        for (int o = 32 / RG; o < 32; o <<= 1) {
+          lmd = fmax(lmd, __shfl_xor_sync(0xffffffffu, lmd, o));
+          lmb = fmax(lmb, __shfl_xor_sync(0xffffffffu, lmb, o));
+        }
+        if (even && rsub == 0) {
+          lred[(warp * M + kq) * 2] = to_red(lmd);
+          lred[(warp * M + kq) * 2 + 1] = to_red(lmb);
+        }
       }
     }
     __syncthreads();
@@ -661,6 +788,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
             if (clock64() - t0 > wait_lim) break;
         }
         ok = __all_sync(0xffffffffu, ok);
+        if (ok) build_list(nxt);
         unsigned int mx = 0u;
         for (int e = lane; e < C * E; e += 32) mx = max(mx, sl[e]);
         for (int o = E; o < 32; o <<= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -684,7 +812,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
       // maxima into slot t % 3: loads of a batch in flight at once, the stale
       // ones again after a short pause until their tag is this iteration's
       const uint32_t want = (uint32_t)t + 1u;
-      T* Dn = Dbuf + (size_t)nxt * ldgs * M;
+      T* Dn = Dbuf + (size_t)nxt * ldd * M;
       const int nw = p * M, nm = C * 2 * M;
       bool bad = false;
       long long w0c = 0;
@@ -741,6 +869,10 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
         if (tid == 0) atomicOr(P.dstatus, kStatTimeout);
         break;
       }
+      if constexpr (kF32) {
+        if (warp == 0) build_list(nxt);
+        __syncthreads();
+      }
     } else if constexpr (kAsync) {
       __syncthreads();
       if (*xfail) {
@@ -791,32 +923,47 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
     ++loops;
     if (P.max_loops > 0 && loops >= P.max_loops) break;
   }
-  if (regst && own) {
-    uhi[kq * maxR + i_own] = r_uhi;
-    ulo[kq * maxR + i_own] = r_ulo;
-  }
   __syncwarp();
   // ---- save the state for a later launch (serving): apply the pending dbeta
   if (tk.st_u) {
     if (!all_done && !skip_mv) {
-      const T* Dc = Dbuf + (size_t)(t & 1) * ldgs * M;
-      for (int ib = wlo; ib < whi; ++ib) {
-        const T* g0 = (ib < smem_rows) ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
-        T acc[M];
+      const T* Dc = Dbuf + (size_t)(t & 1) * ldd * M;
+      // the same sums as the loop's mat-vec, so that a resumed path is the
+      // same as an uninterrupted one
+      if constexpr (kF32) {
+        for (int r0 = wlo; r0 < whi; r0 += 32) {
+          const int i = r0 + lane;
+          const bool in = i < whi;
+          float a[M][4];
 #pragma unroll
-        for (int k = 0; k < M; ++k) acc[k] = T(0);
-        // same column order and lane tree as the loop's mat-vec, so a resumed
-        // path is the same as an uninterrupted one
-        if constexpr (kF32) {
-          for (int j4 = lane * 4; j4 < p; j4 += 128) {
-            const float4 g4 = *reinterpret_cast<const float4*>(g0 + j4);
-            const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+          for (int k = 0; k < M; ++k)
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
+            for (int c = 0; c < 4; ++c) a[k][c] = 0.f;
+          rows_matvec(r0, in, Dc, t & 1, a);
+          if (!in) continue;
 #pragma unroll
-              for (int k = 0; k < M; ++k) acc[k] = fma(gv[c], Dc[dpos<T, M>(j4 + c, k)], acc[k]);
+          for (int k = 0; k < M; ++k) {
+            if (k >= m) continue;
+            const int idx = k * maxR + i;
+            const T y = (a[k][0] + a[k][1]) + (a[k][2] + a[k][3]);
+            const T incr = fma(dk[k], Dc[dpos<T, M>(i0 + i, k)], -y);
+            if (incr != T(0)) {
+              const T h = uhi[idx];
+              const T s1 = h + incr, bb = s1 - h;
+              const T e = (h - (s1 - bb)) + (incr - bb);
+              const T lo = ulo[idx] + e;
+              const T hi2 = s1 + lo;
+              ulo[idx] = lo - (hi2 - s1);
+              uhi[idx] = hi2;
+            }
           }
-        } else {
+        }
+      } else {
+        for (int ib = wlo; ib < whi; ++ib) {
+          const T* g0 = (ib < smem_rows) ? Gs + (size_t)ib * ldgs : Gglob + (size_t)(i0 + ib) * ldgg;
+          T acc[M];
+#pragma unroll
+          for (int k = 0; k < M; ++k) acc[k] = T(0);
           for (int j = lane; j < p; j += 32) {
             T dv[M];
             load_col<T, M>(Dc, j, dv);
@@ -824,26 +971,14 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
 #pragma unroll
             for (int k = 0; k < M; ++k) acc[k] = fma(g, dv[k], acc[k]);
           }
-        }
 #pragma unroll
-        for (int k = 0; k < M; ++k) acc[k] = warp_sum(acc[k]);
-        if (lane == 0) {
+          for (int k = 0; k < M; ++k) acc[k] = warp_sum(acc[k]);
+          if (lane == 0) {
 #pragma unroll
-          for (int k = 0; k < M; ++k) {
-            if (k >= m) continue;
-            const int idx = k * maxR + ib;
-            const T incr = fma(dk[k], Dc[dpos<T, M>(i0 + ib, k)], -acc[k]);
-            if (incr == T(0)) {
-            } else if (kF32) {
-              const T h = uhi[idx];
-              const T s = h + incr, bb = s - h;
-              const T e = (h - (s - bb)) + (incr - bb);
-              const T lo = ulo[idx] + e;
-              const T hi2 = s + lo;
-              ulo[idx] = lo - (hi2 - s);
-              uhi[idx] = hi2;
-            } else {
-              uhi[idx] += incr;
+            for (int k = 0; k < M; ++k) {
+              if (k >= m) continue;
+              const T incr = fma(dk[k], Dc[dpos<T, M>(i0 + ib, k)], -acc[k]);
+              if (incr != T(0)) uhi[k * maxR + ib] += incr;
             }
           }
         }
@@ -878,6 +1013,23 @@ size_t oem_iter_rows_smem_fixed(int p, int npen, int max_rows, int precision) {
   const int tsz = precision == OEM_ITER_F64 ? 8 : 4;
   return iter_smem_layout(p, M, max_rows, tsz, 0).total;
 }
+
+size_t oem_iter_rows_smem_ucache(int p, int npen, int max_rows, int precision, int slots) {
+  const int M = oem_iter_mpad(npen);
+  const int tsz = precision == OEM_ITER_F64 ? 8 : 4;
+  return iter_smem_layout(p, M, max_rows, tsz, 0, slots).total;
+}
+
+int oem_iter_rows_ucache_slots(int p, int npen, int max_rows, int precision, size_t cap) {
+  if (precision == OEM_ITER_F64) return 0;
+  const size_t base = oem_iter_rows_smem_ucache(p, npen, max_rows, precision, 0);
+  if (base >= cap) return 0;
+  const size_t per = (size_t)max_rows * 64;  // one slot: a 16-column block of every row
+  const size_t q = (cap - base) / per;
+  return (int)std::min<size_t>(std::min<size_t>(q, (size_t)iter_blocks(p)), (size_t)kMaxBlockSlots);
+}
+
+int oem_iter_rows_blocks(int p) { return iter_blocks(p); }
 
 size_t oem_iter_rows_xbuf_bytes(int p, int M, int precision, int C) {
   const size_t W = precision == OEM_ITER_F64 ? 2 : 1, Mp = (size_t)oem_iter_mpad(M);

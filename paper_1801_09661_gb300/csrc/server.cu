@@ -373,7 +373,10 @@ static int launch_class(oem_server* S, const std::vector<SrvJob*>& jobs, int t0,
                         : oem_iter_smem_fixed((int)J->p, 1, k.max_rows, OEM_ITER_F32, false, groups);
         const size_t per = rows ? oem_iter_rows_smem_per_row((int)J->p, OEM_ITER_F32)
                                 : oem_iter_smem_per_row((int)J->p, OEM_ITER_F32);
-        smem = std::max(smem, std::min(kIterSmemCap, fixed[t] + (size_t)k.max_rows * per));
+        // row-owned kernel: the column-block cache (all blocks when they fit)
+        const size_t want = rows ? fixed[t] + (size_t)oem_iter_rows_blocks((int)J->p) * k.max_rows * 64
+                                 : fixed[t] + (size_t)k.max_rows * per;
+        smem = std::max(smem, std::min(kIterSmemCap, want));
       }
     }
     smem = std::max<size_t>(smem, 1024);
@@ -392,6 +395,10 @@ static int launch_class(oem_server* S, const std::vector<SrvJob*>& jobs, int t0,
                                   : oem_iter_smem_per_row((int)J->p, OEM_ITER_F32);
           k.p = (int)J->p; k.npen = 1; k.L = L; k.ldg = J->ldg;
           k.smem_rows = smem > fixed[t] ? (int)std::min<size_t>(k.max_rows, (smem - fixed[t]) / per) : 0;
+          if (rows) {
+            k.smem_rows = 0;
+            k.ucache = oem_iter_rows_ucache_slots((int)J->p, 1, k.max_rows, OEM_ITER_F32, smem);
+          }
           k.resume = J->rounds > 0 ? 1 : 0;
           k.G32 = J->G32 + (size_t)b * J->p * J->ldg;
           k.c = J->c + (size_t)b * J->p;

@@ -421,6 +421,33 @@ def test_row_owned_kernel_layouts_identical(oem, ctx):
     _check_paths(*runs[0], G, c, d, op, 10, 0.1, tol=1e-7, its_slack=0.25)
 
 
+def test_row_owned_unit_cache_overflow_identical(oem, ctx):
+    # p = 2100 with 16- and 8-CTA clusters: a slice's Gram rows do not fit in
+    # shared memory, so each CTA caches the 16-column blocks of G that nonzero
+    # dbeta entries touch (zero blocks are skipped). At the small lambdas of a
+    # dense lasso path more blocks are touched than the cache holds and the
+    # rest come from L2. Every layout gives the bits of grid mode (one task of
+    # both paths on 105 CTAs of 20 rows, every block of them cached).
+    p, n = 2100, 2600
+    X, y = _data(n, p, 41, np.float64)
+    G, c, N, _ = oracle.gram_sums(X, y)
+    G, c = G / n, c / n
+    d = oracle.lanczos_d(G)[0]
+    gp, op = _pens(p, [("lasso", {}), ("grp.lasso", {})], gsize=10)
+    runs = []
+    for ncl, mg in [(105, 2), (16, 1), (8, 2), (16, 2)]:
+        out = oem.oem_fit_path(ctx, _dev(G), _dev(c), gp, d=d, nlambda=5, lambda_min_ratio=0.02,
+                               tol=1e-7, max_iter=300, cluster_ctas=ncl, instances_per_task=mg,
+                               autotune=False)
+        assert ctx.sync() in (0, 1)  # 1: some lambda stopped at max_iter
+        runs.append([t.cpu().numpy() for t in out])
+    # enough active columns at the last lambda to overflow every warp's cache
+    assert int(np.count_nonzero(runs[0][0][0, -1])) > 600
+    for r in runs[1:]:
+        for a, b in zip(runs[0], r):
+            np.testing.assert_array_equal(a, b)
+
+
 def test_row_owned_kernel_beyond_4096_columns(oem, ctx):
     p, n = 4200, 9000
     X, y = _data(n, p, 37, np.float64)
