@@ -69,8 +69,9 @@ constexpr int iter_threads() { return 256; }
 // columns (four 16-byte units) of every row of the slice ([slot][unit][row]);
 // nzl[b] lists the column blocks of dbeta buffer b that hold a nonzero value
 // of some instance, in increasing order (entry: the block, and its slot's
-// offset in float4 | state << 30, state 0 cached, 1 to be filled by the
-// mat-vec that reads it, 2 without a slot), nzc[b] their count; cbit[s] has bit l set when block
+// offset in float4 | nonzero units << 26 | state << 30, state 0 cached, 1 to
+// be filled by the mat-vec that reads it, 2 without a slot), nzc[b] their
+// count; cbit[s] has bit l set when block
 // 32 s + l has been given a slot (or refused one); smap[k] is block k's slot
 // (-1: none).
 struct IterSmem {
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
     // without a slot (read from L2)
     auto block_any = [&](uint2 e) {
       const int kb = (int)e.x;
-      const unsigned st2 = e.y >> 30, off = e.y & 0x3FFFFFFFu;
+      const unsigned st2 = e.y >> 30, off = e.y & 0x3FFFFFFu;
       float dv[4][4][M];
       load_dv(kb, dv);
       float4 g[4];
@@ -369,15 +370,28 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
       for (; q + 2 <= cnt; q += 2) {
         const uint4 e2 = *reinterpret_cast<const uint4*>(lst + q);
         if (((e2.y | e2.w) >> 30) == 0u) {
+          // two cached blocks; a unit whose dbeta is zero for every
+          // instance (flag clear) is neither loaded nor added: its terms are
+          // exact zeros
           float dv[2][4][4][M];
           float4 g[2][4];
-          load_dv((int)e2.x, dv[0]);
-          load_dv((int)e2.z, dv[1]);
+          const unsigned ey[2] = {e2.y, e2.w}, ex[2] = {e2.x, e2.z};
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            g[0][j] = ucache[e2.y + (size_t)j * maxR + ii];
-            g[1][j] = ucache[e2.w + (size_t)j * maxR + ii];
-          }
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const bool on = (ey[h] >> (26 + j)) & 1u;
+              g[h][j] = on ? ucache[(ey[h] & 0x3FFFFFFu) + (size_t)j * maxR + ii] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+              for (int q = 0; q < M; ++q) {
+                const int uu = (4 * (int)ex[h] + j) * M + q;
+                const float4 tq = on ? *reinterpret_cast<const float4*>(Dbf + ((uu ^ ((uu >> 3) & (M - 1))) << 2))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float tv[4] = {tq.x, tq.y, tq.z, tq.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) dv[h][j][(q * 4 + c) / M][(q * 4 + c) % M] = tv[c];
+              }
+            }
           fma_block(g[0], dv[0]);
           fma_block(g[1], dv[1]);
         } else {
@@ -399,38 +413,56 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
     const int nbk = iter_blocks(p);
     uint2* lst = nzl + (size_t)b * nll;
     int base = 0;
-    for (int sw = 0; sw < nwd; ++sw) {
-      const int kb = 32 * sw + lane;
-      uint32_t o = 0u;
-      int slv = -1;
-      if (kb < nbk) {
-        // whole blocks: buffer rows past p are zero
+    constexpr int kSB = M <= 2 ? 4 : 1;  // words whose loads are in flight together
+    for (int s0 = 0; s0 < nwd; s0 += kSB) {
+      unsigned fl[kSB], cbw[kSB];  // per lane: its block's nonzero units (4 bits)
+      int slw[kSB];
 #pragma unroll
-        for (int j = 0; j < 4 * M; ++j) {
-          const int uu = 4 * kb * M + j;
-          const float4 v = *reinterpret_cast<const float4*>(Db + ((uu ^ ((uu >> 3) & (M - 1))) << 2));
-          o |= __float_as_uint(v.x) | __float_as_uint(v.y) | __float_as_uint(v.z) | __float_as_uint(v.w);
+      for (int q2 = 0; q2 < kSB; ++q2) {
+        const int kb = 32 * (s0 + q2) + lane;
+        fl[q2] = 0u;
+        slw[q2] = -1;
+        cbw[q2] = s0 + q2 < nwd ? cbit[s0 + q2] : 0u;
+        if (kb < nbk) {
+          // whole blocks: buffer rows past p are zero
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            uint32_t o = 0u;
+#pragma unroll
+            for (int q = 0; q < M; ++q) {
+              const int uu = (4 * kb + j) * M + q;
+              const float4 v = *reinterpret_cast<const float4*>(Db + ((uu ^ ((uu >> 3) & (M - 1))) << 2));
+              o |= __float_as_uint(v.x) | __float_as_uint(v.y) | __float_as_uint(v.z) | __float_as_uint(v.w);
+            }
+            fl[q2] |= ((o & 0x7fffffffu) != 0u ? 1u : 0u) << j;
+          }
+          slw[q2] = smap[kb];
         }
-        slv = smap[kb];
       }
-      const unsigned cb = cbit[sw];
-      const unsigned bits = __ballot_sync(0xffffffffu, (o & 0x7fffffffu) != 0u);
-      const unsigned nb = bits & ~cb;
-      unsigned state = slv >= 0 ? 0u : 2u;
-      if (nb) {  // blocks nonzero for the first time
-        const int sl = nslot + __popc(nb & ((1u << lane) - 1u));
-        if (((nb >> lane) & 1u) && sl < ucs) {
-          smap[kb] = (short)sl;
-          slv = sl;
-          state = 1u;
+#pragma unroll
+      for (int q2 = 0; q2 < kSB; ++q2) {
+        const int sw = s0 + q2;
+        if (sw >= nwd) break;
+        const int kb = 32 * sw + lane;
+        const unsigned bits = __ballot_sync(0xffffffffu, fl[q2] != 0u);
+        const unsigned nb = bits & ~cbw[q2];
+        int slv = slw[q2];
+        unsigned state = slv >= 0 ? 0u : 2u;
+        if (nb) {  // blocks nonzero for the first time
+          const int sl = nslot + __popc(nb & ((1u << lane) - 1u));
+          if (((nb >> lane) & 1u) && sl < ucs) {
+            smap[kb] = (short)sl;
+            slv = sl;
+            state = 1u;
+          }
+          nslot = min(ucs, nslot + __popc(nb));
+          if (lane == 0) cbit[sw] = cbw[q2] | nb;
         }
-        nslot = min(ucs, nslot + __popc(nb));
-        if (lane == 0) cbit[sw] = cb | nb;
+        if ((bits >> lane) & 1u)
+          lst[base + __popc(bits & ((1u << lane) - 1u))] =
+              make_uint2((unsigned)kb, (unsigned)(slv >= 0 ? slv * 4 * maxR : 0) | (fl[q2] << 26) | (state << 30));
+        base += __popc(bits);
       }
-      if ((bits >> lane) & 1u)
-        lst[base + __popc(bits & ((1u << lane) - 1u))] =
-            make_uint2((unsigned)kb, (unsigned)(slv >= 0 ? slv * 4 * maxR : 0) | (state << 30));
-      base += __popc(bits);
     }
     if (lane == 0) nzc[b] = base;
   };
