@@ -50,7 +50,14 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # launch reads its Gram once (independent of n); Gram passes are given per
 # row of X (bytes move in proportion to n). None until the current kernel has
 # been captured.
-NCU_DRAM_BYTES = {}
+NCU_DRAM_BYTES = {
+    # profiles/oem_iter_rows_kernel_group_lasso_bf16_n2e5_p2000.md: 9.28 MB per
+    # launch on the 2e5-row case (every touched 16-column block of G read
+    # once); the iteration reads only the Gram, so a launch of the 2e6-row
+    # workload moves the same
+    ("oem_iter_rows_kernel", "group_lasso_bf16_n2e6_p2000"): 9.279232e6,
+    ("oem_iter_rows_kernel", "group_lasso_bf16_n2e5_p2000"): 9.279232e6,
+}
 
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 HEADLINE = "group_lasso_bf16_n2e6_p2000"
@@ -520,9 +527,11 @@ def measure_workload(args, w, rank, world, local_rank, steps, warmup, gram_mode=
     it_ms_step = it_ms / steps
     it_bytes = loops * iteration_bytes(w)
     it_gbs = it_bytes / (it_ms_step / 1000.0) / 1e9
-    roofline = {"kernel": "oem_iter_kernel", "bound": "hbm", "achieved": it_gbs, "peak": hbm,
+    # the replicated-update kernel serves p <= 1024, the row-owned one beyond
+    it_kernel = "oem_iter_kernel" if p <= 1024 else "oem_iter_rows_kernel"
+    roofline = {"kernel": it_kernel, "bound": "hbm", "achieved": it_gbs, "peak": hbm,
                 "unit": "GB/s", "frac": it_gbs / hbm,
-                "traffic": NCU_DRAM_BYTES.get(("oem_iter_kernel", w.name)),
+                "traffic": NCU_DRAM_BYTES.get((it_kernel, w.name)),
                 "peak_source": peak_src, "algorithmic_bytes_per_step": it_bytes,
                 "algorithmic_bytes_per_loop": iteration_bytes(w), "loop_iterations": loops,
                 "oem_iterations": iters_total, "ms_per_step": it_ms_step,

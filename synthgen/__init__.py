@@ -234,6 +234,12 @@ WORKLOADS = {
         "group_lasso_bf16_n2e6_p2000", 2_000_000, 2000, "bf16", "block",
         sigma=2.0, beta="groups10", penalties=("grp.lasso",), group_size=10,
         seed=3, extra={"rho_in": 0.7, "rho_out": 0.2, "n_active_groups": 10}),
+    # the same problem at n = 200,000 (X = 800 MB, above L2) over a 20-lambda
+    # grid of the same range: profiler captures
+    "group_lasso_bf16_n2e5_p2000": Workload(
+        "group_lasso_bf16_n2e5_p2000", 200_000, 2000, "bf16", "block",
+        sigma=2.0, beta="groups10", penalties=("grp.lasso",), group_size=10, nlambda=20,
+        seed=3, extra={"rho_in": 0.7, "rho_out": 0.2, "n_active_groups": 10}),
 }
 
 
