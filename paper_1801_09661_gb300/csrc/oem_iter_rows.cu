@@ -70,8 +70,8 @@ constexpr int iter_threads() { return 256; }
 // nzl[b] lists the column blocks of dbeta buffer b that hold a nonzero value
 // of some instance, in increasing order (entry: the block, and its slot's
 // offset in float4 | nonzero units << 26 | state << 30, state 0 cached, 1 to
-// be filled by the mat-vec that reads it, 2 without a slot), nzc[b] their
-// count; cbit[s] has bit l set when block
+// be filled by the mat-vec that reads it, 2 without a slot), the blocks of
+// word s (blocks 32 s .. 32 s + 31) at entries 32 s + k, nzc[b][s] of them; cbit[s] has bit l set when block
 // 32 s + l has been given a slot (or refused one); smap[k] is block k's slot
 // (-1: none).
 struct IterSmem {
@@ -81,7 +81,7 @@ constexpr int kIterMaxWarps = 16;
 __host__ __device__ inline int iter_units(int p) { return (p + 3) >> 2; }     // 4 columns
 __host__ __device__ inline int iter_blocks(int p) { return (p + 15) >> 4; }    // 16 columns
 __host__ __device__ inline int iter_block_words(int p) { return (iter_blocks(p) + 31) >> 5; }
-__host__ __device__ inline int iter_list_len(int p) { return (iter_blocks(p) + 3) & ~3; }
+__host__ __device__ inline int iter_list_len(int p) { return 32 * iter_block_words(p); }
 constexpr int kMaxBlockSlots = 32767;  // slot + 1 takes 15 bits of a list entry
 // Rows of a dbeta buffer: float32 whole 16-column blocks, float64 4 rows.
 __host__ __device__ inline int iter_ldd(int p, int tsz) { return tsz == 4 ? (p + 15) & ~15 : (p + 3) & ~3; }
@@ -105,7 +105,7 @@ __host__ __device__ inline IterSmem iter_smem_layout(int p, int M, int maxR, int
   L.xbar = o;  o = al16(o + 2 * 8);
   L.xslot = o; o = al16(o + (size_t)2 * 16 * M * 2 * 4);
   L.xred = o;  o = al16(o + (size_t)(M * 2 + 1) * 4);
-  L.nzc = o;   o = al16(o + (f32 ? (size_t)2 * 4 : 0));
+  L.nzc = o;   o = al16(o + (f32 ? (size_t)(2 * nwd + 1) * 4 : 0));
   L.nzl = o;   o = al16(o + (f32 ? (size_t)2 * iter_list_len(p) * 8 : 0));
   L.cbit = o;  o = al16(o + (f32 ? (size_t)nwd * 4 : 0));
   L.smap = o;  o = al16(o + (f32 ? (size_t)nbk * 2 : 0));
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
   T* Gs = reinterpret_cast<T*>(smem + Ls.gs);
   const int nwd = iter_block_words(p);  // words of the block bitmaps
   const int nll = iter_list_len(p);
-  int* nzc = reinterpret_cast<int*>(smem + Ls.nzc);              // [2]
+  int* nzc = reinterpret_cast<int*>(smem + Ls.nzc);              // [2][nwd], then the slots given
   uint2* nzl = reinterpret_cast<uint2*>(smem + Ls.nzl);          // [2][nll]
   unsigned* cbit = reinterpret_cast<unsigned*>(smem + Ls.cbit);  // [nwd]
   short* smap = reinterpret_cast<short*>(smem + Ls.smap);        // [blocks]
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
   if constexpr (kF32) {
     for (int e = tid; e < iter_blocks(p); e += NT) smap[e] = -1;
     for (int e = tid; e < nwd; e += NT) cbit[e] = 0u;
-    if (tid < 2) nzc[tid] = 0;
+    for (int e = tid; e < 2 * nwd + 1; e += NT) nzc[e] = 0;
   } else {
     for (int e = tid; e < smem_rows * ldgs; e += NT) {
       const int i = e / ldgs, j = e % ldgs;
@@ -318,8 +318,6 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
     const int ii = in ? i : r0;  // a lane past the slice reads a valid row, unused
     const float* grow = reinterpret_cast<const float*>(Gglob) + (size_t)(i0 + ii) * ldgg;
     const float* Dbf = reinterpret_cast<const float*>(Db);
-    const uint2* lst = nzl + (size_t)b * nll;
-    const int cnt = nzc[b];
     // dbeta of block kb: units 4 kb + j, instances q
     auto load_dv = [&](int kb, float (&dv)[4][4][M]) {
 #pragma unroll
@@ -365,6 +363,9 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
       fma_block(g, dv);
     };
     constexpr int UB = M <= 2 ? 2 : 1;  // cached blocks whose loads are in flight together
+    for (int sw = 0; sw < nwd; ++sw) {
+    const uint2* lst = nzl + (size_t)b * nll + 32 * sw;
+    const int cnt = nzc[b * nwd + sw];
     int q = 0;
     if constexpr (UB == 2) {
       for (; q + 2 <= cnt; q += 2) {
@@ -401,70 +402,55 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
       }
     }
     for (; q < cnt; ++q) block_any(lst[q]);
-  };
-  // Float32, warp 0: the list of 16-column blocks of dbeta buffer b with a
-  // nonzero value (every CTA's rows have arrived), giving a cache slot to
-  // each block that is nonzero for the first time (in block order, while
-  // slots last; its entry is marked to be filled by the mat-vec that reads
-  // it).
-  int nslot = 0;  // slots given (uniform in warp 0)
-  auto build_list = [&](int b) {
-    const float* Db = reinterpret_cast<const float*>(Dbuf) + (size_t)b * ldd * M;
-    const int nbk = iter_blocks(p);
-    uint2* lst = nzl + (size_t)b * nll;
-    int base = 0;
-    constexpr int kSB = M <= 2 ? 4 : 1;  // words whose loads are in flight together
-    for (int s0 = 0; s0 < nwd; s0 += kSB) {
-      unsigned fl[kSB], cbw[kSB];  // per lane: its block's nonzero units (4 bits)
-      int slw[kSB];
-#pragma unroll
-      for (int q2 = 0; q2 < kSB; ++q2) {
-        const int kb = 32 * (s0 + q2) + lane;
-        fl[q2] = 0u;
-        slw[q2] = -1;
-        cbw[q2] = s0 + q2 < nwd ? cbit[s0 + q2] : 0u;
-        if (kb < nbk) {
-          // whole blocks: buffer rows past p are zero
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            uint32_t o = 0u;
-#pragma unroll
-            for (int q = 0; q < M; ++q) {
-              const int uu = (4 * kb + j) * M + q;
-              const float4 v = *reinterpret_cast<const float4*>(Db + ((uu ^ ((uu >> 3) & (M - 1))) << 2));
-              o |= __float_as_uint(v.x) | __float_as_uint(v.y) | __float_as_uint(v.z) | __float_as_uint(v.w);
-            }
-            fl[q2] |= ((o & 0x7fffffffu) != 0u ? 1u : 0u) << j;
-          }
-          slw[q2] = smap[kb];
-        }
-      }
-#pragma unroll
-      for (int q2 = 0; q2 < kSB; ++q2) {
-        const int sw = s0 + q2;
-        if (sw >= nwd) break;
-        const int kb = 32 * sw + lane;
-        const unsigned bits = __ballot_sync(0xffffffffu, fl[q2] != 0u);
-        const unsigned nb = bits & ~cbw[q2];
-        int slv = slw[q2];
-        unsigned state = slv >= 0 ? 0u : 2u;
-        if (nb) {  // blocks nonzero for the first time
-          const int sl = nslot + __popc(nb & ((1u << lane) - 1u));
-          if (((nb >> lane) & 1u) && sl < ucs) {
-            smap[kb] = (short)sl;
-            slv = sl;
-            state = 1u;
-          }
-          nslot = min(ucs, nslot + __popc(nb));
-          if (lane == 0) cbit[sw] = cbw[q2] | nb;
-        }
-        if ((bits >> lane) & 1u)
-          lst[base + __popc(bits & ((1u << lane) - 1u))] =
-              make_uint2((unsigned)kb, (unsigned)(slv >= 0 ? slv * 4 * maxR : 0) | (fl[q2] << 26) | (state << 30));
-        base += __popc(bits);
-      }
     }
-    if (lane == 0) nzc[b] = base;
+  };
+  // Float32, one warp: word sw of the list of 16-column blocks of dbeta
+  // buffer b with a nonzero value (every CTA's rows have arrived), giving a
+  // cache slot to each block that is nonzero for the first time (while
+  // slots last; its entry is marked to be filled by the mat-vec that reads
+  // it). Which block gets which slot does not change any result.
+  int* const nslot = nzc + 2 * nwd;  // slots given so far
+  auto build_word = [&](int b, int sw) {
+    const float* Db = reinterpret_cast<const float*>(Dbuf) + (size_t)b * ldd * M;
+    const int kb = 32 * sw + lane;
+    unsigned fl = 0u;  // the block's nonzero 4-column units
+    int slv = -1;
+    if (kb < iter_blocks(p)) {
+      // whole blocks: buffer rows past p are zero
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        uint32_t o = 0u;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+          const int uu = (4 * kb + j) * M + q;
+          const float4 v = *reinterpret_cast<const float4*>(Db + ((uu ^ ((uu >> 3) & (M - 1))) << 2));
+          o |= __float_as_uint(v.x) | __float_as_uint(v.y) | __float_as_uint(v.z) | __float_as_uint(v.w);
+        }
+        fl |= ((o & 0x7fffffffu) != 0u ? 1u : 0u) << j;
+      }
+      slv = smap[kb];
+    }
+    const unsigned cb = cbit[sw];
+    const unsigned bits = __ballot_sync(0xffffffffu, fl != 0u);
+    const unsigned nb = bits & ~cb;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned state = slv >= 0 ? 0u : 2u;
+    if (nb) {  // blocks nonzero for the first time
+      int base = 0;
+      if (lane == 0) base = atomicAdd(nslot, __popc(nb));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      const int sl = base + __popc(nb & lt);
+      if (((nb >> lane) & 1u) && sl < ucs) {
+        smap[kb] = (short)sl;
+        slv = sl;
+        state = 1u;
+      }
+      if (lane == 0) cbit[sw] = cb | nb;
+    }
+    if ((bits >> lane) & 1u)
+      nzl[(size_t)b * nll + 32 * sw + __popc(bits & lt)] =
+          make_uint2((unsigned)kb, (unsigned)(slv >= 0 ? slv * 4 * maxR : 0) | (fl << 26) | (state << 30));
+    if (lane == 0) nzc[b * nwd + sw] = __popc(bits);
   };
   int skip_mv = 1;      // dbeta of the previous iteration is all zero
   int all_done = 1;
@@ -798,9 +784,8 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
       if (lane < E)
         for (int w = 0; w < NW; ++w) v = fmax(v, lred[w * E + lane]);
       if constexpr (kAsync) {
-        // this CTA's maxima into entry [nxt][rank] of every CTA; then the
-        // wait for every peer's dbeta rows and maxima (bounded), and the
-        // maxima over the C entries into xred
+        // this CTA's maxima into entry [nxt][rank] of every CTA (the wait
+        // for every peer's dbeta rows and maxima follows in every warp)
         const uint32_t bar = xbar0 + 8 * nxt;
         unsigned int* sl = xslot + (size_t)nxt * 16 * E;
         for (int base = 0; base < C * E; base += 32) {
@@ -812,20 +797,6 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
           }
         }
         if (lane == 0) xs_arm(bar, (uint32_t)(((p - R) * M + (C - 1) * E) * 4));
-        const uint32_t par = (uint32_t)((t >> 1) & 1);
-        bool ok = xs_try(bar, par);
-        if (!ok) {
-          const long long t0 = clock64();
-          while (!(ok = xs_try(bar, par)))
-            if (clock64() - t0 > wait_lim) break;
-        }
-        ok = __all_sync(0xffffffffu, ok);
-        if (ok) build_list(nxt);
-        unsigned int mx = 0u;
-        for (int e = lane; e < C * E; e += 32) mx = max(mx, sl[e]);
-        for (int o = E; o < 32; o <<= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane < E) xred[lane] = mx;
-        if (lane == 0 && !ok) *xfail = 1u;
       } else if constexpr (kGrid) {
         if (lane < E)
           st_tag1(xm + ((size_t)nxt * C + rank) * E + lane, tag_word(__float_as_uint(v), (uint32_t)t + 1u));
@@ -902,10 +873,35 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
         break;
       }
       if constexpr (kF32) {
-        if (warp == 0) build_list(nxt);
+        for (int sw = warp; sw < nwd; sw += NW) build_word(nxt, sw);
         __syncthreads();
       }
     } else if constexpr (kAsync) {
+      // every warp waits (bounded) for the bytes addressed to this CTA, then
+      // builds its words of the list; warp 0 takes the maxima over the C
+      // entries into xred
+      {
+        constexpr int E = 2 * M;
+        const uint32_t bar = xbar0 + 8 * nxt;
+        const uint32_t par = (uint32_t)((t >> 1) & 1);
+        bool ok = xs_try(bar, par);
+        if (!ok) {
+          const long long t0 = clock64();
+          while (!(ok = xs_try(bar, par)))
+            if (clock64() - t0 > wait_lim) break;
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (ok)
+          for (int sw = warp; sw < nwd; sw += NW) build_word(nxt, sw);
+        if (warp == 0) {
+          const unsigned int* sl = xslot + (size_t)nxt * 16 * E;
+          unsigned int mx = 0u;
+          for (int e = lane; e < C * E; e += 32) mx = max(mx, sl[e]);
+          for (int o = E; o < 32; o <<= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+          if (lane < E) xred[lane] = mx;
+        }
+        if (lane == 0 && !ok) *xfail = 1u;
+      }
       __syncthreads();
       if (*xfail) {
         if (tid == 0) atomicOr(P.dstatus, kStatTimeout);
