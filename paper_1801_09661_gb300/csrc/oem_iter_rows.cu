@@ -78,6 +78,7 @@ struct IterSmem {
   size_t dbuf, uhi, ulo, beta, w, cgr, glen, st, lred, red, xbar, xslot, xred, nzc, nzl, cbit, smap, gs, total;
 };
 constexpr int kIterMaxWarps = 16;
+constexpr int kRowsWarps = 8;  // warps of the row-owned kernel (256 threads)
 __host__ __device__ inline int iter_units(int p) { return (p + 3) >> 2; }     // 4 columns
 __host__ __device__ inline int iter_blocks(int p) { return (p + 15) >> 4; }    // 16 columns
 __host__ __device__ inline int iter_block_words(int p) { return (iter_blocks(p) + 31) >> 5; }
@@ -103,7 +104,7 @@ __host__ __device__ inline IterSmem iter_smem_layout(int p, int M, int maxR, int
   L.lred = o;  o = al16(o + (size_t)kIterMaxWarps * M * 2 * 4);
   L.red = o;   o = al16(o + (size_t)3 * M * 2 * 4);
   L.xbar = o;  o = al16(o + 2 * 8);
-  L.xslot = o; o = al16(o + (size_t)2 * 16 * M * 2 * 4);
+  L.xslot = o; o = al16(o + (size_t)2 * 16 * kRowsWarps * M * 2 * 4);
   L.xred = o;  o = al16(o + (size_t)(M * 2 + 1) * 4);
   L.nzc = o;   o = al16(o + (f32 ? (size_t)(2 * nwd + 1) * 4 : 0));
   L.nzl = o;   o = al16(o + (f32 ? (size_t)2 * iter_list_len(p) * 8 : 0));
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
   float4* ucache = reinterpret_cast<float4*>(smem + Ls.gs);      // [ucs][4][maxR]
   constexpr bool kAsync = kF32 && !kGrid;
   const uint32_t xbar0 = xs_u32(smem + Ls.xbar);  // mbarriers of dbeta buffers 0 / 1
-  unsigned int* xslot = reinterpret_cast<unsigned int*>(smem + Ls.xslot);  // [2][C][2M]
+  unsigned int* xslot = reinterpret_cast<unsigned int*>(smem + Ls.xslot);  // [2][C][NW][2M]
   unsigned int* xred = reinterpret_cast<unsigned int*>(smem + Ls.xred);    // [2M], then the timeout flag
   volatile unsigned int* xfail = xred + 2 * M;
   const T* Gglob = kF32 ? reinterpret_cast<const T*>(tk.G32) : reinterpret_cast<const T*>(tk.G64);
@@ -258,9 +259,11 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
   for (int e = tid; e < 2 * ldd * M; e += NT) Dbuf[e] = T(0);
   for (int e = tid; e < maxR * M; e += NT) st[e] = T(0);  // padded instances keep dbeta = 0
   for (int e = tid; e < 3 * M * 2; e += NT) red[e] = 0u;
+  static_assert(NT / 32 == kRowsWarps, "warps of the row-owned kernel");
   if (kAsync && tid == 0) {
-    xs_init(xbar0);
-    xs_init(xbar0 + 8);
+    // one arrival per warp and phase (warp 0's carries the expected bytes)
+    xs_init_n(xbar0, NW);
+    xs_init_n(xbar0 + 8, NW);
     *xfail = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -751,7 +754,35 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
           store_row<T, M>(cluster.map_shared_rank(Dn, r), i0 + i, st + (size_t)i * M);
         }
       }
-      if constexpr (kF32) {
+      if constexpr (kAsync) {
+        // the warp's maxima per instance into entry [nxt][rank][warp] of
+        // every CTA (st.async counted on the peers' barriers); then the
+        // warp's arrival on this CTA's barrier, after its own stores (warp 0
+        // arms it with every byte the peers send)
+        constexpr int E = 2 * M;
+        const uint32_t bar = xbar0 + 8 * nxt;
+        unsigned int* slw = xslot + (((size_t)nxt * 16 + rank) * NW + warp) * E;
+        float mv[E];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          mv[2 * k] = to_red(warp_max(mx_d[k]));
+          mv[2 * k + 1] = to_red(warp_max(mx_b[k]));
+        }
+        for (int e = lane; e < C * E; e += 32) {
+          const int r = e / E, q = e % E;
+          float val = 0.f;
+#pragma unroll
+          for (int qq = 0; qq < E; ++qq)
+            if (qq == q) val = mv[qq];
+          if (r == rank) slw[q] = __float_as_uint(val);
+          else xs_st1(xs_map(xs_u32(slw + q), r), __float_as_uint(val), xs_map(bar, r));
+        }
+        __syncwarp();
+        if (lane == 0) {
+          if (warp == 0) xs_arm(bar, (uint32_t)(((p - R) * M + (C - 1) * NW * E) * 4));
+          else xs_arrive(bar);
+        }
+      } else if constexpr (kF32) {
         // the warp's maxima per instance into the block table
 #pragma unroll
         for (int k = 0; k < M; ++k) {
@@ -775,29 +806,16 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
         }
       }
     }
-    __syncthreads();
-    // ---- 3b. warp 0: the block's maxima into slot t % 3 of every CTA (the
-    // slot is zeroed after its decisions, two iterations before its reuse)
-    if (warp == 0) {
+    // ---- 3b. (without the asynchronous exchange) warp 0: the block's maxima
+    // into slot t % 3 of every CTA (the slot is zeroed after its decisions,
+    // two iterations before its reuse)
+    if constexpr (!kAsync) __syncthreads();
+    if (!kAsync && warp == 0) {
       constexpr int E = 2 * M;  // values per slot
       float v = 0.f;
       if (lane < E)
         for (int w = 0; w < NW; ++w) v = fmax(v, lred[w * E + lane]);
-      if constexpr (kAsync) {
-        // this CTA's maxima into entry [nxt][rank] of every CTA (the wait
-        // for every peer's dbeta rows and maxima follows in every warp)
-        const uint32_t bar = xbar0 + 8 * nxt;
-        unsigned int* sl = xslot + (size_t)nxt * 16 * E;
-        for (int base = 0; base < C * E; base += 32) {
-          const int e = base + lane, q = e % E, r = e / E;
-          const float val = __shfl_sync(0xffffffffu, v, q);
-          if (e < C * E) {
-            if (r == rank) sl[rank * E + q] = __float_as_uint(val);
-            else xs_st1(xs_map(xs_u32(sl + rank * E + q), r), __float_as_uint(val), xs_map(bar, r));
-          }
-        }
-        if (lane == 0) xs_arm(bar, (uint32_t)(((p - R) * M + (C - 1) * E) * 4));
-      } else if constexpr (kGrid) {
+      if constexpr (kGrid) {
         if (lane < E)
           st_tag1(xm + ((size_t)nxt * C + rank) * E + lane, tag_word(__float_as_uint(v), (uint32_t)t + 1u));
       } else {
@@ -894,9 +912,9 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
         if (ok)
           for (int sw = warp; sw < nwd; sw += NW) build_word(nxt, sw);
         if (warp == 0) {
-          const unsigned int* sl = xslot + (size_t)nxt * 16 * E;
+          const unsigned int* sl = xslot + (size_t)nxt * 16 * NW * E;
           unsigned int mx = 0u;
-          for (int e = lane; e < C * E; e += 32) mx = max(mx, sl[e]);
+          for (int e = lane; e < C * NW * E; e += 32) mx = max(mx, sl[e]);
           for (int o = E; o < 32; o <<= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
           if (lane < E) xred[lane] = mx;
         }
