@@ -72,8 +72,18 @@ __global__ void fold_scan_kernel(const int32_t* __restrict__ blk_counts, int64_t
 
 __global__ void fold_scatter_kernel(const uint8_t* __restrict__ fold, int64_t n, int K,
                                     const int32_t* __restrict__ blk_offsets,
-                                    int32_t* __restrict__ perm) {
+                                    int32_t* __restrict__ perm, int32_t* __restrict__ ipos,
+                                    const int64_t* __restrict__ fold_off) {
   __shared__ int32_t wcnt[32][kMaxK];
+  __shared__ int64_t padpre[kMaxK];  // zero rows of the packed copy before fold f
+  if (ipos && threadIdx.x == 0) {
+    int64_t run = 0;
+    for (int k = 0; k < K; ++k) {
+      padpre[k] = run;
+      const int64_t nk = fold_off[k + 1] - fold_off[k];
+      run += (nk + kGramPackRows - 1) / kGramPackRows * kGramPackRows - nk;
+    }
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < 32 * kMaxK; i += blockDim.x) (&wcnt[0][0])[i] = 0;
   __syncthreads();
@@ -97,6 +107,9 @@ __global__ void fold_scatter_kernel(const uint8_t* __restrict__ fold, int64_t n,
   if (f >= 0) {
     int64_t pos = (int64_t)blk_offsets[(int64_t)blockIdx.x * K + f] + wcnt[warp][f] + rank;
     perm[pos] = (int32_t)r;
+    if (ipos) ipos[r] = (int32_t)(pos + padpre[f]);
+  } else if (ipos && r < n) {
+    ipos[r] = -1;
   }
 }
 
@@ -133,9 +146,9 @@ cudaError_t launch_fold_scan(const int32_t* blk_counts, int64_t nblk, int K, int
 }
 
 cudaError_t launch_fold_scatter(const uint8_t* fold, int64_t n, int K, const int32_t* blk_offsets,
-                                int32_t* perm, cudaStream_t s) {
+                                int32_t* perm, int32_t* ipos, const int64_t* fold_off, cudaStream_t s) {
   int64_t nblk = (n + kSortRows - 1) / kSortRows;
-  fold_scatter_kernel<<<(unsigned)nblk, kSortRows, 0, s>>>(fold, n, K, blk_offsets, perm);
+  fold_scatter_kernel<<<(unsigned)nblk, kSortRows, 0, s>>>(fold, n, K, blk_offsets, perm, ipos, fold_off);
   return cudaGetLastError();
 }
 

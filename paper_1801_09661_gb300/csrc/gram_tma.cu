@@ -388,6 +388,8 @@ struct ZPackArgs {
   const float* shift;   // [p + 1] or NULL (split mode): subtracted exactly
   int32_t qp;           // packed columns (multiple of 64)
   const int32_t* perm;  // sorted -> original row, or NULL
+  const int32_t* ipos;  // original -> packed row (-1: no fold), or NULL
+  int64_t n;
   const int64_t* fold_off;  // [K+1] sorted offsets
   const int64_t* poff;      // [K+1] packed offsets
   int32_t K;
@@ -397,19 +399,39 @@ struct ZPackArgs {
 };
 
 // One warp per packed row; lane l converts columns [8 l, 8 l + 8) + 256 j.
+// With ipos the warps take X's rows in their own order (reads stream through
+// X; each row is written to its place in fold order), then the zero rows
+// that pad every fold; without it, the packed rows in order.
 __global__ void __launch_bounds__(256) zpack_kernel(ZPackArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t total = a.poff[a.K];
-  for (int64_t pr = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pr < total;
-       pr += nwarps) {
-    int k = 0;
-    while (k + 1 < a.K && a.poff[k + 1] <= pr) ++k;
-    const int64_t local = pr - a.poff[k];
-    int64_t row = -1;
-    if (local < a.fold_off[k + 1] - a.fold_off[k]) {
-      const int64_t sr = a.fold_off[k] + local;
-      row = a.perm ? (int64_t)a.perm[sr] : sr;
+  const int64_t total = a.ipos ? a.n + (a.poff[a.K] - a.fold_off[a.K]) : a.poff[a.K];
+  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < total;
+       task += nwarps) {
+    int64_t row = -1, pr = task;
+    if (a.ipos) {
+      if (task < a.n) {
+        pr = a.ipos[task];
+        if (pr < 0) continue;  // outside every fold
+        row = task;
+      } else {
+        int64_t j = task - a.n;
+        int k = 0;
+        for (;; ++k) {
+          const int64_t pad = (a.poff[k + 1] - a.poff[k]) - (a.fold_off[k + 1] - a.fold_off[k]);
+          if (j < pad || k + 1 >= a.K) break;
+          j -= pad;
+        }
+        pr = a.poff[k] + (a.fold_off[k + 1] - a.fold_off[k]) + j;
+      }
+    } else {
+      int k = 0;
+      while (k + 1 < a.K && a.poff[k + 1] <= pr) ++k;
+      const int64_t local = pr - a.poff[k];
+      if (local < a.fold_off[k + 1] - a.fold_off[k]) {
+        const int64_t sr = a.fold_off[k] + local;
+        row = a.perm ? (int64_t)a.perm[sr] : sr;
+      }
     }
     float yp[3] = {0.f, 0.f, 0.f};
     const float yshift = a.shift ? a.shift[a.p] : 0.f;
@@ -559,6 +581,7 @@ cudaError_t launch_zpack(const GramArgs& a, int K, const TmaBufs& t, cudaStream_
   ZPackArgs z{};
   z.X = a.X; z.xtype = a.xtype; z.ldx = a.ldx; z.p = a.p; z.y = (const float*)a.y;
   z.ycols = a.ycols; z.ocols = a.ocols; z.shift = a.shift; z.qp = t.qp; z.perm = a.perm; z.fold_off = a.ct.fold_off; z.poff = t.pc.fold_off;
+  z.ipos = a.ipos; z.n = a.n;
   z.K = K; z.rows_cap = t.rows_cap;
   z.zhi = (__nv_bfloat16*)t.zhi;
   z.zlo = (__nv_bfloat16*)t.zlo;

@@ -341,6 +341,7 @@ inline GramPlan plan_gram(oem_ctx* ctx, int64_t n, int64_t p, int K, int32_t mod
 
 struct GramBufs {
   int32_t *blk_counts = nullptr, *blk_offsets = nullptr, *perm = nullptr;
+  int32_t* ipos = nullptr;  // packed copy in fold order: each row's packed row
   ChunkTable ct{};
   double* partial = nullptr;
   double* Zg = nullptr;
@@ -354,6 +355,7 @@ inline void gram_request(Arena& A, const GramPlan& g, int64_t n, GramBufs& b) {
     A.add(&b.blk_counts, (size_t)g.nblk * g.K);
     A.add(&b.blk_offsets, (size_t)g.nblk * g.K);
     A.add(&b.perm, (size_t)n);
+    if (g.tma && !g.direct) A.add(&b.ipos, (size_t)n);
   }
   A.add(&b.ct.row0, (size_t)g.max_chunks);
   A.add(&b.ct.row1, (size_t)g.max_chunks);
@@ -384,13 +386,14 @@ inline int run_gram(oem_ctx* ctx, const GramPlan& g, GramBufs& b, const void* X,
     LAUNCH(OEM_PROF_FOLD_SORT, launch_fold_count(fold, n, g.K, b.blk_counts, g.nblk, s));
     LAUNCH(OEM_PROF_FOLD_SORT, launch_fold_scan(b.blk_counts, g.nblk, g.K, g.chunk_rows, b.blk_offsets, b.ct,
                             g.max_chunks, ctx->dstatus, require_nonempty ? 1 : 0, s));
-    LAUNCH(OEM_PROF_FOLD_SORT, launch_fold_scatter(fold, n, g.K, b.blk_offsets, b.perm, s));
+    LAUNCH(OEM_PROF_FOLD_SORT, launch_fold_scatter(fold, n, g.K, b.blk_offsets, b.perm, b.ipos, b.ct.fold_off, s));
   } else {
     LAUNCH(OEM_PROF_CHUNKS, launch_identity_chunks(n, g.chunk_rows, b.ct, g.max_chunks, s));
   }
   GramArgs a{};
   a.X = X; a.xtype = xtype; a.n = n; a.p = p; a.ldx = ldx; a.y = y;
   a.perm = g.sorted ? b.perm : nullptr;
+  a.ipos = g.sorted ? b.ipos : nullptr;
   a.mode = g.mode; a.q = g.q; a.ycols = g.ycols; a.T = g.T; a.ntile1 = g.nt; a.ntiles = g.ntiles;
   a.ocols = g.ocols;
   if (g.centre) {

@@ -44,6 +44,7 @@ struct GramArgs {
   int64_t n, p, ldx;
   const void* y;
   const int32_t* perm;  // sorted row -> original row (NULL = identity)
+  const int32_t* ipos;  // original row -> packed row (-1: no fold), or NULL
   int32_t mode;         // OEM_GRAM_*
   int32_t q;            // augmented columns: p + ycols + ocols
   int32_t ycols;        // y columns appended (1, or 3 bfloat16 pieces)
@@ -89,8 +90,11 @@ cudaError_t launch_fold_count(const uint8_t* fold, int64_t n, int K, int32_t* bl
 cudaError_t launch_fold_scan(const int32_t* blk_counts, int64_t nblk, int K, int64_t chunk_rows,
                              int32_t* blk_offsets, ChunkTable ct, int max_chunks,
                              unsigned* dstatus, int require_nonempty, cudaStream_t s);
+// ipos (or NULL): each row's row in the packed copy of Z, in fold order with
+// every fold padded with zero rows to a multiple of kGramPackRows (-1 for a
+// row outside every fold); fold_off: the folds' offsets in sorted order
 cudaError_t launch_fold_scatter(const uint8_t* fold, int64_t n, int K, const int32_t* blk_offsets,
-                                int32_t* perm, cudaStream_t s);
+                                int32_t* perm, int32_t* ipos, const int64_t* fold_off, cudaStream_t s);
 cudaError_t launch_identity_chunks(int64_t n, int64_t chunk_rows, ChunkTable ct, int max_chunks,
                                    cudaStream_t s);
 
