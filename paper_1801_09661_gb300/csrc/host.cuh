@@ -776,8 +776,8 @@ inline int64_t iter_wait_cycles() {
 }
 
 // Tests of the timeout path only: OEM_DEVICE_WAIT_TEST=1 makes the first
-// exchange of every replicated-kernel launch wait for data that nobody
-// sends, so that its bounded wait expires.
+// exchange of every iteration launch wait for data that nobody sends, so
+// that its bounded wait expires.
 inline int iter_test_stall() {
   const char* v = std::getenv("OEM_DEVICE_WAIT_TEST");
   return (v && v[0] == '1') ? 1 : 0;
@@ -1031,7 +1031,7 @@ inline int launch_iter_layout(oem_ctx* ctx, int64_t p, int B, const float* G32, 
   Lc.wide = (!I.rows && o->iter_precision == OEM_ITER_F32 && p > kIterWideP && I.max_rows <= 16 &&
              I.M <= 2) ? 1 : 0;
   Lc.wait_cycles = iter_wait_cycles();
-  Lc.test_stall = I.rows ? 0 : iter_test_stall();
+  Lc.test_stall = iter_test_stall();
   if (I.rows) LAUNCH(OEM_PROF_ITER, launch_oem_iter_rows(Lc, s));
   else LAUNCH(OEM_PROF_ITER, launch_oem_iter(Lc, s));
   return OEM_OK;

@@ -357,7 +357,7 @@ struct IterLaunch {
   int64_t max_loops;     // per launch (<= 0: run to completion)
   int64_t wait_cycles;   // bound of every device wait (clock64 cycles)
   int32_t test_stall;    // tests only: the first exchange waits for data nobody sends,
-                         // so its bounded wait runs out (replicated kernel)
+                         // so its bounded wait runs out (both iteration kernels)
   unsigned* dstatus;
   size_t smem;
 };

@@ -779,7 +779,10 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
         }
         __syncwarp();
         if (lane == 0) {
-          if (warp == 0) xs_arm(bar, (uint32_t)(((p - R) * M + (C - 1) * NW * E) * 4));
+          // test_stall: four bytes more than the peers send, so the first
+          // wait of the launch must run out
+          if (warp == 0)
+            xs_arm(bar, (uint32_t)(((p - R) * M + (C - 1) * NW * E) * 4) + ((P.test_stall && t == 0) ? 4u : 0u));
           else xs_arrive(bar);
         }
       } else if constexpr (kF32) {
@@ -832,7 +835,8 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
       // every CTA's dbeta words into this CTA's next buffer, and every CTA's
       // maxima into slot t % 3: loads of a batch in flight at once, the stale
       // ones again after a short pause until their tag is this iteration's
-      const uint32_t want = (uint32_t)t + 1u;
+      // test_stall: the first exchange waits for a tag that nobody writes
+      const uint32_t want = (uint32_t)t + 1u + ((P.test_stall && t == 0) ? 1u : 0u);
       T* Dn = Dbuf + (size_t)nxt * ldd * M;
       const int nw = p * M, nm = C * 2 * M;
       bool bad = false;

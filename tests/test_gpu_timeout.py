@@ -38,9 +38,12 @@ def _problem(p=300, n=6000, seed=4):
     return torch.from_numpy(G / n).cuda(), torch.from_numpy(c / n).cuda()
 
 
-@pytest.mark.parametrize("layout", [{"cluster_ctas": 8}, {"cluster_ctas": 40}])
-def test_expired_wait_reports_timeout_and_context_stays_usable(oem, layout):
-    G, c = _problem()
+# p = 300: the replicated-update kernel; p = 1100: the row-owned kernel (every
+# warp of a CTA waits on the cluster barrier, or polls the tagged words)
+@pytest.mark.parametrize("p,layout", [(300, {"cluster_ctas": 8}), (300, {"cluster_ctas": 40}),
+                                      (1100, {"cluster_ctas": 16}), (1100, {"cluster_ctas": 60})])
+def test_expired_wait_reports_timeout_and_context_stays_usable(oem, p, layout):
+    G, c = _problem(p=p)
     pens = [oem.Penalty("lasso"), oem.Penalty("mcp", gamma=3.0)]
     kw = dict(nlambda=30, lambda_min_ratio=1e-2, tol=1e-7, autotune=False, **layout)
     ctx = oem.Context(0)
