@@ -51,12 +51,12 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # row of X (bytes move in proportion to n). None until the current kernel has
 # been captured.
 NCU_DRAM_BYTES = {
-    # profiles/oem_iter_rows_kernel_group_lasso_bf16_n2e5_p2000.md: 9.28 MB per
+    # profiles/oem_iter_rows_kernel_group_lasso_bf16_n2e5_p2000.md: 9.06 MB per
     # launch on the 2e5-row case (every touched 16-column block of G read
     # once); the iteration reads only the Gram, so a launch of the 2e6-row
     # workload moves the same
-    ("oem_iter_rows_kernel", "group_lasso_bf16_n2e6_p2000"): 9.279232e6,
-    ("oem_iter_rows_kernel", "group_lasso_bf16_n2e5_p2000"): 9.279232e6,
+    ("oem_iter_rows_kernel", "group_lasso_bf16_n2e6_p2000"): 9.056512e6,
+    ("oem_iter_rows_kernel", "group_lasso_bf16_n2e5_p2000"): 9.056512e6,
 }
 
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
