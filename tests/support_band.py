@@ -1,4 +1,4 @@
-"""Support comparison with the band of the benchmark spec's rule (test helper).
+"""Support comparison within a band around the thresholds (test helper).
 
 The support of the GPU path must equal the FP64 oracle's except where the
 oracle's |u_j| / d (or ||u_g|| / d for a group) lies within `band` of the
