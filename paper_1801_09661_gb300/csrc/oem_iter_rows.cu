@@ -14,38 +14,43 @@
 // One thread-block cluster per task (a Gram with its instances; tasks of one
 // launch may differ in p). CTA r of the cluster owns rows [slice[r],
 // slice[r+1]) of G, u and beta; inside the CTA every warp owns a contiguous
-// block of those rows (aligned to group starts for the group lasso). Per
-// iteration a warp, on its own rows and with no block-wide barrier:
-//   1. forms (G dbeta)_i for all instances of the task at once, 16 / M rows
-//      at a time so that one pass over dbeta serves the group (lane l reads
-//      columns 4l .. 4l+3, + 128, ...; G rows in registers when a warp has
-//      one row group and p <= 512, else resident in shared memory, the rest
-//      read from L2); a reduce-scatter leaves each (row, instance) sum in one
-//      lane pair, which updates u_i and, without groups, applies the
-//      threshold;
-//   2. for group penalties, forms the group norms and thresholds afterwards;
-//   3. writes its dbeta rows into the shared memory of every CTA of the
-//      cluster and its max|dbeta|, max|beta| per instance into the block's
-//      table.
-// One block barrier, then one warp sends the CTA's maxima to every CTA.
-// Float32 iteration: the dbeta rows and the maxima go out as st.async
-// stores, each counting its bytes on the receiving CTA's mbarrier for that
-// buffer, so a CTA waits (bounded) for exactly the bytes addressed to it and
-// there is no cluster barrier in the loop; one warp then takes the maximum
-// over the C entries. Float64 iteration: plain DSMEM stores, DSMEM atomic
-// max into every CTA's slot (order-preserving 32-bit images) and one cluster
-// barrier per iteration. Every thread then takes the same convergence
-// decisions from the same values. A launch may stop after a loop budget and
-// save its state (serving), to be resumed by a later launch.
+// block of those rows (aligned to group starts for the group penalties).
+// Float32 iteration, per iteration and warp (lane = row):
+//   1. y_i = (G dbeta)_i for every instance over the list of 16-column
+//      blocks of dbeta that hold a nonzero value, in increasing column order
+//      with one accumulator per column of each 4-column unit (a zero unit is
+//      skipped: it would add exact zeros), so the sums depend on the nonzero
+//      units only and every layout gives the same bits; G's blocks come from
+//      a cache in shared memory, filled from L2 by the first mat-vec that
+//      needs them (blocks beyond its slots are read from L2 each time); then
+//      the u update and, without groups, the threshold;
+//   2. for group penalties, windows of 32 rows that start at a group start
+//      and hold whole groups: the group norms by segmented warp scans, then
+//      the group steps;
+//   3. its dbeta rows and its own maxima (max|dbeta|, max|beta| per
+//      instance) go to every CTA of the cluster as st.async stores counted
+//      on the receiver's mbarrier for that buffer, then the warp arrives on
+//      its own CTA's barrier (warp 0 arms it with every byte the peers send);
+//   4. every warp waits (bounded) for the bytes addressed to its CTA, builds
+//      its words of the next buffer's block list (giving cache slots to
+//      blocks that are new), and warp 0 takes the maxima over the C x 8
+//      warps' entries; one block barrier, then every thread takes the same
+//      convergence decisions from the same values.
+// Float64 iteration: a warp forms (G dbeta)_i RG rows at a time (lane l
+// takes columns l, l + 32, ...; one reduce-scatter per row group) from the
+// rows resident in shared memory or from L2; plain DSMEM stores, a DSMEM
+// atomic max of the CTA's maxima into every CTA's slot (order-preserving
+// 32-bit images) and one cluster barrier per iteration. A launch may stop
+// after a loop budget and save its state (serving), to be resumed by a later
+// launch.
 //
-// Grid mode (large p: the Gram rows of a task do not fit in the shared memory
-// of one cluster, at most 16 SMs, but fit in that of C > 16 CTAs): the C CTAs
+// Grid mode (the slices of one cluster, at most 16 SMs, cannot keep the
+// Gram's blocks in shared memory, but those of C > 16 CTAs can): the C CTAs
 // of a task are an ordinary group of a cooperative launch, one per SM. Each
-// iteration a CTA reads the whole dbeta from global memory (L2) into its
-// shared memory, writes its own rows of the new dbeta back to global memory,
-// folds its maxima into a global slot with atomics, and waits at a
-// global-memory barrier of the group (bounded spin) instead of the cluster
-// barrier. The arithmetic is the same as in cluster mode.
+// iteration a CTA writes its rows of the new dbeta and its maxima to global
+// memory as 64-bit words tagged with the exchange number, and polls (bounded)
+// for every CTA's words of this exchange; the arithmetic is the same as in
+// cluster mode.
 #include "oem_internal.cuh"
 #include "iter_common.cuh"
 
