@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
   constexpr bool kF32 = sizeof(T) == 4;
 
   extern __shared__ __align__(16) unsigned char smem[];
-  const int ucs = kF32 ? tk.ucache : 0;  // column-unit cache slots
+  const int ucs = kF32 ? tk.ucache : 0;  // column-block cache slots
   const IterSmem Ls = iter_smem_layout(p, M, maxR, (int)sizeof(T), tk.smem_rows, ucs);
   T* Dbuf = reinterpret_cast<T*>(smem + Ls.dbuf);
   T* uhi = reinterpret_cast<T*>(smem + Ls.uhi);
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(NT, 1) oem_iter_rows_kernel(IterLaunch P) {
     cluster.sync();  // every CTA initialised before any DSMEM access
   }
 
-  // Lane roles in the row-group mat-vec: a group is RG rows (V = RG M sums);
+  // Float64 lane roles in the row-group mat-vec: a group is RG rows (V = RG M sums);
   // after the reduce-scatter lane l holds the sum of value v = l / S,
   // S = 32 / V, i.e. row rsub = v / M of the group and instance kq = v % M
   // (the first lane of each group of S acts).
